@@ -1,0 +1,149 @@
+/*
+ * ohm.h -- C ABI of libohm, a single-GPU (GB300, sm_103a) solver for one implicit step of
+ * ohmic dissipation, dB/dt = -curl(eta curl B), on a block-structured AMR hierarchy of
+ * 8^3-cell blocks (T. Matsumoto 2011, "An Implicit Scheme for Ohmic Dissipation with
+ * Adaptive Mesh Refinement", Sec. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev are CUDA device pointers; everything else is host memory.
+ * - Vector fields are contiguous float64 arrays [nblocks][3][8][8][8] in the order of the
+ *   descriptor's block list, innermost index along x ([comp][k][j][i]); eta is
+ *   [nblocks][8][8][8].  The caller owns these buffers; the library never frees them.
+ * - The hierarchy owns every scratch buffer.  It allocates them once, in
+ *   ohm_create_hierarchy; no other call allocates device memory.
+ * - Work is issued on the stream given in the descriptor (NULL = the legacy default
+ *   stream).  Calls that return norms or convergence data synchronise that stream.
+ * - Every entry point returns OHM_OK (0) or a negative status and never throws.  Arguments
+ *   are validated before any work is issued: on OHM_ERR_INVALID nothing was modified.
+ * - Periodic boundaries on all sides (every test of Sec. 3 is periodic).
+ */
+#ifndef OHM_H
+#define OHM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OHM_OK                 0
+#define OHM_ERR_INVALID       -1  /* bad descriptor, nesting, size, dt <= 0, NULL pointer   */
+#define OHM_ERR_NOT_CONVERGED -2  /* max_outer cycles ran; B holds the last iterate       */
+#define OHM_ERR_NONFINITE     -3  /* a residual norm became NaN or Inf                      */
+#define OHM_ERR_OOM           -4  /* device allocation failed in ohm_create_hierarchy      */
+#define OHM_ERR_CUDA          -5  /* a CUDA call or kernel launch failed                    */
+
+#define OHM_FP64  0  /* every kernel in float64                                             */
+#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the residual
+                        R = S - L B, the update B += e, refluxed fluxes and norms stay float64 */
+
+typedef struct ohm_hier ohm_hier;
+
+/* The problem statement of Sec. 2.1 (Eqs. 7, 12-14): unknown B^{n+1} given b = B^n, eta,
+ * dt and the theta parameter lambda, on a hierarchy of cubic cells. */
+typedef struct {
+    int32_t base_cells[3];      /* level-0 cells along x, y, z; each a positive multiple of 8  */
+    double dx0;                 /* level-0 cell width; level l has dx0 / 2^l                   */
+    int32_t nlevels;            /* 1 + number of refinement levels (ratio 2), at most 8        */
+    int64_t nblocks;            /* blocks over all levels                                      */
+    const int32_t *block_lijk;  /* host, 4 int32 per block: level, bi, bj, bk.  Sorted by
+                                   level (level 0 first).  Level 0 must tile the base grid; a
+                                   refined block has all 8 children; the 26 neighbours of a
+                                   refined block's parent exist (proper nesting).  Copied.     */
+    double lambda;              /* theta parameter of Eq. 7: 0.5 Crank-Nicolson, 1 backward
+                                   Euler; any value in (0, 1]                                  */
+    int32_t precision;          /* OHM_FP64 or OHM_MIXED                                       */
+    int32_t nu_pre, nu_post;    /* red-black sweeps before / after coarse correction (>= 0)   */
+    int32_t n_coarse;           /* red-black sweeps on the coarsest grid (>= 1)               */
+    int32_t max_outer;          /* defect-correction cycles allowed per step (>= 1)           */
+    void *stream;               /* cudaStream_t used for all work, NULL = legacy default      */
+} ohm_hier_desc;
+
+typedef struct {
+    int32_t cycles;             /* V-cycles applied (Eqs. 16-18 iterations)                   */
+    int32_t converged;          /* 1 when ||R||/||S|| <= tol was reached                       */
+    double rel_l2_initial;      /* ||S - L b||_2 / ||S||_2 before the first cycle             */
+    double rel_l2;              /* final ||R||_2 / ||S||_2 (leaf cells, volume weighted)       */
+    double max_abs;             /* final max over leaf cells and components of |R| (Sec. 3.1) */
+} ohm_step_stats;
+
+/* Builds the block tables, the multigrid grids below level 0 (coarsened by 2 while every
+ * dimension is even and >= 4) and allocates all device scratch.  *out receives the handle
+ * (NULL on failure).  The coarsest grids are solved inside one thread block; base grids
+ * whose first non-multiple-of-8 coarsening has more than 16384 cells are rejected. */
+int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out);
+
+/* Copies eta (> 0 and finite, [nblocks][8][8][8], every block including covered ones) into
+ * the hierarchy and derives the coarse-fine eta ghosts and the multigrid eta (mean of the 8
+ * children, Sec. 2.2).  Returns OHM_ERR_INVALID for a NULL pointer. */
+int ohm_set_eta(ohm_hier *h, const double *eta_dev);
+
+/* One theta-scheme step, Sec. 2.1-2.3: S = b - (1-lambda) dt div f(b) (Eq. 14), then
+ * R = S - L B and B += MG(0, R) (Eqs. 16-18) from B = b until ||R||/||S|| <= tol or
+ * max_outer cycles.  B_dev is in/out: b on entry, B^{n+1} on return, with covered cells set
+ * to the mean of their children.  eta_dev may be NULL to keep the current eta; otherwise it
+ * is set first as by ohm_set_eta.  tol < 0 runs exactly max_outer cycles (fixed schedule).
+ * stats may be NULL.  Returns OHM_OK, OHM_ERR_NOT_CONVERGED (B = last iterate),
+ * OHM_ERR_NONFINITE, OHM_ERR_INVALID (dt <= 0, no eta set, NULL B) or OHM_ERR_CUDA. */
+int ohm_cn_step(ohm_hier *h, double *B_dev, const double *eta_dev, double dt, double tol,
+                ohm_step_stats *stats);
+
+/* R = S - L B (Eq. 20) for the S and dt of the most recent ohm_cn_step: *rel_l2 receives
+ * ||R||_2/||S||_2 over leaf cells (volume weighted), *max_abs the largest |R| component.
+ * B_dev is read only (its covered cells are not used).  OHM_ERR_INVALID before any step. */
+int ohm_residual_norm(ohm_hier *h, const double *B_dev, double *rel_l2, double *max_abs);
+
+void ohm_destroy(ohm_hier *h);
+const char *ohm_status_string(int status);
+
+/* ---------------------------------------------------------------------------------------
+ * Row-level entry points: each runs one step of the hot path on caller buffers, so every
+ * step can be compared with an independent implementation.  Same layouts and status codes
+ * as above; all are stream ordered and synchronise only where they return host scalars.
+ * ------------------------------------------------------------------------------------- */
+
+/* Composite flux divergence (Eqs. 4-11 and 8) on leaf cells: covered cells are first set to
+ * the mean of their children in a private copy, coarse-fine ghosts are interpolated from
+ * the parent level, and coarse faces at coarse-fine interfaces take the mean of the four
+ * fine fluxes (refluxing, Sec. 4).  out_dev receives 0 on covered blocks. */
+int ohm_op_div_flux(ohm_hier *h, const double *B_dev, double *out_dev);
+
+/* S = b - (1 - lambda) dt div f(b) on leaf cells (Eq. 14), same rules as ohm_op_div_flux. */
+int ohm_op_source(ohm_hier *h, const double *b_dev, double dt, double *S_dev);
+
+/* R = S - B - lambda dt div F(B) on leaf cells (Eqs. 13, 20); norms (host, may be NULL)
+ * receives {||R||/||S||, max|R|, ||R||, ||S||} over leaf cells. */
+int ohm_op_residual(ohm_hier *h, const double *B_dev, const double *S_dev, double dt,
+                    double *R_dev, double *norms);
+
+/* Covered cells := mean of their 8 children, finest level first, in place. */
+int ohm_op_sync_down(ohm_hier *h, double *B_dev);
+
+/* One multigrid V-cycle from a zero guess for the composite residual R_dev (leaf cells):
+ * e_dev receives the correction on leaf cells and 0 on covered blocks.  OHM_FP64 only. */
+int ohm_op_vcycle(ohm_hier *h, const double *R_dev, double dt, double *e_dev);
+
+/* Shape of base multigrid grid m (0 = level 0): dims[3] cells, *nblocks its 8^3 blocks
+ * (0 when the grid is not a multiple of 8 and lives in lexicographic [comp][z][y][x]
+ * layout inside the coarsest-grid solver); when ijk is not NULL it receives 3 int32 per
+ * block (bi, bj, bk) in the grid's storage order (the caller's order for m = 0). */
+int ohm_mg_grid_info(ohm_hier *h, int m, int32_t dims[3], int64_t *nblocks, int32_t *ijk);
+
+/* Single-grid steps on blocked base multigrid grid m (OHM_FP64; arrays in that grid's
+ * block layout; eta_dev [nblocks][8][8][8]):
+ *   smooth:  one red-black colour pass (Eq. 19 with alpha from Eqs. 21-23) in place on e;
+ *   residual: t = r - (e + lambda dt div F(e));
+ *   restrict: coarse grid m+1 (blocked) = mean of 8 children of fine grid m, ncomp comps;
+ *   prolong_add: fine grid m += trilinear interpolation of coarse grid m+1 (blocked). */
+int ohm_op_grid_smooth(ohm_hier *h, int m, double *e_dev, const double *r_dev,
+                       const double *eta_dev, double dt, int colour);
+int ohm_op_grid_residual(ohm_hier *h, int m, const double *e_dev, const double *r_dev,
+                         const double *eta_dev, double dt, double *t_dev);
+int ohm_op_grid_restrict(ohm_hier *h, int m, const double *fine_dev, double *coarse_dev, int ncomp);
+int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double *fine_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OHM_H */

@@ -1,0 +1,926 @@
+// ohm_host.cpp -- hierarchy construction, device memory plan, multigrid schedule and the
+// C ABI of libohm (declared in include/ohm.h).  Every arithmetic step runs in the kernels of
+// ohm_kernels.cu; this file only builds index tables, allocates once and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ohm.h"
+#include "ohm_internal.h"
+
+using namespace ohm;
+
+namespace {
+
+constexpr int MAX_LEVELS = 8;
+constexpr int MAX_BOTTOM_CELLS = 16384;
+
+inline int wrapi(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+inline int64_t key3(int i, int j, int k) { return ((int64_t)k << 42) | ((int64_t)j << 21) | (int64_t)i; }
+
+uint64_t morton(int i, int j, int k) {
+    uint64_t m = 0;
+    for (int b = 0; b < 21; b++)
+        m |= ((uint64_t)((i >> b) & 1) << (3 * b)) | ((uint64_t)((j >> b) & 1) << (3 * b + 1)) |
+             ((uint64_t)((k >> b) & 1) << (3 * b + 2));
+    return m;
+}
+
+// Host tables of one blocked grid; `dev` receives the device pointers after upload.
+struct HGrid {
+    int level = 0;              // AMR level, or -1 for a base multigrid grid
+    int dims[3] = {0, 0, 0};    // cells
+    int nb[3] = {0, 0, 0};      // blocks per axis
+    double h = 0;
+    int off = 0;                // first block in the caller's arrays (AMR levels)
+    std::vector<int> bijk;      // 3 per block
+    std::unordered_map<int64_t, int> index;
+    std::vector<int> nbr, parent, child, origin, freg, rsrc, gslot, slot_block;
+    std::vector<uint8_t> covered, octant;
+    int slot0 = 0, nslot = 0;
+    GridDev dev;
+    int find(int i, int j, int k) const {
+        auto it = index.find(key3(wrapi(i, nb[0]), wrapi(j, nb[1]), wrapi(k, nb[2])));
+        return it == index.end() ? -1 : it->second;
+    }
+    int n() const { return (int)(bijk.size() / 3); }
+};
+
+struct Buffers {  // precision-dependent multigrid arrays (element type T)
+    void *r = nullptr, *e = nullptr, *e2 = nullptr, *eta = nullptr, *inv = nullptr;
+};
+
+}  // namespace
+
+struct ohm_hier {
+    ohm_hier_desc d{};
+    cudaStream_t s = nullptr;
+    bool mixed = false;
+    int nlev = 0;
+    int64_t nblocks = 0;
+    std::vector<int32_t> lijk;
+    std::vector<HGrid> amr;       // AMR levels
+    std::vector<HGrid> mg;        // blocked base multigrid grids m = 1 .. (index m-1)
+    std::vector<std::array<int, 3>> small;  // lexicographic grids below the last blocked one
+    int nslot = 0, nreg = 0, nrsrc = 0;
+    std::vector<int> rsrc_tab;
+
+    // device memory (one pool)
+    void *pool = nullptr;
+    double *S = nullptr, *eta64 = nullptr, *Bscr = nullptr, *ghostB = nullptr, *ghostEta64 = nullptr;
+    double *reg = nullptr, *partials = nullptr, *dnorm = nullptr;
+    int *d_rsrc = nullptr, *d_err = nullptr;
+    void *ghostE = nullptr, *ghostEtaT = nullptr;
+    Buffers amrbuf;               // AMR levels, all blocks
+    std::vector<Buffers> mgbuf;   // blocked multigrid grids
+    Buffers smallbuf[MAX_SMALL];  // small grids (t stored in e2)
+    double *hnorm = nullptr;      // pinned host copy: 4 doubles + error word
+
+    bool eta_set = false;
+    double inv_dt = NAN;
+    bool has_S = false;
+    double last_dt = 0;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int build_tables(ohm_hier *H, std::string &err) {
+    const ohm_hier_desc &d = H->d;
+    const int nlev = d.nlevels;
+    H->amr.resize(nlev);
+    // levels and block ranges
+    int64_t pos = 0;
+    for (int l = 0; l < nlev; l++) {
+        HGrid &g = H->amr[l];
+        g.level = l;
+        for (int a = 0; a < 3; a++) {
+            g.dims[a] = d.base_cells[a] << l;
+            g.nb[a] = g.dims[a] / BS;
+        }
+        g.h = d.dx0 / (double)(1 << l);
+        g.off = (int)pos;
+        while (pos < H->nblocks && H->lijk[4 * pos] == l) {
+            int bi = H->lijk[4 * pos + 1], bj = H->lijk[4 * pos + 2], bk = H->lijk[4 * pos + 3];
+            if (bi < 0 || bj < 0 || bk < 0 || bi >= g.nb[0] || bj >= g.nb[1] || bk >= g.nb[2]) {
+                err = "block " + std::to_string(pos) + " outside its level";
+                return OHM_ERR_INVALID;
+            }
+            if (!g.index.emplace(key3(bi, bj, bk), g.n()).second) {
+                err = "block " + std::to_string(pos) + " duplicated";
+                return OHM_ERR_INVALID;
+            }
+            g.bijk.insert(g.bijk.end(), {bi, bj, bk});
+            pos++;
+        }
+        if (g.n() == 0) {
+            err = "level " + std::to_string(l) + " has no blocks";
+            return OHM_ERR_INVALID;
+        }
+    }
+    if (pos != H->nblocks) {
+        err = "block list not sorted by level or level out of range";
+        return OHM_ERR_INVALID;
+    }
+    if ((int64_t)H->amr[0].n() != (int64_t)H->amr[0].nb[0] * H->amr[0].nb[1] * H->amr[0].nb[2]) {
+        err = "level 0 does not tile the base grid";
+        return OHM_ERR_INVALID;
+    }
+    // octree completeness and proper nesting
+    for (int l = 1; l < nlev; l++) {
+        HGrid &g = H->amr[l], &p = H->amr[l - 1];
+        for (int b = 0; b < g.n(); b++) {
+            int bi = g.bijk[3 * b], bj = g.bijk[3 * b + 1], bk = g.bijk[3 * b + 2];
+            int pi = bi >> 1, pj = bj >> 1, pk = bk >> 1;
+            for (int o = 0; o < 8; o++)
+                if (g.find(2 * pi + (o & 1), 2 * pj + ((o >> 1) & 1), 2 * pk + (o >> 2)) < 0) {
+                    err = "level " + std::to_string(l) + ": incomplete octet";
+                    return OHM_ERR_INVALID;
+                }
+            for (int dk = -1; dk <= 1; dk++)
+                for (int dj = -1; dj <= 1; dj++)
+                    for (int di = -1; di <= 1; di++)
+                        if (p.find(pi + di, pj + dj, pk + dk) < 0) {
+                            err = "level " + std::to_string(l) + ": not properly nested";
+                            return OHM_ERR_INVALID;
+                        }
+        }
+    }
+    // per-level tables
+    for (int l = 0; l < nlev; l++) {
+        HGrid &g = H->amr[l];
+        const int n = g.n();
+        g.nbr.assign((size_t)n * 27, -1);
+        g.covered.assign(n, 0);
+        g.child.assign((size_t)n * 8, -1);
+        g.parent.assign(n, -1);
+        g.octant.assign(n, 0);
+        g.origin = g.bijk;
+        g.gslot.assign(n, -1);
+        g.freg.assign((size_t)n * 6, -1);
+        g.rsrc.assign((size_t)n * 6, -1);
+        for (int b = 0; b < n; b++) {
+            int bi = g.bijk[3 * b], bj = g.bijk[3 * b + 1], bk = g.bijk[3 * b + 2];
+            for (int dk = -1; dk <= 1; dk++)
+                for (int dj = -1; dj <= 1; dj++)
+                    for (int di = -1; di <= 1; di++)
+                        g.nbr[(size_t)b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + di + 1] = g.find(bi + di, bj + dj, bk + dk);
+            if (l + 1 < nlev) {
+                const HGrid &f = H->amr[l + 1];
+                for (int o = 0; o < 8; o++)
+                    g.child[(size_t)b * 8 + o] = f.find(2 * bi + (o & 1), 2 * bj + ((o >> 1) & 1), 2 * bk + (o >> 2));
+                g.covered[b] = g.child[(size_t)b * 8] >= 0;
+            }
+            if (l > 0) {
+                g.parent[b] = H->amr[l - 1].find(bi >> 1, bj >> 1, bk >> 1);
+                g.octant[b] = (uint8_t)((bi & 1) | ((bj & 1) << 1) | ((bk & 1) << 2));
+                bool absent = false;
+                for (int q = 0; q < 27; q++) {
+                    int di = q % 3 - 1, dj = (q / 3) % 3 - 1, dk = q / 9 - 1;
+                    if ((di != 0) + (dj != 0) + (dk != 0) == 3) continue;
+                    if (g.nbr[(size_t)b * 27 + q] < 0) absent = true;
+                }
+                if (absent) {
+                    g.gslot[b] = H->nslot++;
+                    g.slot_block.push_back(b);
+                }
+                for (int s = 0; s < 6; s++) {
+                    int a = s >> 1, hi = s & 1;
+                    int dd[3] = {0, 0, 0};
+                    dd[a] = hi ? 1 : -1;
+                    if (g.nbr[(size_t)b * 27 + (dd[2] + 1) * 9 + (dd[1] + 1) * 3 + dd[0] + 1] < 0) g.freg[(size_t)b * 6 + s] = H->nreg++;
+                }
+            }
+        }
+        g.nslot = (int)g.slot_block.size();
+        g.slot0 = H->nslot - g.nslot;
+    }
+    // reflux sources: leaf block faces next to a covered block take the four fine fluxes
+    for (int l = 0; l + 1 < nlev; l++) {
+        HGrid &g = H->amr[l];
+        const HGrid &f = H->amr[l + 1];
+        for (int b = 0; b < g.n(); b++) {
+            if (g.covered[b]) continue;
+            for (int s = 0; s < 6; s++) {
+                int a = s >> 1, hi = s & 1;
+                int dd[3] = {0, 0, 0};
+                dd[a] = hi ? 1 : -1;
+                int nb = g.nbr[(size_t)b * 27 + (dd[2] + 1) * 9 + (dd[1] + 1) * 3 + dd[0] + 1];
+                if (nb < 0 || !g.covered[nb]) continue;
+                int ax[2], q = 0;
+                for (int c = 0; c < 3; c++)
+                    if (c != a) ax[q++] = c;
+                int ent = H->nrsrc++;
+                g.rsrc[(size_t)b * 6 + s] = ent;
+                for (int vb = 0; vb < 2; vb++)
+                    for (int ub = 0; ub < 2; ub++) {
+                        int o = 0;
+                        o |= (hi ? 0 : 1) << a;
+                        o |= ub << ax[0];
+                        o |= vb << ax[1];
+                        int ch = g.child[(size_t)nb * 8 + o];
+                        int slot = ch >= 0 ? f.freg[(size_t)ch * 6 + 2 * a + (1 - hi)] : -1;
+                        if (slot < 0) {
+                            err = "internal: missing flux register at a coarse-fine face";
+                            return OHM_ERR_INVALID;
+                        }
+                        H->rsrc_tab.push_back(slot);
+                    }
+            }
+        }
+    }
+    // base multigrid grids: halve while every dimension is even and >= 4
+    int dims[3] = {d.base_cells[0], d.base_cells[1], d.base_cells[2]};
+    double h = d.dx0;
+    bool blocked = true;
+    while (dims[0] % 2 == 0 && dims[1] % 2 == 0 && dims[2] % 2 == 0 && dims[0] >= 4 && dims[1] >= 4 && dims[2] >= 4) {
+        for (int a = 0; a < 3; a++) dims[a] /= 2;
+        h *= 2.0;
+        if (blocked && dims[0] % BS == 0 && dims[1] % BS == 0 && dims[2] % BS == 0) {
+            HGrid g;
+            g.level = -1;
+            g.h = h;
+            for (int a = 0; a < 3; a++) {
+                g.dims[a] = dims[a];
+                g.nb[a] = dims[a] / BS;
+            }
+            std::vector<std::array<int, 3>> bl;
+            for (int k = 0; k < g.nb[2]; k++)
+                for (int j = 0; j < g.nb[1]; j++)
+                    for (int i = 0; i < g.nb[0]; i++) bl.push_back({i, j, k});
+            std::stable_sort(bl.begin(), bl.end(), [](const std::array<int, 3> &x, const std::array<int, 3> &y) {
+                return morton(x[0], x[1], x[2]) < morton(y[0], y[1], y[2]);
+            });
+            for (auto &q : bl) {
+                g.index.emplace(key3(q[0], q[1], q[2]), g.n());
+                g.bijk.insert(g.bijk.end(), {q[0], q[1], q[2]});
+            }
+            const int n = g.n();
+            g.nbr.assign((size_t)n * 27, -1);
+            g.origin = g.bijk;
+            g.parent.assign(n, -1);
+            g.octant.assign(n, 0);
+            for (int b = 0; b < n; b++) {
+                int bi = g.bijk[3 * b], bj = g.bijk[3 * b + 1], bk = g.bijk[3 * b + 2];
+                for (int q = 0; q < 27; q++)
+                    g.nbr[(size_t)b * 27 + q] = g.find(bi + q % 3 - 1, bj + (q / 3) % 3 - 1, bk + q / 9 - 1);
+            }
+            H->mg.push_back(std::move(g));
+        } else {
+            blocked = false;
+            if (H->small.size() >= (size_t)MAX_SMALL) {
+                err = "too many coarse grids";
+                return OHM_ERR_INVALID;
+            }
+            H->small.push_back({dims[0], dims[1], dims[2]});
+        }
+    }
+    if (H->small.empty()) {
+        err = "internal: no coarsest grid";
+        return OHM_ERR_INVALID;
+    }
+    if ((int64_t)H->small[0][0] * H->small[0][1] * H->small[0][2] > MAX_BOTTOM_CELLS) {
+        err = "base grid too large for the single-block coarsest solve (first non-blocked grid exceeds 16384 cells)";
+        return OHM_ERR_INVALID;
+    }
+    // parent / octant links from each blocked grid into the next blocked grid
+    auto link = [](HGrid &fine, const HGrid &coarse) {
+        for (int b = 0; b < fine.n(); b++) {
+            int bi = fine.bijk[3 * b], bj = fine.bijk[3 * b + 1], bk = fine.bijk[3 * b + 2];
+            fine.parent[b] = coarse.find(bi >> 1, bj >> 1, bk >> 1);
+            fine.octant[b] = (uint8_t)((bi & 1) | ((bj & 1) << 1) | ((bk & 1) << 2));
+        }
+    };
+    if (!H->mg.empty()) link(H->amr[0], H->mg[0]);
+    for (size_t m = 0; m + 1 < H->mg.size(); m++) link(H->mg[m], H->mg[m + 1]);
+    return OHM_OK;
+}
+
+template <typename V>
+void push_table(std::vector<char> &blob, std::vector<size_t> &offs, const std::vector<V> &v) {
+    size_t o = align256(blob.size());
+    blob.resize(o + v.size() * sizeof(V));
+    if (!v.empty()) memcpy(blob.data() + o, v.data(), v.size() * sizeof(V));
+    offs.push_back(o);
+}
+
+int allocate(ohm_hier *H, std::string &err) {
+    const size_t tsz = H->mixed ? sizeof(float) : sizeof(double);
+    const size_t n = (size_t)H->nblocks;
+    // tables
+    std::vector<char> blob;
+    std::vector<size_t> offs;
+    std::vector<HGrid *> grids;
+    for (auto &g : H->amr) grids.push_back(&g);
+    for (auto &g : H->mg) grids.push_back(&g);
+    for (HGrid *g : grids) {
+        push_table(blob, offs, g->nbr);
+        push_table(blob, offs, g->covered);
+        push_table(blob, offs, g->gslot);
+        push_table(blob, offs, g->parent);
+        push_table(blob, offs, g->octant);
+        push_table(blob, offs, g->child);
+        push_table(blob, offs, g->origin);
+        push_table(blob, offs, g->freg);
+        push_table(blob, offs, g->rsrc);
+        push_table(blob, offs, g->slot_block);
+    }
+    push_table(blob, offs, H->rsrc_tab);
+    // data
+    size_t total = align256(blob.size());
+    std::vector<std::pair<void **, size_t>> plan;
+    auto want = [&](void **p, size_t bytes) { plan.push_back({p, bytes}); };
+    want((void **)&H->S, n * 3 * B3 * 8);
+    want((void **)&H->eta64, n * B3 * 8);
+    want((void **)&H->Bscr, n * 3 * B3 * 8);
+    want((void **)&H->ghostB, (size_t)H->nslot * 3 * T3 * 8);
+    want((void **)&H->ghostEta64, (size_t)H->nslot * T3 * 8);
+    want((void **)&H->reg, (size_t)H->nreg * 128 * 8);
+    want((void **)&H->partials, n * 3 * 8);
+    want((void **)&H->dnorm, 64);
+    want(&H->ghostE, (size_t)H->nslot * 3 * T3 * tsz);
+    if (H->mixed) want(&H->ghostEtaT, (size_t)H->nslot * T3 * tsz);
+    want(&H->amrbuf.r, n * 3 * B3 * tsz);
+    want(&H->amrbuf.e, n * 3 * B3 * tsz);
+    want(&H->amrbuf.e2, n * 3 * B3 * tsz);
+    want(&H->amrbuf.inv, n * 3 * B3 * tsz);
+    if (H->mixed) want(&H->amrbuf.eta, n * B3 * tsz);
+    H->mgbuf.resize(H->mg.size());
+    for (size_t m = 0; m < H->mg.size(); m++) {
+        size_t nb = (size_t)H->mg[m].n();
+        want(&H->mgbuf[m].r, nb * 3 * B3 * tsz);
+        want(&H->mgbuf[m].e, nb * 3 * B3 * tsz);
+        want(&H->mgbuf[m].e2, nb * 3 * B3 * tsz);
+        want(&H->mgbuf[m].inv, nb * 3 * B3 * tsz);
+        want(&H->mgbuf[m].eta, nb * B3 * tsz);
+    }
+    for (size_t q = 0; q < H->small.size(); q++) {
+        size_t nc = (size_t)H->small[q][0] * H->small[q][1] * H->small[q][2];
+        want(&H->smallbuf[q].r, nc * 3 * tsz);
+        want(&H->smallbuf[q].e, nc * 3 * tsz);
+        want(&H->smallbuf[q].e2, nc * 3 * tsz);
+        want(&H->smallbuf[q].inv, nc * 3 * tsz);
+        want(&H->smallbuf[q].eta, nc * tsz);
+    }
+    std::vector<size_t> doff;
+    for (auto &p : plan) {
+        doff.push_back(total);
+        total += align256(p.second);
+    }
+    if (cudaMalloc(&H->pool, total) != cudaSuccess) {
+        cudaGetLastError();
+        err = "device allocation of " + std::to_string(total) + " bytes failed";
+        return OHM_ERR_OOM;
+    }
+    char *base = (char *)H->pool;
+    for (size_t i = 0; i < plan.size(); i++) *plan[i].first = plan[i].second ? base + doff[i] : nullptr;
+    H->d_err = (int *)(H->dnorm + 4);
+    if (!H->mixed) {
+        H->ghostEtaT = H->ghostEta64;
+        H->amrbuf.eta = H->eta64;
+    }
+    if (cudaMemcpy(base, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = "table upload failed";
+        return OHM_ERR_CUDA;
+    }
+    if (cudaMallocHost((void **)&H->hnorm, 64) != cudaSuccess) {
+        err = "pinned allocation failed";
+        return OHM_ERR_OOM;
+    }
+    size_t k = 0;
+    for (HGrid *g : grids) {
+        GridDev &dv = g->dev;
+        dv.nblk = g->n();
+        dv.level_shift = g->level < 0 ? 0 : g->level;
+        dv.h = g->h;
+        for (int a = 0; a < 3; a++) dv.dims[a] = g->dims[a];
+        auto ptr = [&](size_t o, bool nonempty) -> const void * { return nonempty ? base + o : nullptr; };
+        dv.nbr = (const int *)ptr(offs[k + 0], !g->nbr.empty());
+        dv.covered = (const uint8_t *)ptr(offs[k + 1], !g->covered.empty());
+        dv.gslot = (const int *)ptr(offs[k + 2], !g->gslot.empty() && g->level > 0);
+        dv.parent = (const int *)ptr(offs[k + 3], !g->parent.empty());
+        dv.octant = (const uint8_t *)ptr(offs[k + 4], !g->octant.empty());
+        dv.child = (const int *)ptr(offs[k + 5], !g->child.empty());
+        dv.origin = (const int *)ptr(offs[k + 6], !g->origin.empty());
+        dv.freg = (const int *)ptr(offs[k + 7], !g->freg.empty() && g->level > 0);
+        bool anyr = std::any_of(g->rsrc.begin(), g->rsrc.end(), [](int v) { return v >= 0; });
+        dv.rsrc = (const int *)ptr(offs[k + 8], anyr);
+        dv.slot_block = (const int *)ptr(offs[k + 9], !g->slot_block.empty());
+        dv.nslot = g->nslot;
+        dv.slot0 = g->slot0;
+        k += 10;
+    }
+    H->d_rsrc = (int *)(H->rsrc_tab.empty() ? nullptr : base + offs[k]);
+    return OHM_OK;
+}
+
+#define CK(x)                                 \
+    do {                                      \
+        cudaError_t e_ = (x);                 \
+        if (e_ != cudaSuccess) return OHM_ERR_CUDA; \
+    } while (0)
+
+template <typename T>
+T *amr_ptr(void *p, const HGrid &g, int ncomp) {
+    return (T *)p + (size_t)g.off * ncomp * B3;
+}
+
+template <typename T>
+SmallDev<T> small_dev(ohm_hier *H) {
+    SmallDev<T> sm;
+    sm.n = (int)H->small.size();
+    double h = H->d.dx0 * std::pow(2.0, (double)(H->mg.size() + 1));
+    for (int q = 0; q < sm.n; q++) {
+        for (int a = 0; a < 3; a++) sm.dims[q][a] = H->small[q][a];
+        sm.h[q] = h;
+        h *= 2.0;
+        sm.e[q] = (T *)H->smallbuf[q].e;
+        sm.r[q] = (T *)H->smallbuf[q].r;
+        sm.t[q] = (T *)H->smallbuf[q].e2;
+        sm.eta[q] = (T *)H->smallbuf[q].eta;
+        sm.inv[q] = (T *)H->smallbuf[q].inv;
+    }
+    return sm;
+}
+
+// eta: level ghosts, the multigrid copies and the eta chain below level 0
+template <typename T>
+int eta_derive(ohm_hier *H) {
+    cudaStream_t s = H->s;
+    for (int l = 1; l < H->nlev; l++)
+        CK((launch_ghost_fill<double, double>(H->amr[l].dev, H->amr[l - 1].dev, amr_ptr<double>(H->eta64, H->amr[l - 1], 1),
+                                              1, H->ghostEta64, H->d_err, s)));
+    if (H->mixed) {
+        CK((launch_convert<double, T>(H->eta64, (T *)H->amrbuf.eta, (size_t)H->nblocks * B3, s)));
+        CK((launch_convert<double, T>(H->ghostEta64, (T *)H->ghostEtaT, (size_t)H->nslot * T3, s)));
+    }
+    const HGrid *f = &H->amr[0];
+    const T *fe = (const T *)H->amrbuf.eta;
+    for (size_t m = 0; m < H->mg.size(); m++) {
+        CK(launch_restrict<T>(f->dev, fe, 1, (T *)H->mgbuf[m].eta, nullptr, nullptr, s));
+        f = &H->mg[m];
+        fe = (const T *)H->mgbuf[m].eta;
+    }
+    CK(launch_restrict<T>(f->dev, fe, 1, nullptr, (T *)H->smallbuf[0].eta, H->small[0].data(), s));
+    SmallDev<T> sm = small_dev<T>(H);
+    CK(launch_small_setup<T>(sm, 0.0, true, s));
+    H->inv_dt = NAN;
+    return OHM_OK;
+}
+
+// inverse diagonals of every multigrid grid for lambda*dt
+template <typename T>
+int prepare_dt(ohm_hier *H, double dt) {
+    if (H->inv_dt == dt) return OHM_OK;
+    const double lamdt = H->d.lambda * dt;
+    cudaStream_t s = H->s;
+    for (auto &g : H->amr)
+        CK(launch_invdiag<T>(g.dev, amr_ptr<T>(H->amrbuf.eta, g, 1), (const T *)H->ghostEtaT, lamdt,
+                             amr_ptr<T>(H->amrbuf.inv, g, 3), s));
+    for (size_t m = 0; m < H->mg.size(); m++)
+        CK(launch_invdiag<T>(H->mg[m].dev, (const T *)H->mgbuf[m].eta, nullptr, lamdt, (T *)H->mgbuf[m].inv, s));
+    SmallDev<T> sm = small_dev<T>(H);
+    CK(launch_small_setup<T>(sm, lamdt, false, s));
+    H->inv_dt = dt;
+    return OHM_OK;
+}
+
+struct GridRef {
+    const HGrid *g;
+    void *e, *e2, *r, *eta, *inv;
+    const void *Ge, *Geta;
+};
+
+template <typename T>
+GridRef amr_ref(ohm_hier *H, int l, bool with_ghost) {
+    const HGrid &g = H->amr[l];
+    return GridRef{&g,
+                   amr_ptr<T>(H->amrbuf.e, g, 3),
+                   amr_ptr<T>(H->amrbuf.e2, g, 3),
+                   amr_ptr<T>(H->amrbuf.r, g, 3),
+                   amr_ptr<T>(H->amrbuf.eta, g, 1),
+                   amr_ptr<T>(H->amrbuf.inv, g, 3),
+                   with_ghost ? H->ghostE : nullptr,
+                   H->ghostEtaT};
+}
+
+template <typename T>
+GridRef base_ref(ohm_hier *H, int m) {  // m = 0: AMR level 0
+    if (m == 0) return amr_ref<T>(H, 0, false);
+    Buffers &b = H->mgbuf[m - 1];
+    return GridRef{&H->mg[m - 1], b.e, b.e2, b.r, b.eta, b.inv, nullptr, nullptr};
+}
+
+template <typename T>
+int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
+    for (int i = 0; i < n; i++) {
+        CK(launch_smooth<T>(G.g->dev, (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
+                            (const T *)G.Ge, (const T *)G.Geta, lamdt, 0, H->s));
+        CK(launch_smooth<T>(G.g->dev, (const T *)G.e2, (T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
+                            (const T *)G.Ge, (const T *)G.Geta, lamdt, 1, H->s));
+    }
+    return OHM_OK;
+}
+
+// V-cycle on base grid m (e_m zeroed by the caller); m = 0 is AMR level 0
+template <typename T>
+int base_vcycle(ohm_hier *H, int m, double lamdt) {
+    const ohm_hier_desc &d = H->d;
+    GridRef G = base_ref<T>(H, m);
+    int st;
+    if ((st = sweeps<T>(H, G, d.nu_pre, lamdt))) return st;
+    const bool next_blocked = m < (int)H->mg.size();
+    if (next_blocked) {
+        GridRef C = base_ref<T>(H, m + 1);
+        CK(launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
+                                    nullptr, (T *)C.r, nullptr, nullptr, H->s));
+        CK(cudaMemsetAsync(C.e, 0, (size_t)C.g->n() * 3 * B3 * sizeof(T), H->s));
+        if ((st = base_vcycle<T>(H, m + 1, lamdt))) return st;
+        CK(launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+    } else {
+        CK(launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
+                                    nullptr, nullptr, (T *)H->smallbuf[0].r, H->small[0].data(), H->s));
+        SmallDev<T> sm = small_dev<T>(H);
+        CK(launch_bottom<T>(sm, lamdt, d.nu_pre, d.nu_post, d.n_coarse, H->s));
+        CK(launch_prolong_add<T>(G.g->dev, nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
+                                 H->d_err, H->s));
+    }
+    return sweeps<T>(H, G, d.nu_post, lamdt);
+}
+
+// One correction-scheme V-cycle over the AMR levels and the base grid.  r on leaf blocks
+// holds the composite residual; the correction is left in e (all levels).
+template <typename T>
+int vcycle(ohm_hier *H, double lamdt) {
+    const ohm_hier_desc &d = H->d;
+    int st;
+    for (int l = H->nlev - 1; l >= 1; l--) {
+        GridRef G = amr_ref<T>(H, l, true);
+        const HGrid &g = *G.g;
+        CK(cudaMemsetAsync(G.e, 0, (size_t)g.n() * 3 * B3 * sizeof(T), H->s));
+        if (g.nslot) CK(cudaMemsetAsync((T *)H->ghostE + (size_t)g.slot0 * 3 * T3, 0, (size_t)g.nslot * 3 * T3 * sizeof(T), H->s));
+        if ((st = sweeps<T>(H, G, d.nu_pre, lamdt))) return st;
+        GridRef C = amr_ref<T>(H, l - 1, true);
+        CK(launch_resid_restrict<T>(g.dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.Ge,
+                                    (const T *)G.Geta, lamdt, nullptr, (T *)C.r, nullptr, nullptr, H->s));
+    }
+    {
+        GridRef G0 = amr_ref<T>(H, 0, false);
+        CK(cudaMemsetAsync(G0.e, 0, (size_t)G0.g->n() * 3 * B3 * sizeof(T), H->s));
+    }
+    if ((st = base_vcycle<T>(H, 0, lamdt))) return st;
+    for (int l = 1; l < H->nlev; l++) {
+        GridRef G = amr_ref<T>(H, l, true);
+        GridRef C = amr_ref<T>(H, l - 1, true);
+        CK(launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+        CK((launch_ghost_fill<T, T>(G.g->dev, C.g->dev, (const T *)C.e, 3, (T *)H->ghostE, H->d_err, H->s)));
+        if ((st = sweeps<T>(H, G, d.nu_post, lamdt))) return st;
+    }
+    return OHM_OK;
+}
+
+int sync_down(ohm_hier *H, double *B) {
+    for (int l = H->nlev - 2; l >= 0; l--)
+        CK(launch_sync_down(H->amr[l].dev, amr_ptr<double>(B, H->amr[l], 3), amr_ptr<double>(B, H->amr[l + 1], 3), H->s));
+    return OHM_OK;
+}
+
+int fill_ghosts_B(ohm_hier *H, const double *B) {
+    for (int l = 1; l < H->nlev; l++)
+        CK((launch_ghost_fill<double, double>(H->amr[l].dev, H->amr[l - 1].dev,
+                                              amr_ptr<double>((void *)B, H->amr[l - 1], 3), 3, H->ghostB, H->d_err, H->s)));
+    return OHM_OK;
+}
+
+// out = a X + c divF(X) + d Y on leaf blocks of every level (finest first, so refluxed
+// fine fluxes are in the registers before the coarser level reads them).
+template <typename TO>
+int composite(ohm_hier *H, const double *X, const double *Y, double a, double c, double dcoef, TO *out, bool norms) {
+    for (int l = H->nlev - 1; l >= 0; l--) {
+        const HGrid &g = H->amr[l];
+        double vol = g.h * g.h * g.h;
+        CK(launch_composite<TO>(g.dev, amr_ptr<double>((void *)X, g, 3), Y ? amr_ptr<double>((void *)Y, g, 3) : nullptr,
+                                amr_ptr<double>(H->eta64, g, 1), H->ghostB, H->ghostEta64, a, c, dcoef,
+                                out + (size_t)g.off * 3 * B3, H->reg, H->d_rsrc, norms ? H->partials + (size_t)g.off * 3 : nullptr,
+                                vol, H->s));
+    }
+    if (norms) CK(launch_norm_reduce(H->partials, (int)H->nblocks, H->dnorm, H->s));
+    return OHM_OK;
+}
+
+int read_norms(ohm_hier *H, double out[4], int *err_flag) {
+    CK(cudaMemcpyAsync(H->hnorm, H->dnorm, 40, cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    double sr = H->hnorm[0], ss = H->hnorm[1];
+    out[0] = ss > 0 ? std::sqrt(sr / ss) : std::sqrt(sr);
+    out[1] = H->hnorm[2];
+    out[2] = std::sqrt(sr);
+    out[3] = std::sqrt(ss);
+    int e;
+    memcpy(&e, &H->hnorm[4], sizeof(int));
+    *err_flag = e;
+    return OHM_OK;
+}
+
+template <typename T>
+int update_all(ohm_hier *H, double *B) {
+    for (auto &g : H->amr) CK(launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>(H->amrbuf.e, g, 3), H->s));
+    return OHM_OK;
+}
+
+template <typename T>
+int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *stats) {
+    const double lam = H->d.lambda, lamdt = lam * dt;
+    int st;
+    if ((st = prepare_dt<T>(H, dt))) return st;
+    CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->s));
+    if ((st = sync_down(H, B))) return st;
+    if ((st = fill_ghosts_B(H, B))) return st;
+    if ((st = composite<double>(H, B, nullptr, 1.0, -(1.0 - lam) * dt, 0.0, H->S, false))) return st;
+    H->has_S = true;
+    H->last_dt = dt;
+    int it = 0;
+    double nr[4] = {0, 0, 0, 0}, first = 0;
+    int result = OHM_OK;
+    for (;;) {
+        if ((st = composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, (T *)H->amrbuf.r, true))) return st;
+        int ef = 0;
+        if ((st = read_norms(H, nr, &ef))) return st;
+        if (ef) return OHM_ERR_INVALID;
+        if (it == 0) first = nr[0];
+        if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) {
+            result = OHM_ERR_NONFINITE;
+            break;
+        }
+        if (tol >= 0 && nr[0] <= tol) break;
+        if (it >= H->d.max_outer) {
+            result = tol >= 0 ? OHM_ERR_NOT_CONVERGED : OHM_OK;
+            break;
+        }
+        if ((st = vcycle<T>(H, lamdt))) return st;
+        if ((st = update_all<T>(H, B))) return st;
+        if ((st = sync_down(H, B))) return st;
+        if ((st = fill_ghosts_B(H, B))) return st;
+        it++;
+    }
+    if (stats) {
+        stats->cycles = it;
+        stats->converged = (result == OHM_OK && tol >= 0) ? 1 : 0;
+        stats->rel_l2_initial = first;
+        stats->rel_l2 = nr[0];
+        stats->max_abs = nr[1];
+    }
+    return result;
+}
+
+bool valid_desc(const ohm_hier_desc *d, std::string &err) {
+    if (!d) { err = "NULL descriptor"; return false; }
+    for (int a = 0; a < 3; a++)
+        if (d->base_cells[a] <= 0 || d->base_cells[a] % BS) { err = "base cells must be positive multiples of 8"; return false; }
+    if (!(d->dx0 > 0) || !std::isfinite(d->dx0)) { err = "dx0 must be positive"; return false; }
+    if (d->nlevels < 1 || d->nlevels > MAX_LEVELS) { err = "nlevels out of range"; return false; }
+    if (d->nblocks <= 0 || !d->block_lijk) { err = "empty block list"; return false; }
+    if (!(d->lambda > 0 && d->lambda <= 1)) { err = "lambda must be in (0, 1]"; return false; }
+    if (d->precision != OHM_FP64 && d->precision != OHM_MIXED) { err = "unknown precision"; return false; }
+    if (d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1) { err = "bad cycle counts"; return false; }
+    for (int a = 0; a < 3; a++)
+        if (((int64_t)d->base_cells[a] << (d->nlevels - 1)) >= (1 << 20)) { err = "level too fine"; return false; }
+    return true;
+}
+
+thread_local std::string g_last_error;
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char *ohm_status_string(int status) {
+    switch (status) {
+        case OHM_OK: return "ok";
+        case OHM_ERR_INVALID: return g_last_error.empty() ? "invalid argument" : g_last_error.c_str();
+        case OHM_ERR_NOT_CONVERGED: return "not converged within max_outer cycles";
+        case OHM_ERR_NONFINITE: return "residual became non-finite";
+        case OHM_ERR_OOM: return "device allocation failed";
+        case OHM_ERR_CUDA: return "CUDA error";
+        default: return "unknown status";
+    }
+}
+
+int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
+    if (!out) return OHM_ERR_INVALID;
+    *out = nullptr;
+    std::string err;
+    if (!valid_desc(d, err)) {
+        g_last_error = err;
+        return OHM_ERR_INVALID;
+    }
+    ohm_hier *H = new ohm_hier();
+    H->d = *d;
+    H->d.block_lijk = nullptr;
+    H->s = (cudaStream_t)d->stream;
+    H->mixed = d->precision == OHM_MIXED;
+    H->nlev = d->nlevels;
+    H->nblocks = d->nblocks;
+    H->lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);
+    int st = build_tables(H, err);
+    if (st == OHM_OK) st = allocate(H, err);
+    if (st != OHM_OK) {
+        g_last_error = err;
+        ohm_destroy(H);
+        return st;
+    }
+    *out = H;
+    return OHM_OK;
+}
+
+void ohm_destroy(ohm_hier *h) {
+    if (!h) return;
+    if (h->pool) cudaFree(h->pool);
+    if (h->hnorm) cudaFreeHost(h->hnorm);
+    delete h;
+}
+
+int ohm_set_eta(ohm_hier *h, const double *eta_dev) {
+    if (!h || !eta_dev) return OHM_ERR_INVALID;
+    CK(cudaMemcpyAsync(h->eta64, eta_dev, (size_t)h->nblocks * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    int st = h->mixed ? eta_derive<float>(h) : eta_derive<double>(h);
+    if (st) return st;
+    h->eta_set = true;
+    return OHM_OK;
+}
+
+int ohm_cn_step(ohm_hier *h, double *B_dev, const double *eta_dev, double dt, double tol, ohm_step_stats *stats) {
+    if (!h || !B_dev || !(dt > 0) || !std::isfinite(dt)) return OHM_ERR_INVALID;
+    if (eta_dev) {
+        int st = ohm_set_eta(h, eta_dev);
+        if (st) return st;
+    }
+    if (!h->eta_set) return OHM_ERR_INVALID;
+    return h->mixed ? cn_step_impl<float>(h, B_dev, dt, tol, stats) : cn_step_impl<double>(h, B_dev, dt, tol, stats);
+}
+
+int ohm_residual_norm(ohm_hier *h, const double *B_dev, double *rel_l2, double *max_abs) {
+    if (!h || !B_dev || !h->has_S || !h->eta_set) return OHM_ERR_INVALID;
+    CK(cudaMemcpyAsync(h->Bscr, B_dev, (size_t)h->nblocks * 3 * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    int st;
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    if ((st = sync_down(h, h->Bscr))) return st;
+    if ((st = fill_ghosts_B(h, h->Bscr))) return st;
+    // the residual itself lands in the multigrid right-hand side buffer (not needed further)
+    int st2 = h->mixed ? composite<float>(h, h->Bscr, h->S, -1.0, -h->d.lambda * h->last_dt, 1.0, (float *)h->amrbuf.r, true)
+                       : composite<double>(h, h->Bscr, h->S, -1.0, -h->d.lambda * h->last_dt, 1.0, (double *)h->amrbuf.r, true);
+    if (st2) return st2;
+    double nr[4];
+    int ef = 0;
+    if ((st = read_norms(h, nr, &ef))) return st;
+    if (rel_l2) *rel_l2 = nr[0];
+    if (max_abs) *max_abs = nr[1];
+    return ef ? OHM_ERR_INVALID : OHM_OK;
+}
+
+int ohm_op_sync_down(ohm_hier *h, double *B_dev) {
+    if (!h || !B_dev) return OHM_ERR_INVALID;
+    return sync_down(h, B_dev);
+}
+
+static int op_composite(ohm_hier *h, const double *X, const double *Y, double a, double c, double d, double *out,
+                        double *norms) {
+    if (!h->eta_set) return OHM_ERR_INVALID;
+    CK(cudaMemcpyAsync(h->Bscr, X, (size_t)h->nblocks * 3 * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    int st;
+    if ((st = sync_down(h, h->Bscr))) return st;
+    if ((st = fill_ghosts_B(h, h->Bscr))) return st;
+    if ((st = composite<double>(h, h->Bscr, Y, a, c, d, out, norms != nullptr))) return st;
+    for (auto &g : h->amr) CK(launch_zero_covered(g.dev, out + (size_t)g.off * 3 * B3, h->s));
+    double nr[4];
+    int ef = 0;
+    if ((st = read_norms(h, nr, &ef))) return st;
+    if (norms) memcpy(norms, nr, sizeof(nr));
+    return ef ? OHM_ERR_INVALID : OHM_OK;
+}
+
+int ohm_op_div_flux(ohm_hier *h, const double *B_dev, double *out_dev) {
+    if (!h || !B_dev || !out_dev) return OHM_ERR_INVALID;
+    return op_composite(h, B_dev, nullptr, 0.0, 1.0, 0.0, out_dev, nullptr);
+}
+
+int ohm_op_source(ohm_hier *h, const double *b_dev, double dt, double *S_dev) {
+    if (!h || !b_dev || !S_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    return op_composite(h, b_dev, nullptr, 1.0, -(1.0 - h->d.lambda) * dt, 0.0, S_dev, nullptr);
+}
+
+int ohm_op_residual(ohm_hier *h, const double *B_dev, const double *S_dev, double dt, double *R_dev, double *norms) {
+    if (!h || !B_dev || !S_dev || !R_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    double tmp[4];
+    return op_composite(h, B_dev, S_dev, -1.0, -h->d.lambda * dt, 1.0, R_dev, norms ? norms : tmp);
+}
+
+int ohm_op_vcycle(ohm_hier *h, const double *R_dev, double dt, double *e_dev) {
+    if (!h || !R_dev || !e_dev || !(dt > 0) || h->mixed || !h->eta_set) return OHM_ERR_INVALID;
+    int st;
+    if ((st = prepare_dt<double>(h, dt))) return st;
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(cudaMemcpyAsync(h->amrbuf.r, R_dev, (size_t)h->nblocks * 3 * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    if ((st = vcycle<double>(h, h->d.lambda * dt))) return st;
+    CK(cudaMemcpyAsync(e_dev, h->amrbuf.e, (size_t)h->nblocks * 3 * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    for (auto &g : h->amr) CK(launch_zero_covered(g.dev, e_dev + (size_t)g.off * 3 * B3, h->s));
+    double nr[4];
+    int ef = 0;
+    if ((st = read_norms(h, nr, &ef))) return st;
+    return ef ? OHM_ERR_INVALID : OHM_OK;
+}
+
+int ohm_mg_grid_info(ohm_hier *h, int m, int32_t dims[3], int64_t *nblocks, int32_t *ijk) {
+    if (!h || m < 0) return OHM_ERR_INVALID;
+    const int nmg = 1 + (int)h->mg.size() + (int)h->small.size();
+    if (m >= nmg) return OHM_ERR_INVALID;
+    if (m <= (int)h->mg.size()) {
+        const HGrid &g = m == 0 ? h->amr[0] : h->mg[m - 1];
+        if (dims) for (int a = 0; a < 3; a++) dims[a] = g.dims[a];
+        if (nblocks) *nblocks = g.n();
+        if (ijk) memcpy(ijk, g.bijk.data(), g.bijk.size() * sizeof(int32_t));
+    } else {
+        const auto &q = h->small[m - 1 - h->mg.size()];
+        if (dims) for (int a = 0; a < 3; a++) dims[a] = q[a];
+        if (nblocks) *nblocks = 0;
+    }
+    return OHM_OK;
+}
+
+// Single-grid steps: copy the caller's arrays into grid m's buffers, run one kernel, copy
+// back.  They overwrite that grid's eta, so ohm_set_eta is required again before a step.
+static int grid_setup(ohm_hier *h, int m, const double *eta_dev, double dt, GridRef &G) {
+    if (!h || h->mixed || m < 0 || m > (int)h->mg.size() || !eta_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    if (m == 0 && h->nlev > 1) return OHM_ERR_INVALID;
+    G = base_ref<double>(h, m);
+    const size_t nb = (size_t)G.g->n();
+    CK(cudaMemcpyAsync(G.eta, eta_dev, nb * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    CK(launch_invdiag<double>(G.g->dev, (const double *)G.eta, nullptr, h->d.lambda * dt, (double *)G.inv, h->s));
+    h->eta_set = false;
+    h->inv_dt = NAN;
+    return OHM_OK;
+}
+
+int ohm_op_grid_smooth(ohm_hier *h, int m, double *e_dev, const double *r_dev, const double *eta_dev, double dt, int colour) {
+    if (!e_dev || !r_dev || (colour != 0 && colour != 1)) return OHM_ERR_INVALID;
+    GridRef G;
+    int st;
+    if ((st = grid_setup(h, m, eta_dev, dt, G))) return st;
+    const size_t bytes = (size_t)G.g->n() * 3 * B3 * sizeof(double);
+    CK(cudaMemcpyAsync(G.e, e_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(G.r, r_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(launch_smooth<double>(G.g->dev, (const double *)G.e, (double *)G.e2, (const double *)G.r, (const double *)G.eta,
+                             (const double *)G.inv, nullptr, nullptr, h->d.lambda * dt, colour, h->s));
+    CK(cudaMemcpyAsync(e_dev, G.e2, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+int ohm_op_grid_residual(ohm_hier *h, int m, const double *e_dev, const double *r_dev, const double *eta_dev, double dt,
+                         double *t_dev) {
+    if (!e_dev || !r_dev || !t_dev) return OHM_ERR_INVALID;
+    GridRef G;
+    int st;
+    if ((st = grid_setup(h, m, eta_dev, dt, G))) return st;
+    const size_t bytes = (size_t)G.g->n() * 3 * B3 * sizeof(double);
+    CK(cudaMemcpyAsync(G.e, e_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(G.r, r_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(launch_resid_restrict<double>(G.g->dev, (const double *)G.e, (const double *)G.r, (const double *)G.eta, nullptr,
+                                     nullptr, h->d.lambda * dt, t_dev, nullptr, nullptr, nullptr, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+int ohm_op_grid_restrict(ohm_hier *h, int m, const double *fine_dev, double *coarse_dev, int ncomp) {
+    if (!h || h->mixed || !fine_dev || !coarse_dev || (ncomp != 1 && ncomp != 3)) return OHM_ERR_INVALID;
+    if (m < 0 || m >= (int)h->mg.size() || (m == 0 && h->nlev > 1)) return OHM_ERR_INVALID;
+    const HGrid &g = m == 0 ? h->amr[0] : h->mg[m - 1];
+    CK(launch_restrict<double>(g.dev, fine_dev, ncomp, coarse_dev, nullptr, nullptr, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double *fine_dev) {
+    if (!h || h->mixed || !fine_dev || !coarse_dev) return OHM_ERR_INVALID;
+    if (m < 0 || m >= (int)h->mg.size() || (m == 0 && h->nlev > 1)) return OHM_ERR_INVALID;
+    const HGrid &g = m == 0 ? h->amr[0] : h->mg[m - 1];
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(launch_prolong_add<double>(g.dev, &h->mg[m].dev, coarse_dev, nullptr, nullptr, fine_dev, h->d_err, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// ohm_internal.h -- device-side tables and kernel launchers shared by the host orchestration
+// (ohm_host.cpp) and the kernels (ohm_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ohm {
+
+constexpr int BS = 8;      // cells per block edge
+constexpr int B3 = 512;    // cells per block
+constexpr int TS = 10;     // staged tile edge (block + 1-cell halo)
+constexpr int T3 = 1000;   // staged tile cells
+
+// Device tables of one blocked grid (an AMR level or a base multigrid grid).  Block indices
+// inside a grid are local (0..nblk-1); field pointers handed to kernels are offset to the
+// grid's first block.
+struct GridDev {
+    int nblk = 0;
+    int level_shift = 0;            // AMR level (0 for base multigrid grids)
+    double h = 0;                   // cell width
+    int dims[3] = {0, 0, 0};        // cells per axis of the whole grid domain
+    const int *nbr = nullptr;       // [nblk][27] same-grid neighbour or -1 (absent)
+    const uint8_t *covered = nullptr;  // [nblk] 1 if refined by the next AMR level
+    const int *gslot = nullptr;     // [nblk] ghost slot or -1 (AMR levels >= 1)
+    const int *parent = nullptr;    // [nblk] index in the coarser grid (or -1)
+    const uint8_t *octant = nullptr;// [nblk] (bi&1) | (bj&1)<<1 | (bk&1)<<2
+    const int *child = nullptr;     // [nblk][8] index in the finer AMR level or -1
+    const int *origin = nullptr;    // [nblk][3] block coordinates (bi, bj, bk)
+    const int *freg = nullptr;      // [nblk][6] flux-register slot for faces with no neighbour
+    const int *rsrc = nullptr;      // [nblk][6] index into the reflux source table or -1
+    const int *slot_block = nullptr;// [nslot] block owning each ghost slot
+    int nslot = 0;
+    int slot0 = 0;                  // first ghost slot of this grid in the global slot array
+};
+
+// Lexicographic coarse grids below the last blocked grid (solved in one thread block).
+constexpr int MAX_SMALL = 12;
+template <typename T>
+struct SmallDev {
+    int n = 0;                      // number of small grids
+    int dims[MAX_SMALL][3];
+    double h[MAX_SMALL];
+    T *e[MAX_SMALL], *r[MAX_SMALL], *t[MAX_SMALL], *eta[MAX_SMALL], *inv[MAX_SMALL];
+};
+
+// ------------------------------------------------------------------ kernel launchers
+// Every launcher enqueues on `s` and returns cudaGetLastError().
+// Composite operator on AMR level g (float64): out = a X + c divF(X) + d Y on leaf blocks,
+// reading ghosts from Gx (level ghost slots) and eta ghosts from Geta; writes face fluxes to
+// registers for faces without a same-level neighbour and reads refluxed fluxes from the
+// finer level for faces next to covered blocks; optional per-block norm partials.
+template <typename TO>
+cudaError_t launch_composite(const GridDev &g, const double *X, const double *Y, const double *eta,
+                             const double *Gx, const double *Geta, double a, double c, double d,
+                             TO *out, double *reg, const int *rsrc_tab, double *partials,
+                             double vol, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta,
+                          const T *inv, const T *Ge, const T *Geta, double lamdt, int colour,
+                          cudaStream_t s);
+
+// t = r - (e + lamdt divF(e)); restricted (mean of 8) into the coarser grid: blocked
+// (coarse != nullptr, by parent/octant) or lexicographic (lex != nullptr, dims ldims).
+template <typename T>
+cudaError_t launch_resid_restrict(const GridDev &g, const T *e, const T *r, const T *eta,
+                                  const T *Ge, const T *Geta, double lamdt, T *t_out,
+                                  T *coarse, T *lex, const int *ldims, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_prolong_add(const GridDev &g, const GridDev *gc, const T *coarse,
+                               const T *lex, const int *ldims, T *fine, int *err, cudaStream_t s);
+
+// plain restriction of ncomp components (eta chain): blocked fine -> blocked or lex coarse
+template <typename T>
+cudaError_t launch_restrict(const GridDev &g, const T *fine, int ncomp, T *coarse, T *lex,
+                            const int *ldims, cudaStream_t s);
+
+template <typename TS, typename TD>
+cudaError_t launch_ghost_fill(const GridDev &g, const GridDev &gc, const TS *coarse, int ncomp,
+                              TD *ghost, int *err, cudaStream_t s);
+
+cudaError_t launch_sync_down(const GridDev &gc, double *Bc, const double *Bf, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_update(const GridDev &g, double *B, const T *e, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_invdiag(const GridDev &g, const T *eta, const T *Geta, double lamdt, T *inv,
+                           cudaStream_t s);
+
+cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *out, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post,
+                          int n_coarse, cudaStream_t s);
+
+// lexicographic restriction between small grids and small-grid inverse diagonals
+template <typename T>
+cudaError_t launch_small_setup(const SmallDev<T> &sm, double lamdt, bool eta_chain, cudaStream_t s);
+
+template <typename TS, typename TD>
+cudaError_t launch_convert(const TS *src, TD *dst, size_t n, cudaStream_t s);
+
+cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s);
+
+}  // namespace ohm

@@ -1,0 +1,863 @@
+// ohm_kernels.cu -- sm_103a kernels of the implicit ohmic-dissipation step
+// (T. Matsumoto 2011, Sec. 2).  One thread block works on one 8^3-cell block: it stages the
+// block and a one-cell halo (faces and edges; corners are never read by the stencil) in
+// shared memory, from the same-grid neighbour blocks or, where the grid has no neighbour,
+// from the block's coarse-fine ghost slot.
+//
+// Face flux (Eqs. 4-6, 9-11), kept scaled as Phi = 2 h F:
+//   Phi_a^b = (eta_lo + eta_hi) * (T/4 - N),  N = B_b(hi) - B_b(lo)                 (Eq. 9)
+//   T = B_a(lo+e_b) + B_a(hi+e_b) - B_a(lo-e_b) - B_a(hi-e_b)                         (Eq. 10)
+// and the flux divergence (Eq. 8) is sum_a (Phi_a(+) - Phi_a(-)) / (2 h^2).
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "ohm_internal.h"
+
+namespace ohm {
+
+__device__ __forceinline__ int tix(int i, int j, int k) { return (k * TS + j) * TS + i; }
+
+// Stage NC components of block b (grid-local) of field F and its halo into tile[NC][1000].
+// Halo cells of an absent neighbour come from `ghost` (the block's slot, [NC][1000]) or are
+// zero when ghost == nullptr.  Corners of the 10^3 box are skipped.
+template <typename T, int NC>
+__device__ __forceinline__ void load_tile(T *__restrict__ tile, const T *__restrict__ F, int b,
+                                          const int *__restrict__ nbr, const T *__restrict__ ghost) {
+    for (int idx = threadIdx.x; idx < T3; idx += blockDim.x) {
+        int ti = idx % TS, tj = (idx / TS) % TS, tk = idx / (TS * TS);
+        int di = (ti == 0) ? -1 : (ti == TS - 1 ? 1 : 0);
+        int dj = (tj == 0) ? -1 : (tj == TS - 1 ? 1 : 0);
+        int dk = (tk == 0) ? -1 : (tk == TS - 1 ? 1 : 0);
+        int nout = (di != 0) + (dj != 0) + (dk != 0);
+        if (nout == 3) continue;
+        int src = nout == 0 ? b : __ldg(nbr + b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1));
+        if (src >= 0) {
+            int li = ti - 1 - BS * di, lj = tj - 1 - BS * dj, lk = tk - 1 - BS * dk;
+            const T *p = F + (size_t)src * NC * B3 + (lk * BS + lj) * BS + li;
+#pragma unroll
+            for (int c = 0; c < NC; c++) tile[c * T3 + idx] = p[c * B3];
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; c++) tile[c * T3 + idx] = ghost ? ghost[c * T3 + idx] : T(0);
+        }
+    }
+}
+
+// Phi for the face between tile cells p (low) and p + sa.  Components b1 < b2 are the two
+// axes other than a, with tile strides s1, s2.
+template <typename T>
+__device__ __forceinline__ void face_phi(const T *__restrict__ tB, const T *__restrict__ tE, int p, int a,
+                                         int sa, int b1, int s1, int b2, int s2, T &phi1, T &phi2) {
+    const T es = tE[p] + tE[p + sa];
+    const T *Ba = tB + a * T3;
+    const T *B1 = tB + b1 * T3;
+    const T *B2 = tB + b2 * T3;
+    T n1 = B1[p + sa] - B1[p];
+    T t1 = (Ba[p + sa + s1] + Ba[p + s1]) - (Ba[p + sa - s1] + Ba[p - s1]);
+    phi1 = es * (T(0.25) * t1 - n1);
+    T n2 = B2[p + sa] - B2[p];
+    T t2 = (Ba[p + sa + s2] + Ba[p + s2]) - (Ba[p + sa - s2] + Ba[p - s2]);
+    phi2 = es * (T(0.25) * t2 - n2);
+}
+
+// All 1728 face fluxes of a staged block into phi[3 axes][2 comps][576]:
+//   x faces (k*8+j)*9+fi, y faces (k*9+fj)*8+i, z faces (fk*8+j)*8+i.
+template <typename T>
+__device__ __forceinline__ void all_faces(const T *__restrict__ tB, const T *__restrict__ tE, T *__restrict__ phi) {
+    for (int f = threadIdx.x; f < 3 * 576; f += blockDim.x) {
+        int ax = f / 576, r = f - ax * 576;
+        T p1, p2;
+        if (ax == 0) {
+            int fi = r % 9, j = (r / 9) % 8, k = r / 72;
+            face_phi(tB, tE, tix(fi, j + 1, k + 1), 0, 1, 1, TS, 2, TS * TS, p1, p2);
+        } else if (ax == 1) {
+            int i = r % 8, fj = (r / 8) % 9, k = r / 72;
+            face_phi(tB, tE, tix(i + 1, fj, k + 1), 1, TS, 0, 1, 2, TS * TS, p1, p2);
+        } else {
+            int i = r % 8, j = (r / 8) % 8, fk = r / 64;
+            face_phi(tB, tE, tix(i + 1, j + 1, fk), 2, TS * TS, 0, 1, 1, TS, p1, p2);
+        }
+        phi[(ax * 2 + 0) * 576 + r] = p1;
+        phi[(ax * 2 + 1) * 576 + r] = p2;
+    }
+}
+
+// sum_a (Phi_a(+) - Phi_a(-)) at cell (i,j,k) for the three components
+template <typename T>
+__device__ __forceinline__ void cell_div(const T *__restrict__ phi, int i, int j, int k, T &dx, T &dy, T &dz) {
+    const T *px0 = phi + 0 * 576, *px1 = phi + 1 * 576;  // x faces: comps y, z
+    const T *py0 = phi + 2 * 576, *py1 = phi + 3 * 576;  // y faces: comps x, z
+    const T *pz0 = phi + 4 * 576, *pz1 = phi + 5 * 576;  // z faces: comps x, y
+    int xl = (k * 8 + j) * 9 + i, yl = (k * 9 + j) * 8 + i, zl = (k * 8 + j) * 8 + i;
+    dx = (py0[yl + 8] - py0[yl]) + (pz0[zl + 64] - pz0[zl]);
+    dy = (px0[xl + 1] - px0[xl]) + (pz1[zl + 64] - pz1[zl]);
+    dz = (px1[xl + 1] - px1[xl]) + (py1[yl + 8] - py1[yl]);
+}
+
+// index of face-plane value (u, v) of side s = 2a + hi in the phi array
+__device__ __forceinline__ int plane_face(int a, int hi, int u, int v) {
+    if (a == 0) return (v * 8 + u) * 9 + (hi ? 8 : 0);
+    if (a == 1) return (v * 9 + (hi ? 8 : 0)) * 8 + u;
+    return ((hi ? 8 : 0) * 8 + v) * 8 + u;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    T s = 0;
+    for (int i = 0; i < nw; i++) s += red[i];
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    T s = 0;
+    for (int i = 0; i < nw; i++) s = fmax(s, red[i]);
+    return s;
+}
+
+// ------------------------------------------------------------------ composite operator
+template <typename TO>
+__global__ void __launch_bounds__(512) k_composite(GridDev g, const double *__restrict__ X,
+                                                   const double *__restrict__ Y, const double *__restrict__ eta,
+                                                   const double *__restrict__ Gx, const double *__restrict__ Geta,
+                                                   double a, double coef, double d, TO *__restrict__ out,
+                                                   double *__restrict__ reg, const int *__restrict__ rsrc_tab,
+                                                   double *__restrict__ partials, double vol) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *tB = reinterpret_cast<double *>(smem_raw);
+    double *tE = tB + 3 * T3;
+    double *phi = tE + T3;
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    if (g.covered && g.covered[b]) {
+        if (partials && threadIdx.x < 3) partials[b * 3 + threadIdx.x] = 0.0;
+        return;
+    }
+    const int slot = g.gslot ? g.gslot[b] : -1;
+    load_tile<double, 3>(tB, X, b, g.nbr, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
+    load_tile<double, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    __syncthreads();
+    all_faces(tB, tE, phi);
+    __syncthreads();
+    const double inv2h = 0.5 / g.h;
+    // flux registers: faces with no same-level neighbour publish F = Phi / (2h)
+    if (g.freg) {
+        for (int s = 0; s < 6; s++) {
+            int slotr = g.freg[b * 6 + s];
+            if (slotr < 0) continue;
+            int ax = s >> 1, hi = s & 1;
+            for (int q = threadIdx.x; q < 128; q += blockDim.x) {
+                int comp = q >> 6, uv = q & 63;
+                reg[(size_t)slotr * 128 + q] = phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, uv & 7, uv >> 3)] * inv2h;
+            }
+        }
+    }
+    // refluxing: faces next to a covered block take 2h * (mean of the four fine fluxes)
+    if (g.rsrc) {
+        for (int s = 0; s < 6; s++) {
+            int src = g.rsrc[b * 6 + s];
+            if (src < 0) continue;
+            int ax = s >> 1, hi = s & 1;
+            for (int q = threadIdx.x; q < 128; q += blockDim.x) {
+                int comp = q >> 6, u = q & 7, v = (q >> 3) & 7;
+                int fslot = rsrc_tab[src * 4 + (v >> 2) * 2 + (u >> 2)];
+                const double *R = reg + (size_t)fslot * 128 + comp * 64;
+                int fu = 2 * (u & 3), fv = 2 * (v & 3);
+                double m = 0.25 * ((R[fv * 8 + fu] + R[fv * 8 + fu + 1]) + (R[(fv + 1) * 8 + fu] + R[(fv + 1) * 8 + fu + 1]));
+                phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, u, v)] = m * (2.0 * g.h);
+            }
+        }
+    }
+    __syncthreads();
+    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    double dv[3];
+    cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
+    double sr = 0.0, ss = 0.0, mx = 0.0;
+    const int p = tix(i + 1, j + 1, k + 1);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        size_t id = ((size_t)b * 3 + c) * B3 + t;
+        double y = Y ? Y[id] : 0.0;
+        double o = a * tB[c * T3 + p] + coef * dv[c] + d * y;
+        out[id] = (TO)o;
+        sr += o * o;
+        ss += y * y;
+        mx = fmax(mx, fabs(o));
+    }
+    if (partials) {
+        double s1 = block_sum(sr, red);
+        double s2 = block_sum(ss, red);
+        double s3 = block_max(mx, red);
+        if (threadIdx.x == 0) {
+            partials[b * 3 + 0] = s1 * vol;
+            partials[b * 3 + 1] = s2 * vol;
+            partials[b * 3 + 2] = s3;
+        }
+    }
+}
+
+template <typename TO>
+cudaError_t launch_composite(const GridDev &g, const double *X, const double *Y, const double *eta,
+                             const double *Gx, const double *Geta, double a, double c, double d, TO *out,
+                             double *reg, const int *rsrc_tab, double *partials, double vol, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    const size_t sm = (4 * T3 + 6 * 576) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_composite<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    double coef = c / (2.0 * g.h * g.h);
+    k_composite<TO><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, reg, rsrc_tab, partials, vol);
+    return cudaGetLastError();
+}
+template cudaError_t launch_composite<double>(const GridDev &, const double *, const double *, const double *,
+                                              const double *, const double *, double, double, double, double *,
+                                              double *, const int *, double *, double, cudaStream_t);
+template cudaError_t launch_composite<float>(const GridDev &, const double *, const double *, const double *,
+                                             const double *, const double *, double, double, double, float *,
+                                             double *, const int *, double *, double, cudaStream_t);
+
+// ------------------------------------------------------------------ red-black smoothing
+// One colour pass (Eq. 19): colour cells get e + (r - e - lamdt divF(e)) * inv, the other
+// colour is copied; e_in and e_out are distinct buffers so every update reads the pre-pass
+// state (Jacobi within a colour).  256 threads, one per colour cell.
+template <typename T>
+__global__ void __launch_bounds__(256) k_smooth(GridDev g, const T *__restrict__ e_in, T *__restrict__ e_out,
+                                                const T *__restrict__ r, const T *__restrict__ eta,
+                                                const T *__restrict__ inv, const T *__restrict__ Ge,
+                                                const T *__restrict__ Geta, T coef, int colour) {
+    __shared__ __align__(16) T tB[3 * T3];
+    __shared__ __align__(16) T tE[T3];
+    const int b = blockIdx.x;
+    const int slot = g.gslot ? g.gslot[b] : -1;
+    load_tile<T, 3>(tB, e_in, b, g.nbr, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    load_tile<T, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int k = t >> 5, j = (t >> 2) & 7;
+    const int ic = 2 * (t & 3) + ((j + k + colour) & 1);  // colour cell
+    const int io = 2 * (t & 3) + ((j + k + colour + 1) & 1);  // other colour
+    const int p = tix(ic + 1, j + 1, k + 1);
+    T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
+    face_phi(tB, tE, p - 1, 0, 1, 1, TS, 2, TS * TS, xl1, xl2);
+    face_phi(tB, tE, p, 0, 1, 1, TS, 2, TS * TS, xh1, xh2);
+    face_phi(tB, tE, p - TS, 1, TS, 0, 1, 2, TS * TS, yl1, yl2);
+    face_phi(tB, tE, p, 1, TS, 0, 1, 2, TS * TS, yh1, yh2);
+    face_phi(tB, tE, p - TS * TS, 2, TS * TS, 0, 1, 1, TS, zl1, zl2);
+    face_phi(tB, tE, p, 2, TS * TS, 0, 1, 1, TS, zh1, zh2);
+    T dv[3];
+    dv[0] = (yh1 - yl1) + (zh1 - zl1);
+    dv[1] = (xh1 - xl1) + (zh2 - zl2);
+    dv[2] = (xh2 - xl2) + (yh2 - yl2);
+    const int cc = (k * 8 + j) * 8 + ic, co = (k * 8 + j) * 8 + io;
+    const int po = tix(io + 1, j + 1, k + 1);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        size_t base = ((size_t)b * 3 + c) * B3;
+        T ev = tB[c * T3 + p];
+        T res = r[base + cc] - ev - coef * dv[c];
+        e_out[base + cc] = ev + res * inv[base + cc];
+        e_out[base + co] = tB[c * T3 + po];
+    }
+}
+
+template <typename T>
+cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta, const T *inv,
+                          const T *Ge, const T *Geta, double lamdt, int colour, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    T coef = (T)(lamdt / (2.0 * g.h * g.h));
+    k_smooth<T><<<g.nblk, 256, 0, s>>>(g, e_in, e_out, r, eta, inv, Ge, Geta, coef, colour);
+    return cudaGetLastError();
+}
+template cudaError_t launch_smooth<double>(const GridDev &, const double *, double *, const double *, const double *,
+                                           const double *, const double *, const double *, double, int, cudaStream_t);
+template cudaError_t launch_smooth<float>(const GridDev &, const float *, float *, const float *, const float *,
+                                          const float *, const float *, const float *, double, int, cudaStream_t);
+
+// ------------------------------------------------------------------ inverse diagonal
+// inv_c = 1 / (1 + alpha_c), alpha_c = lamdt/h^2 sum_{a != c} (eta_{-1/2} + eta_{+1/2})
+// with face eta the mean of the two cells (Eqs. 11, 21-23).
+template <typename T>
+__global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict__ eta, const T *__restrict__ Geta,
+                                                 double lh2, T *__restrict__ inv) {
+    __shared__ T tE[T3];
+    const int b = blockIdx.x;
+    const int slot = g.gslot ? g.gslot[b] : -1;
+    load_tile<T, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    __syncthreads();
+    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    const int p = tix(i + 1, j + 1, k + 1);
+    const double e0 = (double)tE[p];
+    const double sa[3] = {0.5 * (e0 + (double)tE[p + 1]) + 0.5 * (e0 + (double)tE[p - 1]),
+                          0.5 * (e0 + (double)tE[p + TS]) + 0.5 * (e0 + (double)tE[p - TS]),
+                          0.5 * (e0 + (double)tE[p + TS * TS]) + 0.5 * (e0 + (double)tE[p - TS * TS])};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double al = 0.0;
+        for (int ax = 0; ax < 3; ax++)
+            if (ax != c) al += lh2 * sa[ax];
+        inv[((size_t)b * 3 + c) * B3 + t] = (T)(1.0 / (1.0 + al));
+    }
+}
+
+template <typename T>
+cudaError_t launch_invdiag(const GridDev &g, const T *eta, const T *Geta, double lamdt, T *inv, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    k_invdiag<T><<<g.nblk, 512, 0, s>>>(g, eta, Geta, lamdt / (g.h * g.h), inv);
+    return cudaGetLastError();
+}
+template cudaError_t launch_invdiag<double>(const GridDev &, const double *, const double *, double, double *, cudaStream_t);
+template cudaError_t launch_invdiag<float>(const GridDev &, const float *, const float *, double, float *, cudaStream_t);
+
+// ------------------------------------------------------------------ residual + restriction
+template <typename T>
+__global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__restrict__ e, const T *__restrict__ r,
+                                                        const T *__restrict__ eta, const T *__restrict__ Ge,
+                                                        const T *__restrict__ Geta, T coef, T *__restrict__ t_out,
+                                                        T *__restrict__ coarse, T *__restrict__ lex, int3 ld) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tB = reinterpret_cast<T *>(smem_raw);
+    T *tE = tB + 3 * T3;
+    T *phi = tE + T3;
+    T *tt = phi + 6 * 576;
+    const int b = blockIdx.x;
+    const int slot = g.gslot ? g.gslot[b] : -1;
+    load_tile<T, 3>(tB, e, b, g.nbr, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    load_tile<T, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    __syncthreads();
+    all_faces(tB, tE, phi);
+    __syncthreads();
+    {
+        const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+        T dv[3];
+        cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
+        const int p = tix(i + 1, j + 1, k + 1);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            size_t id = ((size_t)b * 3 + c) * B3 + t;
+            T v = r[id] - tB[c * T3 + p] - coef * dv[c];
+            tt[c * B3 + t] = v;
+            if (t_out) t_out[id] = v;
+        }
+    }
+    __syncthreads();
+    if ((coarse || lex) && threadIdx.x < 192) {
+        const int c = threadIdx.x >> 6, q = threadIdx.x & 63;
+        const int ci = q & 3, cj = (q >> 2) & 3, ck = q >> 4;
+        const T *src = tt + c * B3;
+        T s = 0;
+        for (int dk = 0; dk < 2; dk++)
+            for (int dj = 0; dj < 2; dj++)
+                for (int di = 0; di < 2; di++) s += src[((2 * ck + dk) * 8 + 2 * cj + dj) * 8 + 2 * ci + di];
+        s = s / T(8);
+        if (coarse) {
+            const int pb = g.parent[b], o = g.octant[b];
+            const int x = 4 * (o & 1) + ci, y = 4 * ((o >> 1) & 1) + cj, z = 4 * (o >> 2) + ck;
+            coarse[((size_t)pb * 3 + c) * B3 + (z * 8 + y) * 8 + x] = s;
+        } else {
+            const int x = 4 * g.origin[b * 3 + 0] + ci, y = 4 * g.origin[b * 3 + 1] + cj, z = 4 * g.origin[b * 3 + 2] + ck;
+            lex[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x] = s;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_resid_restrict(const GridDev &g, const T *e, const T *r, const T *eta, const T *Ge, const T *Geta,
+                                  double lamdt, T *t_out, T *coarse, T *lex, const int *ldims, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    const size_t sm = (4 * T3 + 6 * 576 + 3 * B3) * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_resid_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    int3 ld = make_int3(ldims ? ldims[0] : 0, ldims ? ldims[1] : 0, ldims ? ldims[2] : 0);
+    k_resid_restrict<T><<<g.nblk, 512, sm, s>>>(g, e, r, eta, Ge, Geta, (T)(lamdt / (2.0 * g.h * g.h)), t_out, coarse,
+                                                lex, ld);
+    return cudaGetLastError();
+}
+template cudaError_t launch_resid_restrict<double>(const GridDev &, const double *, const double *, const double *,
+                                                   const double *, const double *, double, double *, double *, double *,
+                                                   const int *, cudaStream_t);
+template cudaError_t launch_resid_restrict<float>(const GridDev &, const float *, const float *, const float *,
+                                                  const float *, const float *, double, float *, float *, float *,
+                                                  const int *, cudaStream_t);
+
+// ------------------------------------------------------------------ plain restriction
+template <typename T>
+__global__ void __launch_bounds__(512) k_restrict(GridDev g, const T *__restrict__ fine, int ncomp,
+                                                  T *__restrict__ coarse, T *__restrict__ lex, int3 ld) {
+    const int b = blockIdx.x;
+    for (int q = threadIdx.x; q < 64 * ncomp; q += blockDim.x) {
+        const int c = q >> 6, cq = q & 63;
+        const int ci = cq & 3, cj = (cq >> 2) & 3, ck = cq >> 4;
+        const T *src = fine + ((size_t)b * ncomp + c) * B3;
+        T s = 0;
+        for (int dk = 0; dk < 2; dk++)
+            for (int dj = 0; dj < 2; dj++)
+                for (int di = 0; di < 2; di++) s += src[((2 * ck + dk) * 8 + 2 * cj + dj) * 8 + 2 * ci + di];
+        s = s / T(8);
+        if (coarse) {
+            const int pb = g.parent[b], o = g.octant[b];
+            const int x = 4 * (o & 1) + ci, y = 4 * ((o >> 1) & 1) + cj, z = 4 * (o >> 2) + ck;
+            coarse[((size_t)pb * ncomp + c) * B3 + (z * 8 + y) * 8 + x] = s;
+        } else {
+            const int x = 4 * g.origin[b * 3 + 0] + ci, y = 4 * g.origin[b * 3 + 1] + cj, z = 4 * g.origin[b * 3 + 2] + ck;
+            lex[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x] = s;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_restrict(const GridDev &g, const T *fine, int ncomp, T *coarse, T *lex, const int *ldims,
+                            cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    int3 ld = make_int3(ldims ? ldims[0] : 0, ldims ? ldims[1] : 0, ldims ? ldims[2] : 0);
+    k_restrict<T><<<g.nblk, 256, 0, s>>>(g, fine, ncomp, coarse, lex, ld);
+    return cudaGetLastError();
+}
+template cudaError_t launch_restrict<double>(const GridDev &, const double *, int, double *, double *, const int *, cudaStream_t);
+template cudaError_t launch_restrict<float>(const GridDev &, const float *, int, float *, float *, const int *, cudaStream_t);
+
+// ------------------------------------------------------------------ prolongation
+// fine += trilinear interpolation (weights 3/4, 1/4 per axis) of the coarser grid, read
+// through a 6^3 window around the block's footprint in its parent (blocked) or with
+// periodic wrap (lexicographic coarse grid).
+template <typename T>
+__global__ void __launch_bounds__(512) k_prolong_add(GridDev g, GridDev gc, const T *__restrict__ coarse,
+                                                     const T *__restrict__ lex, int3 ld, T *__restrict__ fine,
+                                                     int *__restrict__ err) {
+    __shared__ T win[3 * 216];
+    const int b = blockIdx.x;
+    const int o = lex ? 0 : g.octant[b];
+    const int pb = lex ? 0 : g.parent[b];
+    for (int q = threadIdx.x; q < 216; q += blockDim.x) {
+        const int wx = q % 6, wy = (q / 6) % 6, wz = q / 36;
+        if (lex) {
+            int x = 4 * g.origin[b * 3 + 0] - 1 + wx, y = 4 * g.origin[b * 3 + 1] - 1 + wy, z = 4 * g.origin[b * 3 + 2] - 1 + wz;
+            x = (x + ld.x) % ld.x; y = (y + ld.y) % ld.y; z = (z + ld.z) % ld.z;
+            for (int c = 0; c < 3; c++) win[c * 216 + q] = lex[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x];
+        } else {
+            int cx = 4 * (o & 1) - 1 + wx, cy = 4 * ((o >> 1) & 1) - 1 + wy, cz = 4 * (o >> 2) - 1 + wz;
+            int dx = cx < 0 ? -1 : (cx > 7 ? 1 : 0), dy = cy < 0 ? -1 : (cy > 7 ? 1 : 0), dz = cz < 0 ? -1 : (cz > 7 ? 1 : 0);
+            int src = gc.nbr[pb * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+            if (src < 0) {
+                if (err) *err = 1;
+                for (int c = 0; c < 3; c++) win[c * 216 + q] = T(0);
+            } else {
+                int lx = cx - 8 * dx, ly = cy - 8 * dy, lz = cz - 8 * dz;
+                for (int c = 0; c < 3; c++) win[c * 216 + q] = coarse[((size_t)src * 3 + c) * B3 + (lz * 8 + ly) * 8 + lx];
+            }
+        }
+    }
+    __syncthreads();
+    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    const int wi = (i >> 1) + 1, wj = (j >> 1) + 1, wk = (k >> 1) + 1;
+    const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const T *w = win + c * 216;
+        T v = 0;
+        for (int ak = 0; ak < 2; ak++)
+            for (int aj = 0; aj < 2; aj++)
+                for (int ai = 0; ai < 2; ai++) {
+                    T wt = (ai ? T(0.25) : T(0.75)) * (aj ? T(0.25) : T(0.75)) * (ak ? T(0.25) : T(0.75));
+                    v += wt * w[((wk + ak * sk) * 6 + (wj + aj * sj)) * 6 + (wi + ai * si)];
+                }
+        fine[((size_t)b * 3 + c) * B3 + t] += v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const GridDev &g, const GridDev *gc, const T *coarse, const T *lex, const int *ldims,
+                               T *fine, int *err, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    int3 ld = make_int3(ldims ? ldims[0] : 0, ldims ? ldims[1] : 0, ldims ? ldims[2] : 0);
+    GridDev c = gc ? *gc : GridDev();
+    k_prolong_add<T><<<g.nblk, 512, 0, s>>>(g, c, coarse, lex, ld, fine, err);
+    return cudaGetLastError();
+}
+template cudaError_t launch_prolong_add<double>(const GridDev &, const GridDev *, const double *, const double *,
+                                                const int *, double *, int *, cudaStream_t);
+template cudaError_t launch_prolong_add<float>(const GridDev &, const GridDev *, const float *, const float *,
+                                               const int *, float *, int *, cudaStream_t);
+
+// ------------------------------------------------------------------ coarse-fine ghosts
+// Ghost slot of a level-l block: every halo cell gets the tri-quadratic interpolant of the
+// parent's 3x3x3 coarse neighbourhood at the child's centre (offset s h_c/4 per axis):
+//   f0 + sum_d [s_d (f+ - f-)/8 + (f+ - 2 f0 + f-)/32] + sum_{d<e} s_d s_e (cross diff)/64.
+// The coarse window is [4o-2, 4o+6) per axis in parent-local cells.
+template <typename TS_, typename TD>
+__global__ void __launch_bounds__(512) k_ghost_fill(GridDev g, GridDev gc, const TS_ *__restrict__ coarse, int ncomp,
+                                                    TD *__restrict__ ghost, int *__restrict__ err) {
+    __shared__ double win[3 * 512];
+    const int sl = blockIdx.x;
+    const int b = g.slot_block[sl];
+    const int pb = g.parent[b], o = g.octant[b];
+    const int ox = 4 * (o & 1), oy = 4 * ((o >> 1) & 1), oz = 4 * (o >> 2);
+    for (int q = threadIdx.x; q < 512; q += blockDim.x) {
+        const int wx = q & 7, wy = (q >> 3) & 7, wz = q >> 6;
+        int cx = ox - 2 + wx, cy = oy - 2 + wy, cz = oz - 2 + wz;
+        int dx = cx < 0 ? -1 : (cx > 7 ? 1 : 0), dy = cy < 0 ? -1 : (cy > 7 ? 1 : 0), dz = cz < 0 ? -1 : (cz > 7 ? 1 : 0);
+        int src = gc.nbr[pb * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+        if (src < 0) {
+            if (err) *err = 1;
+            for (int c = 0; c < ncomp; c++) win[c * 512 + q] = 0.0;
+        } else {
+            int lx = cx - 8 * dx, ly = cy - 8 * dy, lz = cz - 8 * dz;
+            for (int c = 0; c < ncomp; c++)
+                win[c * 512 + q] = (double)coarse[((size_t)src * ncomp + c) * B3 + (lz * 8 + ly) * 8 + lx];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < T3; idx += blockDim.x) {
+        const int ti = idx % TS, tj = (idx / TS) % TS, tk = idx / (TS * TS);
+        const int gi = ti - 1, gj = tj - 1, gk = tk - 1;
+        const int outx = gi < 0 || gi > 7, outy = gj < 0 || gj > 7, outz = gk < 0 || gk > 7;
+        const int nout = outx + outy + outz;
+        if (nout == 0 || nout == 3) continue;
+        const int w[3] = {(gi >> 1) + 2, (gj >> 1) + 2, (gk >> 1) + 2};
+        const double sg[3] = {(gi & 1) ? 1.0 : -1.0, (gj & 1) ? 1.0 : -1.0, (gk & 1) ? 1.0 : -1.0};
+        const int st[3] = {1, 8, 64};
+        const int w0 = (w[2] * 8 + w[1]) * 8 + w[0];
+        for (int c = 0; c < ncomp; c++) {
+            const double *W = win + c * 512;
+            const double f0 = W[w0];
+            double val = f0;
+            for (int d = 0; d < 3; d++) {
+                double fp = W[w0 + st[d]], fm = W[w0 - st[d]];
+                val += sg[d] * (fp - fm) / 8.0 + (fp - 2.0 * f0 + fm) / 32.0;
+            }
+            for (int d = 0; d < 3; d++)
+                for (int e = d + 1; e < 3; e++) {
+                    double x4 = (W[w0 + st[d] + st[e]] - W[w0 + st[d] - st[e]]) - (W[w0 - st[d] + st[e]] - W[w0 - st[d] - st[e]]);
+                    val += sg[d] * sg[e] * x4 / 64.0;
+                }
+            ghost[((size_t)sl * ncomp + c) * T3 + idx] = (TD)val;
+        }
+    }
+}
+
+template <typename TS_, typename TD>
+cudaError_t launch_ghost_fill(const GridDev &g, const GridDev &gc, const TS_ *coarse, int ncomp, TD *ghost, int *err,
+                              cudaStream_t s) {
+    if (g.nslot == 0) return cudaSuccess;
+    k_ghost_fill<TS_, TD><<<g.nslot, 512, 0, s>>>(g, gc, coarse, ncomp, ghost + (size_t)g.slot0 * ncomp * T3, err);
+    return cudaGetLastError();
+}
+template cudaError_t launch_ghost_fill<double, double>(const GridDev &, const GridDev &, const double *, int, double *,
+                                                       int *, cudaStream_t);
+template cudaError_t launch_ghost_fill<double, float>(const GridDev &, const GridDev &, const double *, int, float *,
+                                                      int *, cudaStream_t);
+template cudaError_t launch_ghost_fill<float, float>(const GridDev &, const GridDev &, const float *, int, float *,
+                                                     int *, cudaStream_t);
+
+// ------------------------------------------------------------------ sync down, update
+__global__ void __launch_bounds__(512) k_sync_down(GridDev gc, double *__restrict__ Bc, const double *__restrict__ Bf) {
+    const int b = blockIdx.x;
+    if (!gc.covered[b]) return;
+    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    const int oc = (i >> 2) | ((j >> 2) << 1) | ((k >> 2) << 2);
+    const int ch = gc.child[b * 8 + oc];
+    const int fi = 2 * (i & 3), fj = 2 * (j & 3), fk = 2 * (k & 3);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double *src = Bf + ((size_t)ch * 3 + c) * B3;
+        double s = 0.0;
+        for (int dk = 0; dk < 2; dk++)
+            for (int dj = 0; dj < 2; dj++)
+                for (int di = 0; di < 2; di++) s += src[((fk + dk) * 8 + fj + dj) * 8 + fi + di];
+        Bc[((size_t)b * 3 + c) * B3 + t] = s / 8.0;
+    }
+}
+
+cudaError_t launch_sync_down(const GridDev &gc, double *Bc, const double *Bf, cudaStream_t s) {
+    if (gc.nblk == 0) return cudaSuccess;
+    k_sync_down<<<gc.nblk, 512, 0, s>>>(gc, Bc, Bf);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_update(GridDev g, double *__restrict__ B, const T *__restrict__ e) {
+    const int b = blockIdx.x;
+    if (g.covered && g.covered[b]) return;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        size_t id = ((size_t)b * 3 + c) * B3 + threadIdx.x;
+        B[id] += (double)e[id];
+    }
+}
+
+template <typename T>
+cudaError_t launch_update(const GridDev &g, double *B, const T *e, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    k_update<T><<<g.nblk, 512, 0, s>>>(g, B, e);
+    return cudaGetLastError();
+}
+template cudaError_t launch_update<double>(const GridDev &, double *, const double *, cudaStream_t);
+template cudaError_t launch_update<float>(const GridDev &, double *, const float *, cudaStream_t);
+
+__global__ void __launch_bounds__(512) k_zero_covered(GridDev g, double *__restrict__ x) {
+    const int b = blockIdx.x;
+    if (!(g.covered && g.covered[b])) return;
+    for (int c = 0; c < 3; c++) x[((size_t)b * 3 + c) * B3 + threadIdx.x] = 0.0;
+}
+
+cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s) {
+    if (g.nblk == 0 || !g.covered) return cudaSuccess;
+    k_zero_covered<<<g.nblk, 512, 0, s>>>(g, x);
+    return cudaGetLastError();
+}
+
+// deterministic reduction of per-block partials {sum R^2 dV, sum S^2 dV, max |R|}
+__global__ void __launch_bounds__(1024) k_norm_reduce(const double *__restrict__ part, int n, double *__restrict__ out) {
+    __shared__ double red[32];
+    double a = 0.0, b = 0.0, m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += part[i * 3 + 0];
+        b += part[i * 3 + 1];
+        m = fmax(m, part[i * 3 + 2]);
+    }
+    double sa = block_sum(a, red);
+    double sb = block_sum(b, red);
+    double sm = block_max(m, red);
+    if (threadIdx.x == 0) {
+        out[0] = sa;
+        out[1] = sb;
+        out[2] = sm;
+    }
+}
+
+cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *out, cudaStream_t s) {
+    k_norm_reduce<<<1, 1024, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+template <typename TS_, typename TD>
+__global__ void k_convert(const TS_ *__restrict__ src, TD *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (TD)src[i];
+}
+
+template <typename TS_, typename TD>
+cudaError_t launch_convert(const TS_ *src, TD *dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 152 * 32) grid = 152 * 32;
+    k_convert<TS_, TD><<<grid, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double *, double *, size_t, cudaStream_t);
+
+// ------------------------------------------------------------------ coarsest grids
+// Lexicographic periodic grids below the last blocked grid, all handled by one thread block
+// with a barrier between phases.  Face flux and divergence as above, with periodic wrap.
+template <typename T>
+struct LexGrid {
+    int nx, ny, nz;
+    __device__ __forceinline__ int wrap(int v, int n) const { return v < 0 ? v + n : (v >= n ? v - n : v); }
+    __device__ __forceinline__ size_t id(int c, int x, int y, int z) const {
+        return (((size_t)c * nz + wrap(z, nz)) * ny + wrap(y, ny)) * nx + wrap(x, nx);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void lex_face(const LexGrid<T> &G, const T *B, const T *E, int x, int y, int z, int a,
+                                         T &phi1, T &phi2) {
+    int o[3] = {0, 0, 0};
+    o[a] = 1;
+    const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
+    T es = E[G.id(0, x, y, z)] + E[G.id(0, x + o[0], y + o[1], z + o[2])];
+    T ph[2];
+    const int bb[2] = {b1, b2};
+    for (int q = 0; q < 2; q++) {
+        int b = bb[q];
+        int e[3] = {0, 0, 0};
+        e[b] = 1;
+        T n = B[G.id(b, x + o[0], y + o[1], z + o[2])] - B[G.id(b, x, y, z)];
+        T tr = (B[G.id(a, x + o[0] + e[0], y + o[1] + e[1], z + o[2] + e[2])] + B[G.id(a, x + e[0], y + e[1], z + e[2])]) -
+               (B[G.id(a, x + o[0] - e[0], y + o[1] - e[1], z + o[2] - e[2])] + B[G.id(a, x - e[0], y - e[1], z - e[2])]);
+        ph[q] = es * (T(0.25) * tr - n);
+    }
+    phi1 = ph[0];
+    phi2 = ph[1];
+}
+
+template <typename T>
+__device__ __forceinline__ void lex_div(const LexGrid<T> &G, const T *B, const T *E, int x, int y, int z, T dv[3]) {
+    T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
+    lex_face(G, B, E, x - 1, y, z, 0, xl1, xl2);
+    lex_face(G, B, E, x, y, z, 0, xh1, xh2);
+    lex_face(G, B, E, x, y - 1, z, 1, yl1, yl2);
+    lex_face(G, B, E, x, y, z, 1, yh1, yh2);
+    lex_face(G, B, E, x, y, z - 1, 2, zl1, zl2);
+    lex_face(G, B, E, x, y, z, 2, zh1, zh2);
+    dv[0] = (yh1 - yl1) + (zh1 - zl1);
+    dv[1] = (xh1 - xl1) + (zh2 - zl2);
+    dv[2] = (xh2 - xl2) + (yh2 - yl2);
+}
+
+template <typename T>
+__device__ void lex_sweeps(const SmallDev<T> &sm, int s, double lamdt, int nsweep) {
+    LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+    const int n = G.nx * G.ny * G.nz;
+    const T coef = (T)(lamdt / (2.0 * sm.h[s] * sm.h[s]));
+    T *e = sm.e[s], *d = sm.t[s];
+    const T *r = sm.r[s], *E = sm.eta[s], *inv = sm.inv[s];
+    for (int sw = 0; sw < nsweep; sw++)
+        for (int colour = 0; colour < 2; colour++) {
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                int x = q % G.nx, y = (q / G.nx) % G.ny, z = q / (G.nx * G.ny);
+                if (((x + y + z) & 1) != colour) continue;
+                T dv[3];
+                lex_div(G, e, E, x, y, z, dv);
+                for (int c = 0; c < 3; c++) {
+                    size_t id = (size_t)c * n + q;
+                    d[id] = (r[id] - e[id] - coef * dv[c]) * inv[id];
+                }
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                int x = q % G.nx, y = (q / G.nx) % G.ny, z = q / (G.nx * G.ny);
+                if (((x + y + z) & 1) != colour) continue;
+                for (int c = 0; c < 3; c++) e[(size_t)c * n + q] += d[(size_t)c * n + q];
+            }
+            __syncthreads();
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm, double lamdt, int nu1, int nu2, int nc) {
+    // e on the first small grid starts from zero
+    {
+        const int n0 = sm.dims[0][0] * sm.dims[0][1] * sm.dims[0][2];
+        for (int q = threadIdx.x; q < 3 * n0; q += blockDim.x) sm.e[0][q] = T(0);
+        __syncthreads();
+    }
+    int s = 0;
+    for (; s < sm.n - 1; s++) {
+        lex_sweeps(sm, s, lamdt, nu1);
+        LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+        LexGrid<T> C{sm.dims[s + 1][0], sm.dims[s + 1][1], sm.dims[s + 1][2]};
+        const int n = G.nx * G.ny * G.nz, nc_ = C.nx * C.ny * C.nz;
+        const T coef = (T)(lamdt / (2.0 * sm.h[s] * sm.h[s]));
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            int x = q % G.nx, y = (q / G.nx) % G.ny, z = q / (G.nx * G.ny);
+            T dv[3];
+            lex_div(G, sm.e[s], sm.eta[s], x, y, z, dv);
+            for (int c = 0; c < 3; c++) {
+                size_t id = (size_t)c * n + q;
+                sm.t[s][id] = sm.r[s][id] - sm.e[s][id] - coef * dv[c];
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < 3 * nc_; q += blockDim.x) {
+            int c = q / nc_, cq = q % nc_;
+            int x = cq % C.nx, y = (cq / C.nx) % C.ny, z = cq / (C.nx * C.ny);
+            T acc = 0;
+            for (int dk = 0; dk < 2; dk++)
+                for (int dj = 0; dj < 2; dj++)
+                    for (int di = 0; di < 2; di++) acc += sm.t[s][G.id(c, 2 * x + di, 2 * y + dj, 2 * z + dk)];
+            sm.r[s + 1][q] = acc / T(8);
+            sm.e[s + 1][q] = T(0);
+        }
+        __syncthreads();
+    }
+    lex_sweeps(sm, s, lamdt, nc);
+    for (s = sm.n - 2; s >= 0; s--) {
+        LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+        LexGrid<T> C{sm.dims[s + 1][0], sm.dims[s + 1][1], sm.dims[s + 1][2]};
+        const int n = G.nx * G.ny * G.nz;
+        for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {
+            int c = q / n, fq = q % n;
+            int x = fq % G.nx, y = (fq / G.nx) % G.ny, z = fq / (G.nx * G.ny);
+            int px = x >> 1, py = y >> 1, pz = z >> 1;
+            int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
+            T v = 0;
+            for (int ak = 0; ak < 2; ak++)
+                for (int aj = 0; aj < 2; aj++)
+                    for (int ai = 0; ai < 2; ai++) {
+                        T wt = (ai ? T(0.25) : T(0.75)) * (aj ? T(0.25) : T(0.75)) * (ak ? T(0.25) : T(0.75));
+                        v += wt * sm.e[s + 1][C.id(c, px + ai * sx, py + aj * sy, pz + ak * sz)];
+                    }
+            sm.e[s][q] += v;
+        }
+        __syncthreads();
+        lex_sweeps(sm, s, lamdt, nu2);
+    }
+}
+
+template <typename T>
+cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post, int n_coarse, cudaStream_t s) {
+    if (sm.n == 0) return cudaSuccess;
+    k_bottom<T><<<1, 1024, 0, s>>>(sm, lamdt, nu_pre, nu_post, n_coarse);
+    return cudaGetLastError();
+}
+template cudaError_t launch_bottom<double>(const SmallDev<double> &, double, int, int, int, cudaStream_t);
+template cudaError_t launch_bottom<float>(const SmallDev<float> &, double, int, int, int, cudaStream_t);
+
+// eta chain over the small grids (optional) and their inverse diagonals
+template <typename T>
+__global__ void __launch_bounds__(1024) k_small_setup(SmallDev<T> sm, double lamdt, int eta_chain) {
+    if (eta_chain) {
+        for (int s = 1; s < sm.n; s++) {
+            LexGrid<T> F{sm.dims[s - 1][0], sm.dims[s - 1][1], sm.dims[s - 1][2]};
+            LexGrid<T> C{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+            const int nc_ = C.nx * C.ny * C.nz;
+            for (int q = threadIdx.x; q < nc_; q += blockDim.x) {
+                int x = q % C.nx, y = (q / C.nx) % C.ny, z = q / (C.nx * C.ny);
+                T acc = 0;
+                for (int dk = 0; dk < 2; dk++)
+                    for (int dj = 0; dj < 2; dj++)
+                        for (int di = 0; di < 2; di++) acc += sm.eta[s - 1][F.id(0, 2 * x + di, 2 * y + dj, 2 * z + dk)];
+                sm.eta[s][q] = acc / T(8);
+            }
+            __syncthreads();
+        }
+    }
+    for (int s = 0; s < sm.n; s++) {
+        LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+        const int n = G.nx * G.ny * G.nz;
+        const double lh2 = lamdt / (sm.h[s] * sm.h[s]);
+        const T *E = sm.eta[s];
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            int x = q % G.nx, y = (q / G.nx) % G.ny, z = q / (G.nx * G.ny);
+            double e0 = (double)E[q];
+            double sa[3] = {0.5 * (e0 + (double)E[G.id(0, x + 1, y, z)]) + 0.5 * (e0 + (double)E[G.id(0, x - 1, y, z)]),
+                            0.5 * (e0 + (double)E[G.id(0, x, y + 1, z)]) + 0.5 * (e0 + (double)E[G.id(0, x, y - 1, z)]),
+                            0.5 * (e0 + (double)E[G.id(0, x, y, z + 1)]) + 0.5 * (e0 + (double)E[G.id(0, x, y, z - 1)])};
+            for (int c = 0; c < 3; c++) {
+                double al = 0.0;
+                for (int ax = 0; ax < 3; ax++)
+                    if (ax != c) al += lh2 * sa[ax];
+                sm.inv[s][(size_t)c * n + q] = (T)(1.0 / (1.0 + al));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_small_setup(const SmallDev<T> &sm, double lamdt, bool eta_chain, cudaStream_t s) {
+    if (sm.n == 0) return cudaSuccess;
+    k_small_setup<T><<<1, 1024, 0, s>>>(sm, lamdt, eta_chain ? 1 : 0);
+    return cudaGetLastError();
+}
+template cudaError_t launch_small_setup<double>(const SmallDev<double> &, double, bool, cudaStream_t);
+template cudaError_t launch_small_setup<float>(const SmallDev<float> &, double, bool, cudaStream_t);
+
+}  // namespace ohm

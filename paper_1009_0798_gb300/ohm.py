@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libohm (include/ohm.h), same entry-point names.
+
+Argument marshalling only: tensors are checked (CUDA, float64, contiguous, shape) and passed
+by data_ptr(); every step of the solver runs in the library's CUDA kernels.  There is no
+CPU path: if the compiled library is missing this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+OHM_OK = 0
+OHM_ERR_INVALID = -1
+OHM_ERR_NOT_CONVERGED = -2
+OHM_ERR_NONFINITE = -3
+OHM_ERR_OOM = -4
+OHM_ERR_CUDA = -5
+OHM_FP64 = 0
+OHM_MIXED = 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libohm.so")
+
+
+class OhmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class HierDesc(C.Structure):
+    _fields_ = [("base_cells", C.c_int32 * 3), ("dx0", C.c_double), ("nlevels", C.c_int32), ("nblocks", C.c_int64),
+                ("block_lijk", C.POINTER(C.c_int32)), ("lam", C.c_double), ("precision", C.c_int32),
+                ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32), ("max_outer", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("cycles", C.c_int32), ("converged", C.c_int32), ("rel_l2_initial", C.c_double),
+                ("rel_l2", C.c_double), ("max_abs", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libohm.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                               "python -m paper_1009_0798_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, dp = C.c_void_p, C.c_double
+        L.ohm_create_hierarchy.argtypes = [C.POINTER(HierDesc), C.POINTER(vp)]
+        L.ohm_set_eta.argtypes = [vp, vp]
+        L.ohm_cn_step.argtypes = [vp, vp, vp, dp, dp, C.POINTER(StepStats)]
+        L.ohm_residual_norm.argtypes = [vp, vp, C.POINTER(dp), C.POINTER(dp)]
+        L.ohm_destroy.argtypes = [vp]
+        L.ohm_destroy.restype = None
+        L.ohm_status_string.argtypes = [C.c_int]
+        L.ohm_status_string.restype = C.c_char_p
+        L.ohm_op_div_flux.argtypes = [vp, vp, vp]
+        L.ohm_op_source.argtypes = [vp, vp, dp, vp]
+        L.ohm_op_residual.argtypes = [vp, vp, vp, dp, vp, C.POINTER(dp)]
+        L.ohm_op_sync_down.argtypes = [vp, vp]
+        L.ohm_op_vcycle.argtypes = [vp, vp, dp, vp]
+        L.ohm_mg_grid_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.ohm_op_grid_smooth.argtypes = [vp, C.c_int, vp, vp, vp, dp, C.c_int]
+        L.ohm_op_grid_residual.argtypes = [vp, C.c_int, vp, vp, vp, dp, vp]
+        L.ohm_op_grid_restrict.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+        L.ohm_op_grid_prolong_add.argtypes = [vp, C.c_int, vp, vp]
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().ohm_status_string(status).decode()
+    except Exception:  # library not loadable: keep the numeric status
+        return "status"
+
+
+def _ptr(t, numel=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(status: int, what: str, allow=(OHM_OK,)):
+    if status not in allow:
+        raise OhmError(status, what)
+    return status
+
+
+class Hierarchy:
+    """Owning handle of an ohm_hier (ohm_create_hierarchy / ohm_destroy)."""
+
+    def __init__(self, handle, nblocks: int, lam: float, mixed: bool):
+        self._h = handle
+        self.nblocks = nblocks
+        self.lam = lam
+        self.mixed = mixed
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().ohm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
+                         nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50,
+                         stream=None) -> Hierarchy:
+    """blocks: int32 [nblocks, 4] rows (level, bi, bj, bk) sorted by level.
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None for torch's current stream."""
+    import torch
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    d = HierDesc()
+    d.base_cells[:] = [int(v) for v in base_cells]
+    d.dx0 = float(dx0)
+    d.nlevels = int(blocks[:, 0].max()) + 1 if len(blocks) else 0
+    d.nblocks = len(blocks)
+    d.block_lijk = blocks.ctypes.data_as(C.POINTER(C.c_int32))
+    d.lam = float(lam)
+    d.precision = int(precision)
+    d.nu_pre, d.nu_post, d.n_coarse, d.max_outer = int(nu_pre), int(nu_post), int(n_coarse), int(max_outer)
+    d.stream = C.c_void_p(raw)
+    h = C.c_void_p()
+    _check(lib().ohm_create_hierarchy(C.byref(d), C.byref(h)), "ohm_create_hierarchy")
+    return Hierarchy(h, len(blocks), lam, precision == OHM_MIXED)
+
+
+def ohm_set_eta(h: Hierarchy, eta) -> None:
+    _check(lib().ohm_set_eta(h.handle, _ptr(eta, h.nblocks * 512, "eta")), "ohm_set_eta")
+
+
+def ohm_cn_step(h: Hierarchy, B, eta, dt: float, tol: float) -> dict:
+    """One implicit step in place on B.  Returns the step statistics; raises OhmError on any
+    status other than OHM_OK and OHM_ERR_NOT_CONVERGED (reported as converged=False)."""
+    st = StepStats()
+    e = _ptr(eta, h.nblocks * 512, "eta") if eta is not None else None
+    status = lib().ohm_cn_step(h.handle, _ptr(B, h.nblocks * 1536, "B"), e, float(dt), float(tol), C.byref(st))
+    _check(status, "ohm_cn_step", allow=(OHM_OK, OHM_ERR_NOT_CONVERGED))
+    return {"status": status, "cycles": st.cycles, "converged": bool(st.converged), "rel_l2_initial": st.rel_l2_initial,
+            "rel_l2": st.rel_l2, "max_abs": st.max_abs}
+
+
+def ohm_residual_norm(h: Hierarchy, B) -> tuple[float, float]:
+    r, m = C.c_double(), C.c_double()
+    _check(lib().ohm_residual_norm(h.handle, _ptr(B, h.nblocks * 1536, "B"), C.byref(r), C.byref(m)),
+           "ohm_residual_norm")
+    return r.value, m.value
+
+
+def ohm_op_div_flux(h: Hierarchy, B, out) -> None:
+    _check(lib().ohm_op_div_flux(h.handle, _ptr(B, h.nblocks * 1536, "B"), _ptr(out, h.nblocks * 1536, "out")),
+           "ohm_op_div_flux")
+
+
+def ohm_op_source(h: Hierarchy, b, dt: float, S) -> None:
+    _check(lib().ohm_op_source(h.handle, _ptr(b, h.nblocks * 1536, "b"), float(dt), _ptr(S, h.nblocks * 1536, "S")),
+           "ohm_op_source")
+
+
+def ohm_op_residual(h: Hierarchy, B, S, dt: float, R) -> dict:
+    n = (C.c_double * 4)()
+    _check(lib().ohm_op_residual(h.handle, _ptr(B, h.nblocks * 1536, "B"), _ptr(S, h.nblocks * 1536, "S"), float(dt),
+                                 _ptr(R, h.nblocks * 1536, "R"), n), "ohm_op_residual")
+    return {"rel_l2": n[0], "max_abs": n[1], "l2_R": n[2], "l2_S": n[3]}
+
+
+def ohm_op_sync_down(h: Hierarchy, B) -> None:
+    _check(lib().ohm_op_sync_down(h.handle, _ptr(B, h.nblocks * 1536, "B")), "ohm_op_sync_down")
+
+
+def ohm_op_vcycle(h: Hierarchy, R, dt: float, e) -> None:
+    _check(lib().ohm_op_vcycle(h.handle, _ptr(R, h.nblocks * 1536, "R"), float(dt), _ptr(e, h.nblocks * 1536, "e")),
+           "ohm_op_vcycle")
+
+
+def ohm_mg_grid_info(h: Hierarchy, m: int):
+    dims = (C.c_int32 * 3)()
+    nb = C.c_int64()
+    _check(lib().ohm_mg_grid_info(h.handle, m, dims, C.byref(nb), None), "ohm_mg_grid_info")
+    ijk = np.zeros((max(nb.value, 1), 3), np.int32)
+    if nb.value:
+        _check(lib().ohm_mg_grid_info(h.handle, m, dims, C.byref(nb), ijk.ctypes.data_as(C.POINTER(C.c_int32))),
+               "ohm_mg_grid_info")
+    return tuple(dims), nb.value, ijk[: nb.value]
+
+
+def ohm_op_grid_smooth(h: Hierarchy, m: int, e, r, eta, dt: float, colour: int) -> None:
+    _check(lib().ohm_op_grid_smooth(h.handle, m, _ptr(e), _ptr(r), _ptr(eta), float(dt), int(colour)),
+           "ohm_op_grid_smooth")
+
+
+def ohm_op_grid_residual(h: Hierarchy, m: int, e, r, eta, dt: float, t) -> None:
+    _check(lib().ohm_op_grid_residual(h.handle, m, _ptr(e), _ptr(r), _ptr(eta), float(dt), _ptr(t)),
+           "ohm_op_grid_residual")
+
+
+def ohm_op_grid_restrict(h: Hierarchy, m: int, fine, coarse, ncomp: int = 3) -> None:
+    _check(lib().ohm_op_grid_restrict(h.handle, m, _ptr(fine), _ptr(coarse), int(ncomp)), "ohm_op_grid_restrict")
+
+
+def ohm_op_grid_prolong_add(h: Hierarchy, m: int, coarse, fine) -> None:
+    _check(lib().ohm_op_grid_prolong_add(h.handle, m, _ptr(coarse), _ptr(fine)), "ohm_op_grid_prolong_add")

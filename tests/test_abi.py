@@ -1,0 +1,81 @@
+"""CPU-side checks of the C ABI: the library exports every symbol include/ohm.h declares and
+rejects bad descriptors before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ohm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ohm_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libohm():
+    from paper_1009_0798_gb300 import build
+    build.build()
+    from paper_1009_0798_gb300 import ohm
+    return ohm
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_functions()
+    for n in ("ohm_create_hierarchy", "ohm_set_eta", "ohm_cn_step", "ohm_residual_norm", "ohm_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libohm):
+    L = C.CDLL(libohm.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings(libohm):
+    assert libohm.status_string(libohm.OHM_OK) == "ok"
+    assert "converged" in libohm.status_string(libohm.OHM_ERR_NOT_CONVERGED)
+
+
+def _desc(libohm, base=(16, 16, 16), blocks=None, **kw):
+    from paper_1009_0798_gb300 import workloads as W
+    h = W.uniform(*base, 1.0 / base[0])
+    return h.blocks if blocks is None else blocks
+
+
+@pytest.mark.parametrize("case", ["bad_base", "unsorted", "duplicate", "incomplete_base", "bad_lambda",
+                                  "bad_counts", "not_nested", "incomplete_octet"])
+def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
+    from paper_1009_0798_gb300 import workloads as W
+    kw = dict(lam=0.5, nu_pre=2, nu_post=2, n_coarse=8, max_outer=10, stream=0)
+    base = (16, 16, 16)
+    blocks = W.uniform(16, 16, 16, 1.0 / 16).blocks.copy()
+    if case == "bad_base":
+        base = (12, 16, 16)
+    elif case == "unsorted":
+        h = W.refined(16, 16, 16, 1.0 / 16, [lambda lo, hi: lo[0] < 0.3])
+        blocks = h.blocks[::-1].copy()
+    elif case == "duplicate":
+        blocks = np.concatenate([blocks, blocks[:1]])
+    elif case == "incomplete_base":
+        blocks = blocks[:-1]
+    elif case == "bad_lambda":
+        kw["lam"] = 0.0
+    elif case == "bad_counts":
+        kw["n_coarse"] = 0
+    elif case == "not_nested":
+        # a level-2 octet whose parent's neighbourhood is missing at level 1
+        h = W.refined(32, 32, 32, 1.0 / 32, [lambda lo, hi: lo[0] < 0.2 and lo[1] < 0.2 and lo[2] < 0.2])
+        extra = np.array([[2, 0, 0, 0], [2, 1, 0, 0], [2, 0, 1, 0], [2, 1, 1, 0],
+                          [2, 0, 0, 1], [2, 1, 0, 1], [2, 0, 1, 1], [2, 1, 1, 1]], np.int32)
+        blocks = np.concatenate([h.blocks, extra])
+    elif case == "incomplete_octet":
+        h = W.refined(16, 16, 16, 1.0 / 16, [lambda lo, hi: lo[0] < 0.3])
+        blocks = h.blocks[:-1].copy()
+    with pytest.raises(libohm.OhmError) as ei:
+        libohm.ohm_create_hierarchy(base, 1.0 / base[0], blocks, **kw)
+    assert ei.value.status == libohm.OHM_ERR_INVALID

@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element,
+on seeded inputs: each hot-path step on its own, then whole V-cycles and CN steps.
+
+Tolerance: 1e-12 relative L2 for FP64 (the kernels and the oracle differ only in rounding
+order); mixed precision is held to 1e-9 after refinement to 1e-11.
+"""
+import numpy as np
+import pytest
+
+from paper_1009_0798_gb300 import workloads as W
+from tests.helpers import amr_three_level, amr_two_level, dense_of_grid, grid_of_dense, rand_fields, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ohm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_0798_gb300 import build, ohm as mod
+    build.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def make(ohm, h, lam=0.5, precision=0, **kw):
+    p = dict(nu_pre=2, nu_post=2, n_coarse=8, max_outer=50)
+    p.update(kw)
+    return ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=lam, precision=precision, **p)
+
+
+HIERS = {
+    "uniform_16x24x8": lambda: W.uniform(16, 24, 8, 1.0 / 16),
+    "uniform_32": lambda: W.uniform(32, 32, 32, 1.0 / 32),
+    "amr_2level": lambda: amr_two_level(16),
+    "amr_3level": lambda: amr_three_level(16),
+    "sinusoid_e1": lambda: W.sinusoid_half_refined(N=8).hier,
+}
+
+
+# ------------------------------------------------------------------ single steps
+@pytest.mark.parametrize("name", list(HIERS))
+def test_div_flux(ohm, orc, name):
+    """a1 ghost fill + a2 face fluxes + a8 refluxing + a9 sync of covered cells."""
+    h = HIERS[name]()
+    B, eta = rand_fields(h, 1, 2.0)
+    o = orc.Oracle(h, 0.5, eta)
+    g = make(ohm, h)
+    ohm.ohm_set_eta(g, dev(eta))
+    out = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
+    ohm.ohm_op_div_flux(g, dev(B), out)
+    assert rel_err(host(out), o.div_flux(B).ravel()) < TOL64
+
+
+@pytest.mark.parametrize("name", ["uniform_16x24x8", "amr_3level"])
+@pytest.mark.parametrize("lam", [0.5, 1.0])
+def test_source_and_residual(ohm, orc, name, lam):
+    """a3 source (Eq. 14) and a4 residual with norms (Eq. 20)."""
+    h = HIERS[name]()
+    b, eta = rand_fields(h, 2, 2.0)
+    B = b + 0.1 * np.random.default_rng(3).standard_normal(b.shape)
+    dt = 3.0 * h.dx(h.nlevels - 1) ** 2
+    o = orc.Oracle(h, lam, eta)
+    g = make(ohm, h, lam=lam)
+    ohm.ohm_set_eta(g, dev(eta))
+    S = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
+    ohm.ohm_op_source(g, dev(b), dt, S)
+    S_ref = o.source(b, dt)
+    assert rel_err(host(S), S_ref.ravel()) < TOL64
+    R = torch.zeros_like(S)
+    norms = ohm.ohm_op_residual(g, dev(B), dev(S_ref), dt, R)
+    R_ref, n_ref = o.residual(B, S_ref, dt)
+    assert rel_err(host(R), R_ref.ravel()) < TOL64
+    assert norms["rel_l2"] == pytest.approx(n_ref["rel_l2"], rel=1e-12)
+    assert norms["max_abs"] == pytest.approx(n_ref["max_abs"], rel=1e-12)
+
+
+@pytest.mark.parametrize("name", ["amr_2level", "amr_3level"])
+def test_sync_down(ohm, orc, name):
+    """a9: covered cells become the mean of their children, finest first."""
+    h = HIERS[name]()
+    B, eta = rand_fields(h, 4)
+    g = make(ohm, h)
+    t = dev(B)
+    ohm.ohm_op_sync_down(g, t)
+    assert rel_err(host(t), orc.Oracle(h, 0.5, eta).sync_down(B).ravel()) < 1e-15
+
+
+@pytest.mark.parametrize("m", [0, 1])
+@pytest.mark.parametrize("colour", [0, 1])
+def test_grid_smooth(ohm, orc, m, colour):
+    """a5: one red-black colour pass on base multigrid grid m."""
+    h = W.uniform(64, 32, 32, 1.0 / 64)
+    o = orc.Oracle(h, 0.5)
+    g = make(ohm, h)
+    dims, nb, ijk = ohm.ohm_mg_grid_info(g, m)
+    rng = np.random.default_rng(10 + m)
+    e = rng.standard_normal((3,) + dims[::-1])
+    r = rng.standard_normal((3,) + dims[::-1])
+    eta = 10 ** rng.uniform(-1, 1, (1,) + dims[::-1])
+    dt = 5.0 * h.dx0 ** 2
+    et = dev(grid_of_dense(e, ijk))
+    ohm.ohm_op_grid_smooth(g, m, et, dev(grid_of_dense(r, ijk)), dev(grid_of_dense(eta, ijk)), dt, colour)
+    got = dense_of_grid(host(et).reshape(nb, 3, 8, 8, 8), ijk, dims, 3)
+    want = o.grid_smooth(m, e, r, eta, dt, colour)
+    assert rel_err(got, want) < TOL64
+
+
+@pytest.mark.parametrize("m", [0, 1])
+def test_grid_residual_restrict_prolong(ohm, orc, m):
+    """a4 (level residual), a6 restriction, a7 prolongation on base multigrid grid m."""
+    h = W.uniform(64, 32, 32, 1.0 / 64)
+    o = orc.Oracle(h, 0.5)
+    g = make(ohm, h)
+    dims, nb, ijk = ohm.ohm_mg_grid_info(g, m)
+    cdims, cnb, cijk = ohm.ohm_mg_grid_info(g, m + 1)
+    rng = np.random.default_rng(20 + m)
+    e = rng.standard_normal((3,) + dims[::-1])
+    r = rng.standard_normal((3,) + dims[::-1])
+    eta = 10 ** rng.uniform(-1, 1, (1,) + dims[::-1])
+    dt = 5.0 * h.dx0 ** 2
+    t = torch.zeros(nb * 1536, dtype=torch.float64, device="cuda")
+    ohm.ohm_op_grid_residual(g, m, dev(grid_of_dense(e, ijk)), dev(grid_of_dense(r, ijk)), dev(grid_of_dense(eta, ijk)), dt, t)
+    got = dense_of_grid(host(t).reshape(nb, 3, 8, 8, 8), ijk, dims, 3)
+    assert rel_err(got, o.grid_residual(m, e, r, eta, dt)) < TOL64
+    # restriction of 3 and 1 components
+    for nc, f in ((3, e), (1, eta)):
+        ct = torch.zeros(cnb * 512 * nc, dtype=torch.float64, device="cuda")
+        ohm.ohm_op_grid_restrict(g, m, dev(grid_of_dense(f, ijk)), ct, nc)
+        got = dense_of_grid(host(ct).reshape(cnb, nc, 8, 8, 8), cijk, cdims, nc)
+        assert rel_err(got, o.grid_restrict(m, f, nc)) < 1e-15
+    # prolongation
+    c = rng.standard_normal((3,) + cdims[::-1])
+    ft = dev(grid_of_dense(r, ijk))
+    ohm.ohm_op_grid_prolong_add(g, m, dev(grid_of_dense(c, cijk)), ft)
+    got = dense_of_grid(host(ft).reshape(nb, 3, 8, 8, 8), ijk, dims, 3)
+    assert rel_err(got, o.grid_prolong_add(m, c, r)) < 1e-15
+
+
+# ------------------------------------------------------------------ whole cycles
+@pytest.mark.parametrize("name", list(HIERS))
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3)])
+def test_vcycle(ohm, orc, name, nu):
+    """One V-cycle (a5, a6, a7, a11 and the AMR coarse-fine ghosts) from a zero guess."""
+    h = HIERS[name]()
+    R, eta = rand_fields(h, 5, 2.0)
+    R[~h.is_leaf()] = 0.0
+    dt = 8.0 * h.dx(h.nlevels - 1) ** 2
+    o = orc.Oracle(h, 0.5, eta)
+    g = make(ohm, h, nu_pre=nu[0], nu_post=nu[1], n_coarse=6)
+    ohm.ohm_set_eta(g, dev(eta))
+    e = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
+    ohm.ohm_op_vcycle(g, dev(R), dt, e)
+    want = o.vcycle(R, dt, nu[0], nu[1], 6)
+    assert rel_err(host(e), want.ravel()) < TOL64
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+@pytest.mark.parametrize("lam", [0.5, 1.0])
+def test_cn_step_fixed_schedule(ohm, orc, name, lam):
+    """Whole step with a fixed number of cycles: identical schedule on both sides."""
+    h = HIERS[name]()
+    b, eta = rand_fields(h, 6, 2.0)
+    dt = 6.0 * h.dx(h.nlevels - 1) ** 2
+    o = orc.Oracle(h, lam, eta)
+    g = make(ohm, h, lam=lam, max_outer=4, n_coarse=6)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, -1.0)
+    want, info = o.cn_step(b, dt, -1.0, 2, 2, 6, 4)
+    assert st["cycles"] == 4
+    assert rel_err(host(B), want.ravel()) < TOL64
+    assert st["rel_l2"] == pytest.approx(info["history"][-1], rel=1e-9)
+
+
+@pytest.mark.parametrize("name", ["uniform_32", "amr_3level"])
+def test_cn_step_converged(ohm, orc, name):
+    """Both sides converged to 1e-13 reach the same B^{n+1}."""
+    h = HIERS[name]()
+    b, eta = rand_fields(h, 7, 1.0)
+    b = orc.Oracle(h, 0.5, eta).sync_down(b)
+    dt = 3.0 * h.dx(h.nlevels - 1) ** 2
+    o = orc.Oracle(h, 0.5, eta)
+    g = make(ohm, h, max_outer=80)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-13)
+    want, info = o.cn_step(b, dt, 1e-13, 2, 2, 8, 80)
+    assert st["converged"] and info["converged"]
+    assert rel_err(host(B), want.ravel()) < TOL64
+    rel, mx = ohm.ohm_residual_norm(g, B)
+    assert rel <= 1e-13
+
+
+def test_periodic_box_32_workload(ohm, orc):
+    """The 32^3 periodic workload (eta = 1, dt = 10x explicit limit): 20 CN steps to 1e-10
+    on the GPU track the oracle step by step."""
+    wl = W.periodic_box_32()
+    o = orc.Oracle(wl.hier, 0.5, wl.eta)
+    g = make(ohm, wl.hier, max_outer=60)
+    B = dev(wl.B)
+    ohm.ohm_set_eta(g, dev(wl.eta))
+    Bo = wl.B.copy()
+    for _ in range(wl.steps):
+        st = ohm.ohm_cn_step(g, B, None, wl.dt, wl.tol)
+        Bo, info = o.cn_step(Bo, wl.dt, wl.tol, 2, 2, 8, 60)
+        assert st["converged"]
+    assert rel_err(host(B), Bo.ravel()) < 1e-10
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("name", ["uniform_32", "amr_3level", "sinusoid_e1"])
+def test_mixed_precision_matches_fp64_oracle(ohm, orc, name):
+    """FP32 multigrid inside FP64 defect correction reaches the FP64 solution."""
+    h = HIERS[name]()
+    b, eta = rand_fields(h, 8, 1.0)
+    b = orc.Oracle(h, 0.5, eta).sync_down(b)
+    dt = 4.0 * h.dx(h.nlevels - 1) ** 2
+    want, _ = orc.Oracle(h, 0.5, eta).cn_step(b, dt, 1e-14, 2, 2, 8, 80)
+    g = make(ohm, h, precision=1, max_outer=80)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-11)
+    assert st["converged"]
+    assert rel_err(host(B), want.ravel()) < 1e-9
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_block_grid(ohm, orc):
+    """8^3: one block whose neighbours are all itself (periodic)."""
+    h = W.uniform(8, 8, 8, 0.125)
+    b, eta = rand_fields(h, 9, 1.0)
+    dt = 0.05
+    g = make(ohm, h, max_outer=3)
+    B = dev(b)
+    ohm.ohm_cn_step(g, B, dev(eta), dt, -1.0)
+    want, _ = orc.Oracle(h, 0.5, eta).cn_step(b, dt, -1.0, 2, 2, 8, 3)
+    assert rel_err(host(B), want.ravel()) < TOL64
+
+
+def test_zero_field_stays_zero_and_not_converged_status(ohm, orc):
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    _, eta = rand_fields(h, 10)
+    g = make(ohm, h, max_outer=1)
+    B = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
+    st = ohm.ohm_cn_step(g, B, dev(eta), 0.01, 1e-9)
+    assert float(B.abs().max()) == 0.0
+    b, _ = rand_fields(h, 11)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, None, 1.0, 1e-14)
+    assert st["status"] == ohm.OHM_ERR_NOT_CONVERGED and not st["converged"] and st["cycles"] == 1
+
+
+def test_invalid_calls(ohm):
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    g = make(ohm, h)
+    B = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
+    with pytest.raises(ohm.OhmError) as ei:
+        ohm.ohm_cn_step(g, B, None, 0.1, 1e-9)  # eta never set
+    assert ei.value.status == ohm.OHM_ERR_INVALID
+    with pytest.raises(ohm.OhmError):
+        ohm.ohm_cn_step(g, B, torch.ones(h.nblocks * 512, dtype=torch.float64, device="cuda"), -1.0, 1e-9)
+    with pytest.raises(ohm.OhmError):
+        ohm.ohm_residual_norm(g, B)  # no step yet
+
+
+def test_nonfinite_eta_reports_nonfinite(ohm):
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    g = make(ohm, h, max_outer=3)
+    eta = torch.ones(h.nblocks * 512, dtype=torch.float64, device="cuda")
+    eta[100] = float("nan")
+    b, _ = rand_fields(h, 12)
+    with pytest.raises(ohm.OhmError) as ei:
+        ohm.ohm_cn_step(g, dev(b), eta, 0.01, 1e-9)
+    assert ei.value.status == ohm.OHM_ERR_NONFINITE
