@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the implicit ohmic-dissipation step (Matsumoto 2011, Sec. 2) on one GB300.
+
+Workload: uniform 256^3 periodic unit box, eta = 1e-3 (1 + 999 exp(-|x-c|^2/0.05^2)), B the
+curl of a seeded k^-2 random vector potential (rms 1), dt = 100x the explicit limit at the
+largest eta, consecutive CN steps each converged to ||R||/||S|| <= 1e-9.  One bench step is
+one CN step (source, defect-correction cycles of residual + V-cycle + update).
+
+Metric: cell-steps/s = cells x CN steps / device time.  `value` is the mixed-precision path
+(FP32 multigrid inside FP64 defect correction); the plain FP64 path is reported beside it.
+The oracle (FP64 CPU reference) is timed on the host cores as `cpu_baseline`, and is the
+`--impl reference` arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s at 256^3 to rel. residual 1e-9"
+UNIT = "cell-steps/s"
+L2_BYTES = 129e6
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--size", type=int, default=256, help="cells per axis (multiple of 8)")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 issue rate measured on this machine's GB300 by a DFMA throughput probe (600 G DFMA/s,
+# i.e. 1.2 TFLOP/s): the "alu" roofline denominator for float64 stencil kernels.
+FP64_PEAK_TFLOPS = 1.20
+
+# Algorithmic work per cell of one launch (bytes that must cross HBM, flops
+# that the stencil must execute), by kernel kind and precision of its multigrid arrays.
+#   smooth pass:   e in, r, eta, inv in, e out  -> 13 words of the multigrid type
+#                  57 flops per cell (114 per updated cell, half the cells per pass)
+#   composite:     B, S, eta (float64) in, residual out in the multigrid type
+#                  1728 faces x 15 flops / 512 + 9 (divergence) + 9 (combination) = 68.6 flops
+ALGO = {
+    ("smooth", 4): {"bytes": 13 * 4, "flops": 57.0},
+    ("smooth", 8): {"bytes": 13 * 8, "flops": 57.0},
+    ("composite", 4): {"bytes": 7 * 8 + 3 * 4, "flops": 68.6},
+    ("composite", 8): {"bytes": 7 * 8 + 3 * 8, "flops": 68.6},
+}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        smax = max(num(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(num(r[3]) for r in rows)}
+
+
+def dist():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    td.barrier()
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_cycle_count(n: int):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_cycles.json")
+    if os.path.exists(path):
+        d = json.load(open(path)).get(f"resistive_bump_{n}")
+        if d and d.get("converged"):
+            return int(d["cycles"]), "tests/golden/oracle_cycles.json"
+    return None, None
+
+
+def time_oracle_sample(wl, gpu_cycles=None):
+    """Times the oracle on the full workload: one source + residual (max_outer = 0) and one
+    more defect-correction cycle (max_outer = 1); a CN step costs t0 + cycles x (t1 - t0)."""
+    from oracle.oracle import Oracle
+    n = wl.hier.base_cells[0]
+    cycles, src = oracle_cycle_count(n)
+    if cycles is None:
+        cycles, src = gpu_cycles, "FP64 GPU run of the same schedule (parity-tested identical)"
+    o = Oracle(wl.hier, wl.lam, wl.eta)
+    t = time.perf_counter()
+    o.cn_step(wl.B, wl.dt, -1.0, 2, 2, 16, 0)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    o.cn_step(wl.B, wl.dt, -1.0, 2, 2, 16, 1)
+    t1 = time.perf_counter() - t
+    per_step = t0 + cycles * max(t1 - t0, 0.0)
+    cells = wl.hier.leaf_cells()
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": cells / per_step, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"one 256^3 step's source+residual ({t0:.1f} s) and one defect-correction cycle "
+                       f"({t1 - t0:.1f} s) on the full input; step = source + {cycles} cycles ({src})"),
+            "seconds_per_step": per_step}
+
+
+def run_reference(args):
+    ws, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from paper_1009_0798_gb300 import workloads as W
+    import __graft_entry__ as ge
+    from oracle import build as obuild
+    obuild.build()
+    wl = W.resistive_bump_256(n=args.size)
+    samples = []
+    for k in range(args.warmup + args.steps):
+        s = time_oracle_sample(wl)
+        if k >= args.warmup:
+            samples.append(s)
+    v = statistics.median(s["value"] for s in samples)
+    per = statistics.median(s["seconds_per_step"] for s in samples)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"resistive_bump_{args.size}^3", "cells": wl.hier.leaf_cells(), "tol": wl.tol,
+                       "precision": "fp64 CPU oracle", "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    del ge
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def kernel_traffic(kind: str):
+    """DRAM bytes per cell of a kernel from a committed ncu capture, if it was taken on the
+    current kernel source (hash match), else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_1009_0798_gb300", "csrc", "ohm_kernels.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    d = json.load(open(path))
+    e = d.get(kind)
+    if not e or e.get("source_sha") != h:
+        return None
+    return float(e["dram_bytes_per_cell"])
+
+
+def run_steps(ohm, g, B, B0, eta, wl, nsteps, stream, evs=None):
+    import torch
+    infos = []
+    B.copy_(B0)
+    for k in range(nsteps):
+        if evs is not None:
+            evs[k].record(stream)
+        st = ohm.ohm_cn_step(g, B, None, wl.dt, wl.tol)
+        infos.append(st)
+        if not st["converged"]:
+            raise RuntimeError(f"step {k} did not converge: {st}")
+    if evs is not None:
+        evs[nsteps].record(stream)
+    torch.cuda.synchronize()
+    return infos
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_1009_0798_gb300 import ohm
+    from paper_1009_0798_gb300 import workloads as W
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    ge.build()
+    wl = W.resistive_bump_256(n=args.size)
+    cells = wl.hier.leaf_cells()
+    stream = torch.cuda.current_stream()
+    B0 = torch.from_numpy(np.ascontiguousarray(wl.B)).cuda()
+    eta = torch.from_numpy(np.ascontiguousarray(wl.eta)).cuda()
+    B = torch.empty_like(B0)
+    hbm_peak, peak_src = peaks()
+
+    def make(precision):
+        g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam,
+                                     precision=precision, nu_pre=2, nu_post=2, n_coarse=16, max_outer=400,
+                                     stream=stream)
+        ohm.ohm_set_eta(g, eta)
+        return g
+
+    def timed(g, precision, profile=True):
+        tsize = 4 if precision == ohm.OHM_MIXED else 8
+        # warm-up; the first two also pick the dominant kernel (composite vs smooth)
+        totals = {}
+        for k in range(args.warmup):
+            kind = [ohm.OHM_K_COMPOSITE, ohm.OHM_K_SMOOTH][k % 2] if k < 2 else None
+            if kind is not None:
+                ohm.ohm_prof_enable(g, kind, min_blocks=wl.hier.nblocks, max_launches=8192)
+            run_steps(ohm, g, B, B0, eta, wl, 1, stream)
+            if kind is not None:
+                totals[kind] = ohm.ohm_prof_read(g)["ms"]
+                ohm.ohm_prof_enable(g, -1)
+        dom = max(totals, key=totals.get) if totals else ohm.OHM_K_SMOOTH
+        if profile:
+            ohm.ohm_prof_enable(g, dom, min_blocks=wl.hier.nblocks, max_launches=1 << 16)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        n0 = ohm.ohm_launch_count(g)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            infos = run_steps(ohm, g, B, B0, eta, wl, args.steps, stream, evs)
+        launches = ohm.ohm_launch_count(g) - n0
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+        total_ms = evs[0].elapsed_time(evs[args.steps])
+        prof = ohm.ohm_prof_read(g) if profile else None
+        ohm.ohm_prof_enable(g, -1)
+        name = "composite" if dom == ohm.OHM_K_COMPOSITE else "smooth"
+        return {"total_ms": total_ms, "per_step_ms": per, "infos": infos, "launches": launches,
+                "clocks": clk.summary(), "dom": name, "prof": prof, "tsize": tsize}
+
+    # mixed precision (the headline path)
+    gm = make(ohm.OHM_MIXED)
+    mixed = timed(gm, ohm.OHM_MIXED)
+    t_max = barrier_max(ws, mixed["total_ms"])
+    value = ws * cells * args.steps / (t_max * 1e-3)
+    # plain FP64 for comparison
+    fp64 = None
+    if not args.no_fp64:
+        gd = make(ohm.OHM_FP64)
+        r = timed(gd, ohm.OHM_FP64, profile=False)
+        fp64 = {"value": ws * cells * args.steps / (barrier_max(ws, r["total_ms"]) * 1e-3),
+                "ms_per_step": r["total_ms"] / args.steps,
+                "cycles_per_step": [s["cycles"] for s in r["infos"]]}
+        gd.close()
+        del gd
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Bh = torch.from_numpy(np.ascontiguousarray(wl.B)).pin_memory()
+        Eh = torch.from_numpy(np.ascontiguousarray(wl.eta)).pin_memory()
+        out = torch.empty_like(Bh).pin_memory()
+        for _ in range(1):
+            B.copy_(Bh, non_blocking=True)
+            ohm.ohm_cn_step(gm, B, eta.copy_(Eh, non_blocking=True), wl.dt, wl.tol)
+            out.copy_(B, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = Bh
+        e0.record(stream)
+        for k in range(args.steps):
+            B.copy_(cur, non_blocking=True)
+            eta.copy_(Eh, non_blocking=True)
+            st = ohm.ohm_cn_step(gm, B, eta, wl.dt, wl.tol)
+            out.copy_(B, non_blocking=True)
+            cur = out
+        e1.record(stream)
+        torch.cuda.synchronize()
+        et = barrier_max(ws, e0.elapsed_time(e1))
+        e2e = {"value": ws * cells * args.steps / (et * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": Bh.numel() * 8 + Eh.numel() * 8, "d2h_bytes_per_step": out.numel() * 8}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel, measured with events inside the timed region
+    prof = mixed["prof"]
+    algo = ALGO[(mixed["dom"], mixed["tsize"])]
+    per_launch_cells = prof["cells"] / max(prof["launches"], 1)
+    sec = prof["ms"] * 1e-3
+    if mixed["dom"] == "composite":
+        achieved = algo["flops"] * prof["cells"] / sec * 1e-12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "measured FP64 DFMA rate (x2 flops)"}
+    else:
+        achieved = algo["bytes"] * prof["cells"] / sec * 1e-9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    tb = kernel_traffic(mixed["dom"] + ("_f32" if mixed["tsize"] == 4 else "_f64"))
+    roof.update({"kernel": mixed["dom"], "launches": prof["launches"], "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
+                 "algorithmic_bytes_per_launch": algo["bytes"] * per_launch_cells,
+                 "traffic": tb * per_launch_cells if tb is not None else None})
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        try:
+            from oracle import build as obuild
+            obuild.build()
+            cpu = time_oracle_sample(wl, gpu_cycles=None)
+            cpu.pop("seconds_per_step", None)
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
+    lat = sorted(mixed["per_step_ms"])
+    p99 = lat[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
+            "config": {"workload": f"resistive_bump_{args.size}^3", "cells": cells, "tol": wl.tol,
+                       "dt_over_explicit_limit": 100, "cn_steps_per_run": args.steps, "precision": "mixed",
+                       "multigrid": "V(2,2), 16 coarsest sweeps, defect correction", "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (402 MB per float64 field vs 129 MB L2), no flush"},
+            "latency_ms": {"p50": statistics.median(lat), "p99": p99},
+            "cycles_per_step": [s["cycles"] for s in mixed["infos"]],
+            "final_rel_l2": [s["rel_l2"] for s in mixed["infos"]],
+            "fp64_plain": fp64,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": mixed["clocks"],
+            "gpu_launches": mixed["launches"]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = args_parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

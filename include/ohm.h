@@ -143,6 +143,33 @@ int ohm_op_grid_residual(ohm_hier *h, int m, const double *e_dev, const double *
 int ohm_op_grid_restrict(ohm_hier *h, int m, const double *fine_dev, double *coarse_dev, int ncomp);
 int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double *fine_dev);
 
+/* ---------------------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper): launch counting and CUDA-event timing of
+ * one kernel kind, used by the benchmark to measure a kernel inside a running step.
+ * ------------------------------------------------------------------------------------- */
+#define OHM_K_COMPOSITE      0  /* composite source / residual / flux divergence, float64    */
+#define OHM_K_SMOOTH         1  /* red-black colour pass                                      */
+#define OHM_K_RESID_RESTRICT 2  /* multigrid residual + restriction                           */
+#define OHM_K_PROLONG        3  /* prolongation + correction                                  */
+#define OHM_K_GHOST          4  /* coarse-fine ghost fill                                     */
+#define OHM_K_SYNC_DOWN      5  /* covered cells from their children                          */
+#define OHM_K_UPDATE         6  /* B += e                                                     */
+#define OHM_K_BOTTOM         7  /* coarsest-grid V-cycle (one thread block)                   */
+#define OHM_K_NORM           8  /* norm reduction                                             */
+
+/* From now on, bracket every launch of `kernel` that covers at least min_blocks blocks with
+ * a pair of CUDA events on the hierarchy's stream, up to max_launches launches (events are
+ * created here; kernel < 0 disables and releases them).  Adds one event record before and
+ * after each timed launch and nothing else. */
+int ohm_prof_enable(ohm_hier *h, int kernel, int min_blocks, int max_launches);
+
+/* Synchronises the stream, returns the summed event time of the timed launches since the
+ * last read, their count and the cells they covered, then resets the counters. */
+int ohm_prof_read(ohm_hier *h, double *total_ms, int64_t *launches, int64_t *cells);
+
+/* Kernel launches this hierarchy has issued since creation (all kinds). */
+int64_t ohm_launch_count(const ohm_hier *h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,12 @@ struct ohm_hier {
     double inv_dt = NAN;
     bool has_S = false;
     double last_dt = 0;
+
+    // instrumentation: kernel launches issued, and CUDA-event timing of one kernel kind
+    int64_t nlaunch = 0;
+    int prof_kind = -1, prof_min_blocks = 0, prof_used = 0;
+    int64_t prof_launches = 0, prof_cells = 0;
+    std::vector<cudaEvent_t> prof_ev;
 };
 
 namespace {
@@ -431,6 +437,30 @@ int allocate(ohm_hier *H, std::string &err) {
         if (e_ != cudaSuccess) return OHM_ERR_CUDA; \
     } while (0)
 
+// Kernel launch with bookkeeping: counts the launch and, when this kernel kind is being
+// timed and the launch covers at least prof_min_blocks blocks, brackets it with events.
+inline int prof_begin(ohm_hier *H, int kind, int nblk) {
+    if (H->prof_kind != kind || nblk < H->prof_min_blocks || H->prof_used + 2 > (int)H->prof_ev.size()) return -1;
+    int i = H->prof_used;
+    cudaEventRecord(H->prof_ev[i], H->s);
+    return i;
+}
+inline void prof_end(ohm_hier *H, int i, int nblk) {
+    H->nlaunch++;
+    if (i < 0) return;
+    cudaEventRecord(H->prof_ev[i + 1], H->s);
+    H->prof_used += 2;
+    H->prof_launches++;
+    H->prof_cells += (int64_t)nblk * B3;
+}
+#define LAUNCH(H, kind, nblk, call)            \
+    do {                                       \
+        int pi_ = prof_begin((H), (kind), (nblk)); \
+        cudaError_t e_ = (call);               \
+        prof_end((H), pi_, (nblk));            \
+        if (e_ != cudaSuccess) return OHM_ERR_CUDA; \
+    } while (0)
+
 template <typename T>
 T *amr_ptr(void *p, const HGrid &g, int ncomp) {
     return (T *)p + (size_t)g.off * ncomp * B3;
@@ -525,9 +555,9 @@ GridRef base_ref(ohm_hier *H, int m) {  // m = 0: AMR level 0
 template <typename T>
 int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
     for (int i = 0; i < n; i++) {
-        CK(launch_smooth<T>(G.g->dev, (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
+        LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(G.g->dev, (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
                             (const T *)G.Ge, (const T *)G.Geta, lamdt, 0, H->s));
-        CK(launch_smooth<T>(G.g->dev, (const T *)G.e2, (T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
+        LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(G.g->dev, (const T *)G.e2, (T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
                             (const T *)G.Ge, (const T *)G.Geta, lamdt, 1, H->s));
     }
     return OHM_OK;
@@ -543,17 +573,17 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const bool next_blocked = m < (int)H->mg.size();
     if (next_blocked) {
         GridRef C = base_ref<T>(H, m + 1);
-        CK(launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
+        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, (T *)C.r, nullptr, nullptr, H->s));
         CK(cudaMemsetAsync(C.e, 0, (size_t)C.g->n() * 3 * B3 * sizeof(T), H->s));
         if ((st = base_vcycle<T>(H, m + 1, lamdt))) return st;
-        CK(launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
     } else {
-        CK(launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
+        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, nullptr, (T *)H->smallbuf[0].r, H->small[0].data(), H->s));
         SmallDev<T> sm = small_dev<T>(H);
-        CK(launch_bottom<T>(sm, lamdt, d.nu_pre, d.nu_post, d.n_coarse, H->s));
-        CK(launch_prolong_add<T>(G.g->dev, nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(sm, lamdt, d.nu_pre, d.nu_post, d.n_coarse, H->s));
+        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(G.g->dev, nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
                                  H->d_err, H->s));
     }
     return sweeps<T>(H, G, d.nu_post, lamdt);
@@ -572,7 +602,7 @@ int vcycle(ohm_hier *H, double lamdt) {
         if (g.nslot) CK(cudaMemsetAsync((T *)H->ghostE + (size_t)g.slot0 * 3 * T3, 0, (size_t)g.nslot * 3 * T3 * sizeof(T), H->s));
         if ((st = sweeps<T>(H, G, d.nu_pre, lamdt))) return st;
         GridRef C = amr_ref<T>(H, l - 1, true);
-        CK(launch_resid_restrict<T>(g.dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.Ge,
+        LAUNCH(H, OHM_K_RESID_RESTRICT, g.n(), launch_resid_restrict<T>(g.dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.Ge,
                                     (const T *)G.Geta, lamdt, nullptr, (T *)C.r, nullptr, nullptr, H->s));
     }
     {
@@ -583,8 +613,8 @@ int vcycle(ohm_hier *H, double lamdt) {
     for (int l = 1; l < H->nlev; l++) {
         GridRef G = amr_ref<T>(H, l, true);
         GridRef C = amr_ref<T>(H, l - 1, true);
-        CK(launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
-        CK((launch_ghost_fill<T, T>(G.g->dev, C.g->dev, (const T *)C.e, 3, (T *)H->ghostE, H->d_err, H->s)));
+        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+        LAUNCH(H, OHM_K_GHOST, G.g->nslot, (launch_ghost_fill<T, T>(G.g->dev, C.g->dev, (const T *)C.e, 3, (T *)H->ghostE, H->d_err, H->s)));
         if ((st = sweeps<T>(H, G, d.nu_post, lamdt))) return st;
     }
     return OHM_OK;
@@ -592,13 +622,13 @@ int vcycle(ohm_hier *H, double lamdt) {
 
 int sync_down(ohm_hier *H, double *B) {
     for (int l = H->nlev - 2; l >= 0; l--)
-        CK(launch_sync_down(H->amr[l].dev, amr_ptr<double>(B, H->amr[l], 3), amr_ptr<double>(B, H->amr[l + 1], 3), H->s));
+        LAUNCH(H, OHM_K_SYNC_DOWN, H->amr[l].n(), launch_sync_down(H->amr[l].dev, amr_ptr<double>(B, H->amr[l], 3), amr_ptr<double>(B, H->amr[l + 1], 3), H->s));
     return OHM_OK;
 }
 
 int fill_ghosts_B(ohm_hier *H, const double *B) {
     for (int l = 1; l < H->nlev; l++)
-        CK((launch_ghost_fill<double, double>(H->amr[l].dev, H->amr[l - 1].dev,
+        LAUNCH(H, OHM_K_GHOST, H->amr[l].nslot, (launch_ghost_fill<double, double>(H->amr[l].dev, H->amr[l - 1].dev,
                                               amr_ptr<double>((void *)B, H->amr[l - 1], 3), 3, H->ghostB, H->d_err, H->s)));
     return OHM_OK;
 }
@@ -610,12 +640,12 @@ int composite(ohm_hier *H, const double *X, const double *Y, double a, double c,
     for (int l = H->nlev - 1; l >= 0; l--) {
         const HGrid &g = H->amr[l];
         double vol = g.h * g.h * g.h;
-        CK(launch_composite<TO>(g.dev, amr_ptr<double>((void *)X, g, 3), Y ? amr_ptr<double>((void *)Y, g, 3) : nullptr,
+        LAUNCH(H, OHM_K_COMPOSITE, g.n(), launch_composite<TO>(g.dev, amr_ptr<double>((void *)X, g, 3), Y ? amr_ptr<double>((void *)Y, g, 3) : nullptr,
                                 amr_ptr<double>(H->eta64, g, 1), H->ghostB, H->ghostEta64, a, c, dcoef,
                                 out + (size_t)g.off * 3 * B3, H->reg, H->d_rsrc, norms ? H->partials + (size_t)g.off * 3 : nullptr,
                                 vol, H->s));
     }
-    if (norms) CK(launch_norm_reduce(H->partials, (int)H->nblocks, H->dnorm, H->s));
+    if (norms) LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->dnorm, H->s));
     return OHM_OK;
 }
 
@@ -635,7 +665,7 @@ int read_norms(ohm_hier *H, double out[4], int *err_flag) {
 
 template <typename T>
 int update_all(ohm_hier *H, double *B) {
-    for (auto &g : H->amr) CK(launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>(H->amrbuf.e, g, 3), H->s));
+    for (auto &g : H->amr) LAUNCH(H, OHM_K_UPDATE, g.n(), launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>(H->amrbuf.e, g, 3), H->s));
     return OHM_OK;
 }
 
@@ -747,6 +777,7 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
 
 void ohm_destroy(ohm_hier *h) {
     if (!h) return;
+    for (auto ev : h->prof_ev) cudaEventDestroy(ev);
     if (h->pool) cudaFree(h->pool);
     if (h->hnorm) cudaFreeHost(h->hnorm);
     delete h;
@@ -842,6 +873,42 @@ int ohm_op_vcycle(ohm_hier *h, const double *R_dev, double dt, double *e_dev) {
     if ((st = read_norms(h, nr, &ef))) return st;
     return ef ? OHM_ERR_INVALID : OHM_OK;
 }
+
+int ohm_prof_enable(ohm_hier *h, int kernel, int min_blocks, int max_launches) {
+    if (!h || max_launches < 0 || max_launches > (1 << 20)) return OHM_ERR_INVALID;
+    h->prof_kind = -1;
+    for (auto ev : h->prof_ev) cudaEventDestroy(ev);
+    h->prof_ev.clear();
+    h->prof_used = 0;
+    h->prof_launches = 0;
+    h->prof_cells = 0;
+    if (kernel < 0) return OHM_OK;
+    h->prof_ev.resize(2 * (size_t)max_launches);
+    for (auto &ev : h->prof_ev) CK(cudaEventCreate(&ev));
+    h->prof_kind = kernel;
+    h->prof_min_blocks = min_blocks;
+    return OHM_OK;
+}
+
+int ohm_prof_read(ohm_hier *h, double *total_ms, int64_t *launches, int64_t *cells) {
+    if (!h) return OHM_ERR_INVALID;
+    CK(cudaStreamSynchronize(h->s));
+    double tot = 0;
+    for (int i = 0; i + 1 < h->prof_used; i += 2) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, h->prof_ev[i], h->prof_ev[i + 1]));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = h->prof_launches;
+    if (cells) *cells = h->prof_cells;
+    h->prof_used = 0;
+    h->prof_launches = 0;
+    h->prof_cells = 0;
+    return OHM_OK;
+}
+
+int64_t ohm_launch_count(const ohm_hier *h) { return h ? h->nlaunch : -1; }
 
 int ohm_mg_grid_info(ohm_hier *h, int m, int32_t dims[3], int64_t *nblocks, int32_t *ijk) {
     if (!h || m < 0) return OHM_ERR_INVALID;

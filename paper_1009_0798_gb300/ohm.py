@@ -19,6 +19,8 @@ OHM_ERR_OOM = -4
 OHM_ERR_CUDA = -5
 OHM_FP64 = 0
 OHM_MIXED = 1
+OHM_K_COMPOSITE, OHM_K_SMOOTH, OHM_K_RESID_RESTRICT, OHM_K_PROLONG, OHM_K_GHOST = 0, 1, 2, 3, 4
+OHM_K_SYNC_DOWN, OHM_K_UPDATE, OHM_K_BOTTOM, OHM_K_NORM = 5, 6, 7, 8
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libohm.so")
 
@@ -70,6 +72,10 @@ def lib():
         L.ohm_op_grid_residual.argtypes = [vp, C.c_int, vp, vp, vp, dp, vp]
         L.ohm_op_grid_restrict.argtypes = [vp, C.c_int, vp, vp, C.c_int]
         L.ohm_op_grid_prolong_add.argtypes = [vp, C.c_int, vp, vp]
+        L.ohm_prof_enable.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.ohm_prof_read.argtypes = [vp, C.POINTER(dp), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.ohm_launch_count.argtypes = [vp]
+        L.ohm_launch_count.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -221,3 +227,17 @@ def ohm_op_grid_restrict(h: Hierarchy, m: int, fine, coarse, ncomp: int = 3) -> 
 
 def ohm_op_grid_prolong_add(h: Hierarchy, m: int, coarse, fine) -> None:
     _check(lib().ohm_op_grid_prolong_add(h.handle, m, _ptr(coarse), _ptr(fine)), "ohm_op_grid_prolong_add")
+
+
+def ohm_prof_enable(h: Hierarchy, kernel: int, min_blocks: int = 0, max_launches: int = 4096) -> None:
+    _check(lib().ohm_prof_enable(h.handle, int(kernel), int(min_blocks), int(max_launches)), "ohm_prof_enable")
+
+
+def ohm_prof_read(h: Hierarchy) -> dict:
+    ms, n, cells = C.c_double(), C.c_int64(), C.c_int64()
+    _check(lib().ohm_prof_read(h.handle, C.byref(ms), C.byref(n), C.byref(cells)), "ohm_prof_read")
+    return {"ms": ms.value, "launches": n.value, "cells": cells.value}
+
+
+def ohm_launch_count(h: Hierarchy) -> int:
+    return int(lib().ohm_launch_count(h.handle))

@@ -27,8 +27,8 @@ def amr_three_level(n=16):
 
 
 def rel_err(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
     den = np.sqrt(np.sum(b * b))
     return float(np.sqrt(np.sum((a - b) ** 2)) / (den if den > 0 else 1.0))
 
