@@ -367,7 +367,8 @@ def run_ours(args):
         try:
             from oracle import build as obuild
             obuild.build()
-            cpu = time_oracle_sample(wl, gpu_cycles=None)
+            cyc = fp64["cycles_per_step"][0] if fp64 else mixed["infos"][0]["cycles"]
+            cpu = time_oracle_sample(wl, gpu_cycles=cyc)
             cpu.pop("seconds_per_step", None)
         except Exception as ex:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}

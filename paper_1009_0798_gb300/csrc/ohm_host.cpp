@@ -81,6 +81,7 @@ struct ohm_hier {
     double *reg = nullptr, *partials = nullptr, *dnorm = nullptr;
     int *d_rsrc = nullptr, *d_err = nullptr;
     void *ghostE = nullptr, *ghostEtaT = nullptr;
+    void *rout = nullptr, *eacc = nullptr;  // mixed precision: float32 outer residual, inner correction
     Buffers amrbuf;               // AMR levels, all blocks
     std::vector<Buffers> mgbuf;   // blocked multigrid grids
     Buffers smallbuf[MAX_SMALL];  // small grids (t stored in e2)
@@ -358,6 +359,10 @@ int allocate(ohm_hier *H, std::string &err) {
     want(&H->ghostE, (size_t)H->nslot * 3 * T3 * tsz);
     if (H->mixed) want(&H->ghostEtaT, (size_t)H->nslot * T3 * tsz);
     want(&H->amrbuf.r, n * 3 * B3 * tsz);
+    if (H->mixed) {
+        want(&H->rout, n * 3 * B3 * tsz);
+        want(&H->eacc, n * 3 * B3 * tsz);
+    }
     want(&H->amrbuf.e, n * 3 * B3 * tsz);
     want(&H->amrbuf.e2, n * 3 * B3 * tsz);
     want(&H->amrbuf.inv, n * 3 * B3 * tsz);
@@ -634,18 +639,44 @@ int fill_ghosts_B(ohm_hier *H, const double *B) {
 }
 
 // out = a X + c divF(X) + d Y on leaf blocks of every level (finest first, so refluxed
-// fine fluxes are in the registers before the coarser level reads them).
-template <typename TO>
-int composite(ohm_hier *H, const double *X, const double *Y, double a, double c, double dcoef, TO *out, bool norms) {
+// fine fluxes are in the registers before the coarser level reads them), computed in TC.
+template <typename TC, typename TO>
+int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta, double a, double c,
+                double dcoef, TO *out, TO *out2, bool norms) {
     for (int l = H->nlev - 1; l >= 0; l--) {
         const HGrid &g = H->amr[l];
         double vol = g.h * g.h * g.h;
-        LAUNCH(H, OHM_K_COMPOSITE, g.n(), launch_composite<TO>(g.dev, amr_ptr<double>((void *)X, g, 3), Y ? amr_ptr<double>((void *)Y, g, 3) : nullptr,
-                                amr_ptr<double>(H->eta64, g, 1), H->ghostB, H->ghostEta64, a, c, dcoef,
-                                out + (size_t)g.off * 3 * B3, H->reg, H->d_rsrc, norms ? H->partials + (size_t)g.off * 3 : nullptr,
-                                vol, H->s));
+        const size_t o3 = (size_t)g.off * 3 * B3;
+        LAUNCH(H, OHM_K_COMPOSITE, g.n(),
+               (launch_composite<TC, TO>(g.dev, X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta, a, c,
+                                         dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
+                                         norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s)));
     }
     if (norms) LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->dnorm, H->s));
+    return OHM_OK;
+}
+
+// float64 composite operator on B-like fields (eta and ghosts of the state)
+template <typename TO>
+int composite(ohm_hier *H, const double *X, const double *Y, double a, double c, double dcoef, TO *out, bool norms,
+              TO *out2 = nullptr) {
+    return composite_t<double, TO>(H, X, Y, H->eta64, H->ghostB, H->ghostEta64, a, c, dcoef, out, out2, norms);
+}
+
+template <typename T>
+int sync_down_t(ohm_hier *H, T *x) {
+    for (int l = H->nlev - 2; l >= 0; l--)
+        LAUNCH(H, OHM_K_SYNC_DOWN, H->amr[l].n(),
+               launch_sync_down<T>(H->amr[l].dev, amr_ptr<T>(x, H->amr[l], 3), amr_ptr<T>(x, H->amr[l + 1], 3), H->s));
+    return OHM_OK;
+}
+
+template <typename T>
+int fill_ghosts_t(ohm_hier *H, const T *x, T *ghost) {
+    for (int l = 1; l < H->nlev; l++)
+        LAUNCH(H, OHM_K_GHOST, H->amr[l].nslot,
+               (launch_ghost_fill<T, T>(H->amr[l].dev, H->amr[l - 1].dev, amr_ptr<T>((void *)x, H->amr[l - 1], 3), 3,
+                                        ghost, H->d_err, H->s)));
     return OHM_OK;
 }
 
@@ -664,8 +695,9 @@ int read_norms(ohm_hier *H, double out[4], int *err_flag) {
 }
 
 template <typename T>
-int update_all(ohm_hier *H, double *B) {
-    for (auto &g : H->amr) LAUNCH(H, OHM_K_UPDATE, g.n(), launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>(H->amrbuf.e, g, 3), H->s));
+int update_all(ohm_hier *H, double *B, const T *e) {
+    for (auto &g : H->amr)
+        LAUNCH(H, OHM_K_UPDATE, g.n(), launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>((void *)e, g, 3), H->s));
     return OHM_OK;
 }
 
@@ -699,13 +731,80 @@ int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *
             break;
         }
         if ((st = vcycle<T>(H, lamdt))) return st;
-        if ((st = update_all<T>(H, B))) return st;
+        if ((st = update_all<T>(H, B, (const T *)H->amrbuf.e))) return st;
         if ((st = sync_down(H, B))) return st;
         if ((st = fill_ghosts_B(H, B))) return st;
         it++;
     }
     if (stats) {
         stats->cycles = it;
+        stats->converged = (result == OHM_OK && tol >= 0) ? 1 : 0;
+        stats->rel_l2_initial = first;
+        stats->rel_l2 = nr[0];
+        stats->max_abs = nr[1];
+    }
+    return result;
+}
+
+// Mixed precision as iterative refinement around Eqs. 16-18: the float64 residual
+// R = S - L B is handed to a float32 multigrid solve of L e = R (V-cycles, each followed by
+// the float32 composite residual of the correction equation) until that inner residual has
+// dropped by max(1e-4, 0.3 tol / ||R||/||S||), then B += e in float64.  max_outer bounds the
+// total number of V-cycles of the step.
+constexpr double INNER_FLOOR = 1e-4;
+
+int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *stats) {
+    using T = float;
+    const double lam = H->d.lambda, lamdt = lam * dt;
+    int st;
+    if ((st = prepare_dt<T>(H, dt))) return st;
+    CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->s));
+    if ((st = sync_down(H, B))) return st;
+    if ((st = fill_ghosts_B(H, B))) return st;
+    if ((st = composite<double>(H, B, nullptr, 1.0, -(1.0 - lam) * dt, 0.0, H->S, false))) return st;
+    H->has_S = true;
+    H->last_dt = dt;
+    T *r = (T *)H->amrbuf.r, *e = (T *)H->amrbuf.e, *rout = (T *)H->rout, *eacc = (T *)H->eacc;
+    const size_t nbytes = (size_t)H->nblocks * 3 * B3 * sizeof(T);
+    int cycles = 0, result = OHM_OK;
+    double nr[4] = {0, 0, 0, 0}, first = 0;
+    for (int outer = 0;; outer++) {
+        if ((st = composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, rout))) return st;
+        int ef = 0;
+        if ((st = read_norms(H, nr, &ef))) return st;
+        if (ef) return OHM_ERR_INVALID;
+        if (outer == 0) first = nr[0];
+        if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) {
+            result = OHM_ERR_NONFINITE;
+            break;
+        }
+        if (tol >= 0 && nr[0] <= tol) break;
+        if (cycles >= H->d.max_outer) {
+            result = tol >= 0 ? OHM_ERR_NOT_CONVERGED : OHM_OK;
+            break;
+        }
+        const double target = tol >= 0 ? std::max(INNER_FLOOR, 0.3 * tol / std::max(nr[0], 1e-300)) : INNER_FLOOR;
+        CK(cudaMemsetAsync(eacc, 0, nbytes, H->s));
+        while (cycles < H->d.max_outer) {
+            if ((st = vcycle<T>(H, lamdt))) return st;
+            for (auto &g : H->amr)
+                LAUNCH(H, OHM_K_UPDATE, g.n(), launch_axpy_leaf<T>(g.dev, amr_ptr<T>(eacc, g, 3), amr_ptr<T>(e, g, 3), H->s));
+            cycles++;
+            if ((st = sync_down_t<T>(H, eacc))) return st;
+            if ((st = fill_ghosts_t<T>(H, eacc, (T *)H->ghostE))) return st;
+            if ((st = composite_t<T, T>(H, eacc, rout, (const T *)H->amrbuf.eta, (const T *)H->ghostE,
+                                        (const T *)H->ghostEtaT, -1.0, -lamdt, 1.0, r, (T *)nullptr, true)))
+                return st;
+            double ni[4];
+            if ((st = read_norms(H, ni, &ef))) return st;
+            if (!std::isfinite(ni[0]) || ni[0] <= target) break;
+        }
+        if ((st = update_all<T>(H, B, eacc))) return st;
+        if ((st = sync_down(H, B))) return st;
+        if ((st = fill_ghosts_B(H, B))) return st;
+    }
+    if (stats) {
+        stats->cycles = cycles;
         stats->converged = (result == OHM_OK && tol >= 0) ? 1 : 0;
         stats->rel_l2_initial = first;
         stats->rel_l2 = nr[0];
@@ -799,7 +898,7 @@ int ohm_cn_step(ohm_hier *h, double *B_dev, const double *eta_dev, double dt, do
         if (st) return st;
     }
     if (!h->eta_set) return OHM_ERR_INVALID;
-    return h->mixed ? cn_step_impl<float>(h, B_dev, dt, tol, stats) : cn_step_impl<double>(h, B_dev, dt, tol, stats);
+    return h->mixed ? cn_step_mixed(h, B_dev, dt, tol, stats) : cn_step_impl<double>(h, B_dev, dt, tol, stats);
 }
 
 int ohm_residual_norm(ohm_hier *h, const double *B_dev, double *rel_l2, double *max_abs) {

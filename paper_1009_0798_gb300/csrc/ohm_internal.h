@@ -50,11 +50,12 @@ struct SmallDev {
 // reading ghosts from Gx (level ghost slots) and eta ghosts from Geta; writes face fluxes to
 // registers for faces without a same-level neighbour and reads refluxed fluxes from the
 // finer level for faces next to covered blocks; optional per-block norm partials.
-template <typename TO>
-cudaError_t launch_composite(const GridDev &g, const double *X, const double *Y, const double *eta,
-                             const double *Gx, const double *Geta, double a, double c, double d,
-                             TO *out, double *reg, const int *rsrc_tab, double *partials,
-                             double vol, cudaStream_t s);
+// Computed in TC; out (and out2 when not null) receive the result as TO.
+template <typename TC, typename TO>
+cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const TC *eta, const TC *Gx,
+                             const TC *Geta, double a, double c, double d, TO *out, TO *out2,
+                             double *reg, const int *rsrc_tab, double *partials, double vol,
+                             cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta,
@@ -81,7 +82,11 @@ template <typename TS, typename TD>
 cudaError_t launch_ghost_fill(const GridDev &g, const GridDev &gc, const TS *coarse, int ncomp,
                               TD *ghost, int *err, cudaStream_t s);
 
-cudaError_t launch_sync_down(const GridDev &gc, double *Bc, const double *Bf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sync_down(const GridDev &gc, T *Bc, const T *Bf, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_axpy_leaf(const GridDev &g, T *x, const T *y, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_update(const GridDev &g, double *B, const T *e, cudaStream_t s);

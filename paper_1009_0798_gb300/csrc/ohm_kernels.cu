@@ -128,17 +128,19 @@ __device__ __forceinline__ T block_max(T v, T *red) {
 }
 
 // ------------------------------------------------------------------ composite operator
-template <typename TO>
-__global__ void __launch_bounds__(512) k_composite(GridDev g, const double *__restrict__ X,
-                                                   const double *__restrict__ Y, const double *__restrict__ eta,
-                                                   const double *__restrict__ Gx, const double *__restrict__ Geta,
-                                                   double a, double coef, double d, TO *__restrict__ out,
+// Computed in TC (float64 for the outer residual and the source, float32 for the inner
+// residual of mixed precision); refluxed fluxes travel through float64 registers.
+template <typename TC, typename TO>
+__global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restrict__ X, const TC *__restrict__ Y,
+                                                   const TC *__restrict__ eta, const TC *__restrict__ Gx,
+                                                   const TC *__restrict__ Geta, TC a, TC coef, TC d,
+                                                   TO *__restrict__ out, TO *__restrict__ out2,
                                                    double *__restrict__ reg, const int *__restrict__ rsrc_tab,
                                                    double *__restrict__ partials, double vol) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *tB = reinterpret_cast<double *>(smem_raw);
-    double *tE = tB + 3 * T3;
-    double *phi = tE + T3;
+    TC *tB = reinterpret_cast<TC *>(smem_raw);
+    TC *tE = tB + 3 * T3;
+    TC *phi = tE + T3;
     __shared__ double red[32];
     const int b = blockIdx.x;
     if (g.covered && g.covered[b]) {
@@ -146,8 +148,8 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const double *__re
         return;
     }
     const int slot = g.gslot ? g.gslot[b] : -1;
-    load_tile<double, 3>(tB, X, b, g.nbr, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
-    load_tile<double, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    load_tile<TC, 3>(tB, X, b, g.nbr, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
+    load_tile<TC, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     all_faces(tB, tE, phi);
     __syncthreads();
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const double *__re
             int ax = s >> 1, hi = s & 1;
             for (int q = threadIdx.x; q < 128; q += blockDim.x) {
                 int comp = q >> 6, uv = q & 63;
-                reg[(size_t)slotr * 128 + q] = phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, uv & 7, uv >> 3)] * inv2h;
+                reg[(size_t)slotr * 128 + q] = (double)phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, uv & 7, uv >> 3)] * inv2h;
             }
         }
     }
@@ -176,30 +178,33 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const double *__re
                 const double *R = reg + (size_t)fslot * 128 + comp * 64;
                 int fu = 2 * (u & 3), fv = 2 * (v & 3);
                 double m = 0.25 * ((R[fv * 8 + fu] + R[fv * 8 + fu + 1]) + (R[(fv + 1) * 8 + fu] + R[(fv + 1) * 8 + fu + 1]));
-                phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, u, v)] = m * (2.0 * g.h);
+                phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, u, v)] = (TC)(m * (2.0 * g.h));
             }
         }
     }
     __syncthreads();
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-    double dv[3];
+    TC dv[3];
     cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
-    double sr = 0.0, ss = 0.0, mx = 0.0;
+    TC sr = 0, ss = 0, mx = 0;
     const int p = tix(i + 1, j + 1, k + 1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         size_t id = ((size_t)b * 3 + c) * B3 + t;
-        double y = Y ? Y[id] : 0.0;
-        double o = a * tB[c * T3 + p] + coef * dv[c] + d * y;
+        TC y = Y ? Y[id] : TC(0);
+        TC o = a * tB[c * T3 + p] + coef * dv[c] + d * y;
         out[id] = (TO)o;
-        sr += o * o;
-        ss += y * y;
-        mx = fmax(mx, fabs(o));
+        if (out2) out2[id] = (TO)o;
+        if (partials) {
+            sr += o * o;
+            ss += y * y;
+            mx = fmax(mx, fabs(o));
+        }
     }
     if (partials) {
-        double s1 = block_sum(sr, red);
-        double s2 = block_sum(ss, red);
-        double s3 = block_max(mx, red);
+        double s1 = block_sum((double)sr, red);
+        double s2 = block_sum((double)ss, red);
+        double s3 = block_max((double)mx, red);
         if (threadIdx.x == 0) {
             partials[b * 3 + 0] = s1 * vol;
             partials[b * 3 + 1] = s2 * vol;
@@ -208,27 +213,29 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const double *__re
     }
 }
 
-template <typename TO>
-cudaError_t launch_composite(const GridDev &g, const double *X, const double *Y, const double *eta,
-                             const double *Gx, const double *Geta, double a, double c, double d, TO *out,
-                             double *reg, const int *rsrc_tab, double *partials, double vol, cudaStream_t s) {
+template <typename TC, typename TO>
+cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta,
+                             double a, double c, double d, TO *out, TO *out2, double *reg, const int *rsrc_tab,
+                             double *partials, double vol, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
-    const size_t sm = (4 * T3 + 6 * 576) * sizeof(double);
+    const size_t sm = (4 * T3 + 6 * 576) * sizeof(TC);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_composite<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_composite<TC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
     double coef = c / (2.0 * g.h * g.h);
-    k_composite<TO><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, reg, rsrc_tab, partials, vol);
+    k_composite<TC, TO><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg, rsrc_tab,
+                                                partials, vol);
     return cudaGetLastError();
 }
-template cudaError_t launch_composite<double>(const GridDev &, const double *, const double *, const double *,
-                                              const double *, const double *, double, double, double, double *,
-                                              double *, const int *, double *, double, cudaStream_t);
-template cudaError_t launch_composite<float>(const GridDev &, const double *, const double *, const double *,
-                                             const double *, const double *, double, double, double, float *,
-                                             double *, const int *, double *, double, cudaStream_t);
+#define INST_COMPOSITE(TC, TO)                                                                                        \
+    template cudaError_t launch_composite<TC, TO>(const GridDev &, const TC *, const TC *, const TC *, const TC *,     \
+                                                  const TC *, double, double, double, TO *, TO *, double *, const int *, \
+                                                  double *, double, cudaStream_t);
+INST_COMPOSITE(double, double)
+INST_COMPOSITE(double, float)
+INST_COMPOSITE(float, float)
 
 // ------------------------------------------------------------------ red-black smoothing
 // One colour pass (Eq. 19): colour cells get e + (r - e - lamdt divF(e)) * inv, the other
@@ -566,7 +573,8 @@ template cudaError_t launch_ghost_fill<float, float>(const GridDev &, const Grid
                                                      int *, cudaStream_t);
 
 // ------------------------------------------------------------------ sync down, update
-__global__ void __launch_bounds__(512) k_sync_down(GridDev gc, double *__restrict__ Bc, const double *__restrict__ Bf) {
+template <typename T>
+__global__ void __launch_bounds__(512) k_sync_down(GridDev gc, T *__restrict__ Bc, const T *__restrict__ Bf) {
     const int b = blockIdx.x;
     if (!gc.covered[b]) return;
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
@@ -575,20 +583,44 @@ __global__ void __launch_bounds__(512) k_sync_down(GridDev gc, double *__restric
     const int fi = 2 * (i & 3), fj = 2 * (j & 3), fk = 2 * (k & 3);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const double *src = Bf + ((size_t)ch * 3 + c) * B3;
-        double s = 0.0;
+        const T *src = Bf + ((size_t)ch * 3 + c) * B3;
+        T s = 0;
         for (int dk = 0; dk < 2; dk++)
             for (int dj = 0; dj < 2; dj++)
                 for (int di = 0; di < 2; di++) s += src[((fk + dk) * 8 + fj + dj) * 8 + fi + di];
-        Bc[((size_t)b * 3 + c) * B3 + t] = s / 8.0;
+        Bc[((size_t)b * 3 + c) * B3 + t] = s / T(8);
     }
 }
 
-cudaError_t launch_sync_down(const GridDev &gc, double *Bc, const double *Bf, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_sync_down(const GridDev &gc, T *Bc, const T *Bf, cudaStream_t s) {
     if (gc.nblk == 0) return cudaSuccess;
-    k_sync_down<<<gc.nblk, 512, 0, s>>>(gc, Bc, Bf);
+    k_sync_down<T><<<gc.nblk, 512, 0, s>>>(gc, Bc, Bf);
     return cudaGetLastError();
 }
+template cudaError_t launch_sync_down<double>(const GridDev &, double *, const double *, cudaStream_t);
+template cudaError_t launch_sync_down<float>(const GridDev &, float *, const float *, cudaStream_t);
+
+// x += y on leaf blocks (inner correction accumulation)
+template <typename T>
+__global__ void __launch_bounds__(512) k_axpy_leaf(GridDev g, T *__restrict__ x, const T *__restrict__ y) {
+    const int b = blockIdx.x;
+    if (g.covered && g.covered[b]) return;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        size_t id = ((size_t)b * 3 + c) * B3 + threadIdx.x;
+        x[id] += y[id];
+    }
+}
+
+template <typename T>
+cudaError_t launch_axpy_leaf(const GridDev &g, T *x, const T *y, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    k_axpy_leaf<T><<<g.nblk, 512, 0, s>>>(g, x, y);
+    return cudaGetLastError();
+}
+template cudaError_t launch_axpy_leaf<float>(const GridDev &, float *, const float *, cudaStream_t);
+template cudaError_t launch_axpy_leaf<double>(const GridDev &, double *, const double *, cudaStream_t);
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_update(GridDev g, double *__restrict__ B, const T *__restrict__ e) {
