@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -559,6 +560,16 @@ GridRef base_ref(ohm_hier *H, int m) {  // m = 0: AMR level 0
 
 template <typename T>
 int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
+    if (std::is_same<T, float>::value && G.g->nslot == 0) {
+        // float32 grids with every neighbour: one fused red+black launch per sweep
+        for (int i = 0; i < n; i++) {
+            const T *src = (const T *)((i & 1) ? G.e2 : G.e);
+            T *dst = (T *)((i & 1) ? G.e : G.e2);
+            LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb<T>(G.g->dev, src, dst, (const T *)G.r, (const T *)G.eta, lamdt, H->s));
+        }
+        if (n & 1) CK(cudaMemcpyAsync(G.e, G.e2, (size_t)G.g->n() * 3 * B3 * sizeof(T), cudaMemcpyDeviceToDevice, H->s));
+        return OHM_OK;
+    }
     for (int i = 0; i < n; i++) {
         LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(G.g->dev, (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
                             (const T *)G.Ge, (const T *)G.Geta, lamdt, 0, H->s));

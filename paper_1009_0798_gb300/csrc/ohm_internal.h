@@ -62,6 +62,12 @@ cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r,
                           const T *inv, const T *Ge, const T *Geta, double lamdt, int colour,
                           cudaStream_t s);
 
+// One full red + black sweep in one launch (grids without coarse-fine ghosts), inverse
+// diagonal formed on the fly; e_in != e_out.
+template <typename T>
+cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta, double lamdt,
+                             cudaStream_t s);
+
 // t = r - (e + lamdt divF(e)); restricted (mean of 8) into the coarser grid: blocked
 // (coarse != nullptr, by parent/octant) or lexicographic (lex != nullptr, dims ldims).
 template <typename T>

@@ -62,6 +62,24 @@ __device__ __forceinline__ void face_phi(const T *__restrict__ tB, const T *__re
     phi2 = es * (T(0.25) * t2 - n2);
 }
 
+// Same for a tile whose components are cs elements apart; the two flux components are the
+// axes other than a in ascending order, with tile strides s1 and s2.
+template <typename T>
+__device__ __forceinline__ void face_phi_s(const T *__restrict__ tB, const T *__restrict__ tE, int p, int a, int sa,
+                                           int s1, int s2, int cs, T &phi1, T &phi2) {
+    const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
+    const T es = tE[p] + tE[p + sa];
+    const T *Ba = tB + a * cs;
+    const T *B1 = tB + b1 * cs;
+    const T *B2 = tB + b2 * cs;
+    T n1 = B1[p + sa] - B1[p];
+    T t1 = (Ba[p + sa + s1] + Ba[p + s1]) - (Ba[p + sa - s1] + Ba[p - s1]);
+    phi1 = es * (T(0.25) * t1 - n1);
+    T n2 = B2[p + sa] - B2[p];
+    T t2 = (Ba[p + sa + s2] + Ba[p + s2]) - (Ba[p + sa - s2] + Ba[p - s2]);
+    phi2 = es * (T(0.25) * t2 - n2);
+}
+
 // All 1728 face fluxes of a staged block into phi[3 axes][2 comps][576]:
 //   x faces (k*8+j)*9+fi, y faces (k*9+fj)*8+i, z faces (fk*8+j)*8+i.
 template <typename T>
@@ -293,6 +311,123 @@ template cudaError_t launch_smooth<double>(const GridDev &, const double *, doub
                                            const double *, const double *, const double *, double, int, cudaStream_t);
 template cudaError_t launch_smooth<float>(const GridDev &, const float *, float *, const float *, const float *,
                                           const float *, const float *, const float *, double, int, cudaStream_t);
+
+// ------------------------------------------------------------------ fused red + black sweep
+// One full red-black sweep in one launch, for grids whose blocks have every neighbour (no
+// coarse-fine ghosts).  The block and a 2-cell halo (12^3, all 26 neighbours) are staged;
+// red cells of the block and of its 1-cell ring get their update from the pre-sweep state,
+// then the block's black cells are updated from the post-red state.  The ring updates are
+// the ones the neighbouring blocks compute, in the same order with the same arithmetic, so
+// the result equals two global colour passes.  The inverse diagonal is formed on the fly
+// from eta (Eqs. 21-23).  e_in and e_out are distinct buffers.
+constexpr int RS = 12, R3 = RS * RS * RS;
+__device__ __forceinline__ int rix(int i, int j, int k) { return (k * RS + j) * RS + i; }
+
+template <typename T>
+__device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
+                                          const T rr[3], T out[3]) {
+    T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
+    face_phi_s(tB, tE, p - 1, 0, 1, RS, RS * RS, R3, xl1, xl2);
+    face_phi_s(tB, tE, p, 0, 1, RS, RS * RS, R3, xh1, xh2);
+    face_phi_s(tB, tE, p - RS, 1, RS, 1, RS * RS, R3, yl1, yl2);
+    face_phi_s(tB, tE, p, 1, RS, 1, RS * RS, R3, yh1, yh2);
+    face_phi_s(tB, tE, p - RS * RS, 2, RS * RS, 1, RS, R3, zl1, zl2);
+    face_phi_s(tB, tE, p, 2, RS * RS, 1, RS, R3, zh1, zh2);
+    const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
+    const T e0 = tE[p];
+    const T sx = e0 + T(0.5) * (tE[p + 1] + tE[p - 1]);
+    const T sy = e0 + T(0.5) * (tE[p + RS] + tE[p - RS]);
+    const T sz = e0 + T(0.5) * (tE[p + RS * RS] + tE[p - RS * RS]);
+    const T al[3] = {lh2 * (sy + sz), lh2 * (sz + sx), lh2 * (sx + sy)};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        T ev = tB[c * R3 + p];
+        T res = rr[c] - ev - coef * dv[c];
+        out[c] = ev + res / (T(1) + al[c]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restrict__ e_in, T *__restrict__ e_out,
+                                                   const T *__restrict__ r, const T *__restrict__ eta, T coef, T lh2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tB = reinterpret_cast<T *>(smem_raw);  // [3][12^3]
+    T *tE = tB + 3 * R3;                      // [12^3]
+    const int b = blockIdx.x;
+    for (int idx = threadIdx.x; idx < R3; idx += blockDim.x) {
+        const int ti = idx % RS, tj = (idx / RS) % RS, tk = idx / (RS * RS);
+        const int li = ti - 2, lj = tj - 2, lk = tk - 2;
+        const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int src = (di | dj | dk) ? __ldg(g.nbr + b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1)) : b;
+        const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
+        const T *p = e_in + (size_t)src * 3 * B3 + off;
+        tB[idx] = p[0];
+        tB[R3 + idx] = p[B3];
+        tB[2 * R3 + idx] = p[2 * B3];
+        tE[idx] = eta[(size_t)src * B3 + off];
+    }
+    __syncthreads();
+    // red cells ((i+j+k) even) of the block and its face/edge ring: the 10^3 box without corners
+    // each of the 256 threads owns box positions q = t + 256 s, s = 0..3 (launch uses 256)
+    T nv[4][3];
+    int np[4];
+#pragma unroll
+    for (int s4 = 0; s4 < 4; s4++) {
+        np[s4] = -1;
+        const int q = threadIdx.x + 256 * s4;
+        if (q >= T3) continue;
+        const int ti = q % TS, tj = (q / TS) % TS, tk = q / (TS * TS);
+        const int li = ti - 1, lj = tj - 1, lk = tk - 1;
+        if (((li + lj + lk) & 1) != 0) continue;
+        const int nout = (li < 0 || li > 7) + (lj < 0 || lj > 7) + (lk < 0 || lk > 7);
+        if (nout == 3) continue;
+        const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int src = (di | dj | dk) ? __ldg(g.nbr + b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1)) : b;
+        const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
+        const T rr[3] = {r[(size_t)src * 3 * B3 + off], r[(size_t)src * 3 * B3 + B3 + off], r[(size_t)src * 3 * B3 + 2 * B3 + off]};
+        np[s4] = rix(li + 2, lj + 2, lk + 2);
+        rb_update(tB, tE, np[s4], coef, lh2, rr, nv[s4]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s4 = 0; s4 < 4; s4++)
+        if (np[s4] >= 0)
+            for (int c = 0; c < 3; c++) tB[c * R3 + np[s4]] = nv[s4][c];
+    __syncthreads();
+    // black cells of the block, one per thread, then the whole block is written out
+    const int t = threadIdx.x;
+    const int k = t >> 5, j = (t >> 2) & 7;
+    const int ib = 2 * (t & 3) + ((j + k + 1) & 1), ir = 2 * (t & 3) + ((j + k) & 1);
+    const int cb = (k * 8 + j) * 8 + ib, cr = (k * 8 + j) * 8 + ir;
+    const T rr[3] = {r[(size_t)b * 3 * B3 + cb], r[(size_t)b * 3 * B3 + B3 + cb], r[(size_t)b * 3 * B3 + 2 * B3 + cb]};
+    T out[3];
+    const int pb = rix(ib + 2, j + 2, k + 2), pr = rix(ir + 2, j + 2, k + 2);
+    rb_update(tB, tE, pb, coef, lh2, rr, out);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        e_out[((size_t)b * 3 + c) * B3 + cb] = out[c];
+        e_out[((size_t)b * 3 + c) * B3 + cr] = tB[c * R3 + pr];
+    }
+}
+
+template <typename T>
+cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta, double lamdt,
+                             cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    const size_t sm = 4 * R3 * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_smooth_rb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    k_smooth_rb<T><<<g.nblk, 256, sm, s>>>(g, e_in, e_out, r, eta, (T)(lamdt / (2.0 * g.h * g.h)),
+                                          (T)(lamdt / (g.h * g.h)));
+    return cudaGetLastError();
+}
+template cudaError_t launch_smooth_rb<float>(const GridDev &, const float *, float *, const float *, const float *, double,
+                                             cudaStream_t);
+template cudaError_t launch_smooth_rb<double>(const GridDev &, const double *, double *, const double *, const double *,
+                                              double, cudaStream_t);
 
 // ------------------------------------------------------------------ inverse diagonal
 // inv_c = 1 / (1 + alpha_c), alpha_c = lamdt/h^2 sum_{a != c} (eta_{-1/2} + eta_{+1/2})
