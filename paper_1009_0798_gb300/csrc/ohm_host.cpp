@@ -79,7 +79,7 @@ struct ohm_hier {
     // device memory (one pool)
     void *pool = nullptr;
     double *S = nullptr, *eta64 = nullptr, *Bscr = nullptr, *ghostB = nullptr, *ghostEta64 = nullptr;
-    double *reg = nullptr, *partials = nullptr, *dnorm = nullptr;
+    double *reg = nullptr, *partials = nullptr, *dnorm = nullptr, *redscr = nullptr;
     int *d_rsrc = nullptr, *d_err = nullptr;
     void *ghostE = nullptr, *ghostEtaT = nullptr;
     void *rout = nullptr, *eacc = nullptr;  // mixed precision: float32 outer residual, inner correction
@@ -357,6 +357,7 @@ int allocate(ohm_hier *H, std::string &err) {
     want((void **)&H->reg, (size_t)H->nreg * 128 * 8);
     want((void **)&H->partials, n * 3 * 8);
     want((void **)&H->dnorm, 64);
+    want((void **)&H->redscr, NORM_SCRATCH_BYTES);
     want(&H->ghostE, (size_t)H->nslot * 3 * T3 * tsz);
     if (H->mixed) want(&H->ghostEtaT, (size_t)H->nslot * T3 * tsz);
     want(&H->amrbuf.r, n * 3 * B3 * tsz);
@@ -402,7 +403,8 @@ int allocate(ohm_hier *H, std::string &err) {
         H->ghostEtaT = H->ghostEta64;
         H->amrbuf.eta = H->eta64;
     }
-    if (cudaMemcpy(base, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemset(H->redscr, 0, NORM_SCRATCH_BYTES) != cudaSuccess ||
+        cudaMemcpy(base, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         err = "table upload failed";
         return OHM_ERR_CUDA;
     }
@@ -663,7 +665,7 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
                                          dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
                                          norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s)));
     }
-    if (norms) LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->dnorm, H->s));
+    if (norms) LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->redscr, H->dnorm, H->s));
     return OHM_OK;
 }
 

@@ -101,7 +101,9 @@ template <typename T>
 cudaError_t launch_invdiag(const GridDev &g, const T *eta, const T *Geta, double lamdt, T *inv,
                            cudaStream_t s);
 
-cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *out, cudaStream_t s);
+// scratch: NORM_SCRATCH_BYTES, zero-filled once before first use (it resets itself)
+constexpr size_t NORM_SCRATCH_BYTES = 128 * 3 * sizeof(double) + 16;
+cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post,

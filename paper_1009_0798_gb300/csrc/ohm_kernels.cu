@@ -121,27 +121,34 @@ __device__ __forceinline__ int plane_face(int a, int hi, int u, int v) {
     return ((hi ? 8 : 0) * 8 + v) * 8 + u;
 }
 
+// Block-wide sum / max in a fixed order (deterministic); the result is valid in thread 0.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[w] = v;
     __syncthreads();
     T s = 0;
-    for (int i = 0; i < nw; i++) s += red[i];
+    if (w == 0) {
+        s = threadIdx.x < nw ? red[threadIdx.x] : T(0);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
     return s;
 }
 
 template <typename T>
 __device__ __forceinline__ T block_max(T v, T *red) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[w] = v;
     __syncthreads();
     T s = 0;
-    for (int i = 0; i < nw; i++) s = fmax(s, red[i]);
+    if (w == 0) {
+        s = threadIdx.x < nw ? red[threadIdx.x] : T(0);
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    }
     return s;
 }
 
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
     TC *tB = reinterpret_cast<TC *>(smem_raw);
     TC *tE = tB + 3 * T3;
     TC *phi = tE + T3;
-    __shared__ double red[32];
+    __shared__ TC red[32];
     const int b = blockIdx.x;
     if (g.covered && g.covered[b]) {
         if (partials && threadIdx.x < 3) partials[b * 3 + threadIdx.x] = 0.0;
@@ -220,13 +227,13 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
         }
     }
     if (partials) {
-        double s1 = block_sum((double)sr, red);
-        double s2 = block_sum((double)ss, red);
-        double s3 = block_max((double)mx, red);
+        TC s1 = block_sum(sr, red);
+        TC s2 = block_sum(ss, red);
+        TC s3 = block_max(mx, red);
         if (threadIdx.x == 0) {
-            partials[b * 3 + 0] = s1 * vol;
-            partials[b * 3 + 1] = s2 * vol;
-            partials[b * 3 + 2] = s3;
+            partials[b * 3 + 0] = (double)s1 * vol;
+            partials[b * 3 + 1] = (double)s2 * vol;
+            partials[b * 3 + 2] = (double)s3;
         }
     }
 }
@@ -789,11 +796,18 @@ cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// deterministic reduction of per-block partials {sum R^2 dV, sum S^2 dV, max |R|}
-__global__ void __launch_bounds__(1024) k_norm_reduce(const double *__restrict__ part, int n, double *__restrict__ out) {
+// Deterministic reduction of per-block partials {sum R^2 dV, sum S^2 dV, max |R|}: every
+// thread block folds a fixed contiguous chunk in a fixed order, and the last block to finish
+// (atomic ticket) folds the per-chunk results in chunk order.
+constexpr int NRED = 128;
+__global__ void __launch_bounds__(256) k_norm_reduce(const double *__restrict__ part, int n, double *__restrict__ chunk,
+                                                     unsigned int *__restrict__ ticket, double *__restrict__ out) {
     __shared__ double red[32];
+    __shared__ bool last;
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * per, hi = min(n, lo + per);
     double a = 0.0, b = 0.0, m = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         a += part[i * 3 + 0];
         b += part[i * 3 + 1];
         m = fmax(m, part[i * 3 + 2]);
@@ -802,14 +816,36 @@ __global__ void __launch_bounds__(1024) k_norm_reduce(const double *__restrict__
     double sb = block_sum(b, red);
     double sm = block_max(m, red);
     if (threadIdx.x == 0) {
+        chunk[blockIdx.x * 3 + 0] = sa;
+        chunk[blockIdx.x * 3 + 1] = sb;
+        chunk[blockIdx.x * 3 + 2] = sm;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    a = b = m = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        a += __ldcg(chunk + i * 3 + 0);
+        b += __ldcg(chunk + i * 3 + 1);
+        m = fmax(m, __ldcg(chunk + i * 3 + 2));
+    }
+    sa = block_sum(a, red);
+    sb = block_sum(b, red);
+    sm = block_max(m, red);
+    if (threadIdx.x == 0) {
         out[0] = sa;
         out[1] = sb;
         out[2] = sm;
+        *ticket = 0u;
     }
 }
 
-cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *out, cudaStream_t s) {
-    k_norm_reduce<<<1, 1024, 0, s>>>(partials, nblocks, out);
+// scratch: NRED * 3 doubles followed by one unsigned ticket (zero on first use)
+cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s) {
+    int grid = nblocks < NRED * 64 ? (nblocks + 63) / 64 : NRED;
+    k_norm_reduce<<<grid, 256, 0, s>>>(partials, nblocks, scratch, (unsigned int *)(scratch + 3 * NRED), out);
     return cudaGetLastError();
 }
 
