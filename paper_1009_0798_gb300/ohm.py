@@ -241,3 +241,25 @@ def ohm_prof_read(h: Hierarchy) -> dict:
 
 def ohm_launch_count(h: Hierarchy) -> int:
     return int(lib().ohm_launch_count(h.handle))
+
+
+def ohm_residual_static(base_cells, dx: float, lam: float, dt: float, block_ijk, B, S, eta, R, stream=None) -> dict:
+    """Allocation-free residual on one uniform periodic grid (no hierarchy needed), for
+    callers that cannot allocate device memory; see include/ohm.h.  block_ijk: int32 [n, 3]."""
+    import torch
+    ijk = np.ascontiguousarray(block_ijk, dtype=np.int32)
+    n = len(ijk)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    L = lib()
+    if not getattr(L.ohm_residual_static, "argtypes", None):
+        L.ohm_residual_static.argtypes = [C.POINTER(C.c_int32), C.c_double, C.c_double, C.c_double, C.c_int64,
+                                          C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.POINTER(C.c_double), C.c_void_p]
+    cells = (C.c_int32 * 3)(*[int(v) for v in base_cells])
+    out = (C.c_double * 4)()
+    _check(L.ohm_residual_static(cells, float(dx), float(lam), float(dt), n, ijk.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 _ptr(B, n * 1536, "B"), _ptr(S, n * 1536, "S"), _ptr(eta, n * 512, "eta"),
+                                 _ptr(R, n * 1536, "R"), out, C.c_void_p(raw)), "ohm_residual_static")
+    return {"rel_l2": out[0], "max_abs": out[1], "l2_R": out[2], "l2_S": out[3]}
