@@ -56,7 +56,12 @@ typedef struct {
     int32_t precision;          /* OHM_FP64 or OHM_MIXED                                       */
     int32_t nu_pre, nu_post;    /* red-black sweeps before / after coarse correction (>= 0)   */
     int32_t n_coarse;           /* red-black sweeps on the coarsest grid (>= 1)               */
-    int32_t max_outer;          /* defect-correction cycles allowed per step (>= 1)           */
+    int32_t max_outer;          /* V-cycles allowed per step (>= 1)                           */
+    int32_t krylov;             /* OHM_MIXED only: 0 = the float32 inner solve is defect
+                                   correction with the V-cycle (Eqs. 16-18); m in 1..11 = it is
+                                   FGMRES(m) right-preconditioned by the same V-cycle (not in
+                                   the paper; same converged solution, fewer cycles).  Must be
+                                   0 for OHM_FP64.                                              */
     void *stream;               /* cudaStream_t used for all work, NULL = legacy default      */
 } ohm_hier_desc;
 

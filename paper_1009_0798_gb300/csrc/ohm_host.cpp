@@ -83,6 +83,11 @@ struct ohm_hier {
     int *d_rsrc = nullptr, *d_err = nullptr;
     void *ghostE = nullptr, *ghostEtaT = nullptr;
     void *rout = nullptr, *eacc = nullptr;  // mixed precision: float32 outer residual, inner correction
+    // FGMRES inner solve (mixed precision, krylov > 0): Arnoldi basis, preconditioned vectors,
+    // per-block inner-product weights, multi-dot scratch and results (device and pinned host)
+    float *kv[KMAX + 1] = {}, *kz[KMAX] = {};
+    double *wblk = nullptr, *kpart = nullptr, *kdots = nullptr, *hdots = nullptr;
+    std::vector<double> wblk_host;
     Buffers amrbuf;               // AMR levels, all blocks
     std::vector<Buffers> mgbuf;   // blocked multigrid grids
     Buffers smallbuf[MAX_SMALL];  // small grids (t stored in e2)
@@ -364,6 +369,14 @@ int allocate(ohm_hier *H, std::string &err) {
     if (H->mixed) {
         want(&H->rout, n * 3 * B3 * tsz);
         want(&H->eacc, n * 3 * B3 * tsz);
+        const int m = H->d.krylov;
+        if (m > 0) {
+            for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * sizeof(float));
+            for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
+            want((void **)&H->wblk, n * sizeof(double));
+            want((void **)&H->kpart, n * (KMAX + 1) * sizeof(double));
+            want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
+        }
     }
     want(&H->amrbuf.e, n * 3 * B3 * tsz);
     want(&H->amrbuf.e2, n * 3 * B3 * tsz);
@@ -408,9 +421,19 @@ int allocate(ohm_hier *H, std::string &err) {
         err = "table upload failed";
         return OHM_ERR_CUDA;
     }
-    if (cudaMallocHost((void **)&H->hnorm, 64) != cudaSuccess) {
+    if (cudaMallocHost((void **)&H->hnorm, 256) != cudaSuccess) {
         err = "pinned allocation failed";
         return OHM_ERR_OOM;
+    }
+    H->hdots = H->hnorm + 8;
+    if (H->wblk) {  // inner-product weights: h^3 on leaf blocks, 0 on covered ones
+        std::vector<double> w((size_t)H->nblocks, 0.0);
+        for (auto &g : H->amr)
+            for (int b = 0; b < g.n(); b++) w[(size_t)g.off + b] = g.covered[b] ? 0.0 : g.h * g.h * g.h;
+        if (cudaMemcpy(H->wblk, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            err = "weight upload failed";
+            return OHM_ERR_CUDA;
+        }
     }
     size_t k = 0;
     for (HGrid *g : grids) {
@@ -766,6 +789,121 @@ int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *
 // total number of V-cycles of the step.
 constexpr double INNER_FLOOR = 1e-4;
 
+// Weighted inner products <w, v_i> (i < S.k) and <w, w>, read back to the host.
+int mdot(ohm_hier *H, const float *w, const VecSet &S, double *out) {
+    LAUNCH(H, OHM_K_NORM, 0, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s));
+    CK(cudaMemcpyAsync(H->hdots, H->kdots, (S.k + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    memcpy(out, H->hdots, (S.k + 1) * sizeof(double));
+    return OHM_OK;
+}
+
+// L x for a float32 field (covered cells first set from their children, ghosts filled)
+int apply_L32(ohm_hier *H, float *x, const float *y, double a, double c, double d, float *out, double lamdt) {
+    (void)lamdt;
+    int st;
+    if ((st = sync_down_t<float>(H, x))) return st;
+    if ((st = fill_ghosts_t<float>(H, x, (float *)H->ghostE))) return st;
+    return composite_t<float, float>(H, x, y, (const float *)H->amrbuf.eta, (const float *)H->ghostE,
+                                     (const float *)H->ghostEtaT, a, c, d, out, (float *)nullptr, false);
+}
+
+// Float32 inner solve of L x = rout by FGMRES(m) (Saad 1993), right-preconditioned by one
+// V-cycle per Arnoldi step, classical Gram-Schmidt in the leaf-volume inner product, Givens
+// rotations on the host, restarts from the true residual.  Stops when the residual has
+// dropped by `target` or the step's V-cycle budget is used.  x is left in eacc.
+int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
+    const int m = H->d.krylov;
+    const size_t nel = (size_t)H->nblocks * 3 * B3;
+    float *x = (float *)H->eacc, *rhs = (float *)H->rout;
+    int st;
+    CK(cudaMemsetAsync(x, 0, nel * sizeof(float), H->s));
+    double nn[KMAX + 1];
+    VecSet none;
+    none.k = 0;
+    if ((st = mdot(H, rhs, none, nn))) return st;
+    const double beta0 = std::sqrt(nn[0]);
+    if (!(beta0 > 0) || !std::isfinite(beta0)) return OHM_OK;
+    double beta = beta0;
+    CK(launch_maxpy(H->kv[0], rhs, none, (float)(1.0 / beta), nel, H->s));
+    std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    auto h = [&](int i, int j) -> double & { return Hm[(size_t)i * m + j]; };
+    for (;;) {
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jend = 0;
+        bool done = false;
+        for (int j = 0; j < m && *cycles < H->d.max_outer; j++) {
+            // z_j = V-cycle applied to v_j (the cycle's right-hand side and correction buffers
+            // are pointed at v_j and z_j)
+            void *r_save = H->amrbuf.r, *e_save = H->amrbuf.e;
+            H->amrbuf.r = H->kv[j];
+            H->amrbuf.e = H->kz[j];
+            st = vcycle<float>(H, lamdt);
+            H->amrbuf.r = r_save;
+            H->amrbuf.e = e_save;
+            if (st) return st;
+            (*cycles)++;
+            // w = L z_j, orthogonalised against v_0..v_j
+            if ((st = apply_L32(H, H->kz[j], nullptr, 1.0, lamdt, 0.0, H->kv[j + 1], lamdt))) return st;
+            VecSet S;
+            S.k = j + 1;
+            for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
+            if ((st = mdot(H, H->kv[j + 1], S, nn))) return st;
+            for (int i = 0; i <= j; i++) {
+                h(i, j) = nn[i];
+                S.c[i] = (float)nn[i];
+            }
+            CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, 1.0f, nel, H->s));
+            if ((st = mdot(H, H->kv[j + 1], none, nn))) return st;
+            const double hn = std::sqrt(std::max(nn[0], 0.0));
+            h(j + 1, j) = hn;
+            if (hn > 0) CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], none, (float)(1.0 / hn), nel, H->s));
+            // Givens rotations
+            for (int i = 0; i < j; i++) {
+                double t = cs[i] * h(i, j) + sn[i] * h(i + 1, j);
+                h(i + 1, j) = -sn[i] * h(i, j) + cs[i] * h(i + 1, j);
+                h(i, j) = t;
+            }
+            double den = std::hypot(h(j, j), h(j + 1, j));
+            cs[j] = den > 0 ? h(j, j) / den : 1.0;
+            sn[j] = den > 0 ? h(j + 1, j) / den : 0.0;
+            h(j, j) = den;
+            h(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jend = j + 1;
+            if (std::fabs(g[j + 1]) <= target * beta0 || !(hn > 0)) {
+                done = true;
+                break;
+            }
+        }
+        // x += sum y_i z_i with R y = g
+        for (int i = jend - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int k = i + 1; k < jend; k++) s -= h(i, k) * y[k];
+            y[i] = h(i, i) != 0 ? s / h(i, i) : 0.0;
+        }
+        if (jend > 0) {
+            VecSet Z;
+            Z.k = jend;
+            for (int i = 0; i < jend; i++) {
+                Z.v[i] = H->kz[i];
+                Z.c[i] = (float)(-y[i]);
+            }
+            CK(launch_maxpy(x, x, Z, 1.0f, nel, H->s));
+        }
+        if (done || *cycles >= H->d.max_outer || jend == 0) break;
+        // restart from the true residual rhs - L x
+        if ((st = apply_L32(H, x, rhs, -1.0, -lamdt, 1.0, H->kv[0], lamdt))) return st;
+        if ((st = mdot(H, H->kv[0], none, nn))) return st;
+        beta = std::sqrt(std::max(nn[0], 0.0));
+        if (beta <= target * beta0 || !(beta > 0)) break;
+        CK(launch_maxpy(H->kv[0], H->kv[0], none, (float)(1.0 / beta), nel, H->s));
+    }
+    return OHM_OK;
+}
+
 int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *stats) {
     using T = float;
     const double lam = H->d.lambda, lamdt = lam * dt;
@@ -797,6 +935,9 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
             break;
         }
         const double target = tol >= 0 ? std::max(INNER_FLOOR, 0.3 * tol / std::max(nr[0], 1e-300)) : INNER_FLOOR;
+        if (H->d.krylov > 0) {
+            if ((st = inner_fgmres(H, lamdt, target, &cycles))) return st;
+        } else {
         CK(cudaMemsetAsync(eacc, 0, nbytes, H->s));
         while (cycles < H->d.max_outer) {
             if ((st = vcycle<T>(H, lamdt))) return st;
@@ -811,6 +952,7 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
             double ni[4];
             if ((st = read_norms(H, ni, &ef))) return st;
             if (!std::isfinite(ni[0]) || ni[0] <= target) break;
+        }
         }
         if ((st = update_all<T>(H, B, eacc))) return st;
         if ((st = sync_down(H, B))) return st;
@@ -836,6 +978,10 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     if (!(d->lambda > 0 && d->lambda <= 1)) { err = "lambda must be in (0, 1]"; return false; }
     if (d->precision != OHM_FP64 && d->precision != OHM_MIXED) { err = "unknown precision"; return false; }
     if (d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1) { err = "bad cycle counts"; return false; }
+    if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision != OHM_MIXED)) {
+        err = "krylov must be 0, or 1..11 with OHM_MIXED";
+        return false;
+    }
     for (int a = 0; a < 3; a++)
         if (((int64_t)d->base_cells[a] << (d->nlevels - 1)) >= (1 << 20)) { err = "level too fine"; return false; }
     return true;

@@ -116,6 +116,20 @@ cudaError_t launch_small_setup(const SmallDev<T> &sm, double lamdt, bool eta_cha
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS *src, TD *dst, size_t n, cudaStream_t s);
 
+// Krylov vector operations (float32 fields [nblk][3][512]); at most KMAX vectors at once.
+constexpr int KMAX = 12;
+struct VecSet {
+    const float *v[KMAX];
+    float c[KMAX];
+    int k = 0;
+};
+// out[0..k-1] = <w, v_i>, out[k] = <w, w>, volume weighted per block by wb (0 = excluded);
+// part: scratch of nblk * (k + 1) doubles.
+cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
+                        cudaStream_t s);
+// dst = (src - sum c_i v_i) * scale
+cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s);
+
 cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s);
 
 }  // namespace ohm

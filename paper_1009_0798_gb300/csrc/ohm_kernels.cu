@@ -10,6 +10,7 @@
 // and the flux divergence (Eq. 8) is sum_a (Phi_a(+) - Phi_a(-)) / (2 h^2).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
@@ -865,6 +866,70 @@ cudaError_t launch_convert(const TS_ *src, TD *dst, size_t n, cudaStream_t s) {
 }
 template cudaError_t launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
 template cudaError_t launch_convert<double, double>(const double *, double *, size_t, cudaStream_t);
+
+// ------------------------------------------------------------------ Krylov vector kernels
+// Vectors are block fields [nblk][3][512]; inner products are volume weighted over leaf
+// blocks (weight w_b = h^3, 0 for covered blocks), the norm of the convergence tests.
+__global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
+                                              double *__restrict__ part) {
+    __shared__ float red[32];
+    const int b = blockIdx.x;
+    const int ncol = V.k + 1;
+    const double wt = wb[b];
+    const size_t base = (size_t)b * 1536;
+    float acc[KMAX + 1];
+#pragma unroll
+    for (int i = 0; i <= KMAX; i++) acc[i] = 0.f;
+    if (wt != 0.0) {
+        for (int q = threadIdx.x; q < 1536; q += blockDim.x) {
+            const float x = w[base + q];
+            acc[KMAX] += x * x;
+#pragma unroll
+            for (int i = 0; i < KMAX; i++)
+                if (i < V.k) acc[i] += x * V.v[i][base + q];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i <= KMAX; i++) {
+        if (i > V.k) break;
+        float s = block_sum(i == V.k ? acc[KMAX] : acc[i < KMAX ? i : KMAX], red);
+        if (threadIdx.x == 0) part[(size_t)b * ncol + i] = (double)s * wt;
+    }
+}
+
+// column sums of part[nblk][ncol] in a fixed order (one thread block per column)
+__global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part, int nblk, int ncol, double *__restrict__ out) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += part[(size_t)b * ncol + c];
+    double s = block_sum(a, red);
+    if (threadIdx.x == 0) out[c] = s;
+}
+
+cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
+                        cudaStream_t s) {
+    k_mdot<<<nblk, 256, 0, s>>>(w, V, wb, part);
+    k_colsum<<<V.k + 1, 256, 0, s>>>(part, nblk, V.k + 1, out);
+    return cudaGetLastError();
+}
+
+// dst = (src - sum_i c_i v_i) * scale   (dst may equal src)
+__global__ void k_maxpy(float *dst, const float *src, VecSet V, float scale, size_t n) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        float x = src[q];
+#pragma unroll
+        for (int i = 0; i < KMAX; i++)
+            if (i < V.k) x -= V.c[i] * V.v[i][q];
+        dst[q] = x * scale;
+    }
+}
+
+cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s) {
+    int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    k_maxpy<<<grid, 256, 0, s>>>(dst, src, V, scale, n);
+    return cudaGetLastError();
+}
 
 // ------------------------------------------------------------------ coarsest grids
 // Lexicographic periodic grids below the last blocked grid, all handled by one thread block

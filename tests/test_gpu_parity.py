@@ -224,18 +224,36 @@ def test_periodic_box_32_workload(ohm, orc):
 
 # ------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("name", ["uniform_32", "amr_3level", "sinusoid_e1"])
-def test_mixed_precision_matches_fp64_oracle(ohm, orc, name):
-    """FP32 multigrid inside FP64 defect correction reaches the FP64 solution."""
+@pytest.mark.parametrize("krylov", [0, 4])
+def test_mixed_precision_matches_fp64_oracle(ohm, orc, name, krylov):
+    """FP32 multigrid (plain or FGMRES-accelerated) inside FP64 iterative refinement reaches
+    the FP64 solution."""
     h = HIERS[name]()
     b, eta = rand_fields(h, 8, 1.0)
     b = orc.Oracle(h, 0.5, eta).sync_down(b)
     dt = 4.0 * h.dx(h.nlevels - 1) ** 2
     want, _ = orc.Oracle(h, 0.5, eta).cn_step(b, dt, 1e-14, 2, 2, 8, 80)
-    g = make(ohm, h, precision=1, max_outer=80)
+    g = make(ohm, h, precision=1, max_outer=80, krylov=krylov)
     B = dev(b)
     st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-11)
     assert st["converged"]
     assert rel_err(host(B), want.ravel()) < 1e-9
+    rel, _ = ohm.ohm_residual_norm(g, B)
+    assert rel <= 1e-11
+
+
+def test_fgmres_takes_fewer_cycles_than_defect_correction(ohm):
+    """Same converged tolerance, fewer V-cycles with the Krylov-accelerated inner solve on a
+    stiff case (3-decade eta, dt = 100x the explicit limit)."""
+    wl = W.resistive_bump_256(n=32)
+    counts = {}
+    for krylov in (0, 6):
+        g = make(ohm, wl.hier, precision=1, max_outer=200, krylov=krylov)
+        B = dev(wl.B)
+        st = ohm.ohm_cn_step(g, B, dev(wl.eta), wl.dt, 1e-9)
+        assert st["converged"]
+        counts[krylov] = st["cycles"]
+    assert counts[6] < counts[0]
 
 
 # ------------------------------------------------------------------ edge cases
@@ -266,6 +284,8 @@ def test_zero_field_stays_zero_and_not_converged_status(ohm, orc):
 
 def test_invalid_calls(ohm):
     h = W.uniform(16, 16, 16, 1.0 / 16)
+    with pytest.raises(ohm.OhmError):
+        make(ohm, h, krylov=4)  # Krylov inner solve needs OHM_MIXED
     g = make(ohm, h)
     B = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
     with pytest.raises(ohm.OhmError) as ei:
