@@ -42,6 +42,8 @@ def args_parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--only", choices=["fgmres", "mixed", "fp64"], default=None,
+                   help="run just this path for a few steps and print its timing (for profiler captures)")
     return p.parse_args()
 
 
@@ -307,6 +309,19 @@ def run_ours(args):
     def summary(r):
         return {"value": ws * cells * args.steps / (barrier_max(ws, r["total_ms"]) * 1e-3),
                 "ms_per_step": r["total_ms"] / args.steps, "cycles_per_step": [s["cycles"] for s in r["infos"]]}
+
+    if args.only:
+        prec = ohm.OHM_FP64 if args.only == "fp64" else ohm.OHM_MIXED
+        g1 = make(prec, KRYLOV if args.only == "fgmres" else 0)
+        for _ in range(args.warmup):
+            run_steps(ohm, g1, B, B0, eta, wl, 1, stream)
+        t0 = time.perf_counter()
+        infos = run_steps(ohm, g1, B, B0, eta, wl, args.steps, stream)
+        dt_s = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "host_seconds": dt_s,
+                              "cycles_per_step": [s["cycles"] for s in infos]}), flush=True)
+        return
 
     # headline: float32 multigrid, FGMRES-accelerated, inside float64 iterative refinement
     gm = make(ohm.OHM_MIXED, KRYLOV)

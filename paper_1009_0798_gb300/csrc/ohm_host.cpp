@@ -374,7 +374,7 @@ int allocate(ohm_hier *H, std::string &err) {
             for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * sizeof(float));
             for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
             want((void **)&H->wblk, n * sizeof(double));
-            want((void **)&H->kpart, n * (KMAX + 1) * sizeof(double));
+            want((void **)&H->kpart, (size_t)152 * 4 * (KMAX + 1) * sizeof(double));
             want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
         }
     }
@@ -850,15 +850,27 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             S.k = j + 1;
             for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
             if ((st = mdot(H, H->kv[j + 1], S, nn))) return st;
+            double proj = 0.0;
             for (int i = 0; i <= j; i++) {
                 h(i, j) = nn[i];
                 S.c[i] = (float)nn[i];
+                proj += nn[i] * nn[i];
             }
-            CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, 1.0f, nel, H->s));
-            if ((st = mdot(H, H->kv[j + 1], none, nn))) return st;
-            const double hn = std::sqrt(std::max(nn[0], 0.0));
+            // ||w - sum h_i v_i||^2 = <w,w> - sum h_i^2 for orthonormal v_i: when that keeps more
+            // than 1% of <w,w> the orthogonalisation and the normalisation are one pass,
+            // otherwise the norm is measured after orthogonalising
+            const double ww = nn[j + 1];
+            double hn;
+            if (ww - proj > 0.01 * ww) {
+                hn = std::sqrt(ww - proj);
+                CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, (float)(1.0 / hn), nel, H->s));
+            } else {
+                CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, 1.0f, nel, H->s));
+                if ((st = mdot(H, H->kv[j + 1], none, nn))) return st;
+                hn = std::sqrt(std::max(nn[0], 0.0));
+                if (hn > 0) CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], none, (float)(1.0 / hn), nel, H->s));
+            }
             h(j + 1, j) = hn;
-            if (hn > 0) CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], none, (float)(1.0 / hn), nel, H->s));
             // Givens rotations
             for (int i = 0; i < j; i++) {
                 double t = cs[i] * h(i, j) + sn[i] * h(i + 1, j);

@@ -46,6 +46,74 @@ __device__ __forceinline__ void load_tile(T *__restrict__ tile, const T *__restr
     }
 }
 
+// 8 consecutive values of a block row (16-byte aligned in global memory) as vector loads
+template <typename T>
+struct Row8 {
+    T v[8];
+};
+__device__ __forceinline__ Row8<float> load_row8(const float *__restrict__ p) {
+    Row8<float> r;
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+    r.v[4] = b.x; r.v[5] = b.y; r.v[6] = b.z; r.v[7] = b.w;
+    return r;
+}
+__device__ __forceinline__ Row8<double> load_row8(const double *__restrict__ p) {
+    Row8<double> r;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + q);
+        r.v[2 * q] = a.x;
+        r.v[2 * q + 1] = a.y;
+    }
+    return r;
+}
+
+// Row-wise staging of a block and a halo of width HW (tile edge S = 8 + 2 HW), NC components
+// of field F, from the 27 neighbour ids in shared memory (snb, -1 = absent).  One task per
+// (component, tile row along x): the 8 interior values of the row come from one block as
+// vector loads, the HW halo cells at each end from the x-neighbours of that block.  Rows or
+// halo cells of an absent neighbour come from `ghost` ([NC][10^3], HW = 1 only) or are zero.
+// Values at the corners of the box are never read by the stencil and may be left stale.
+template <typename T, int NC, int HW>
+__device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__restrict__ F, const int *__restrict__ snb,
+                                           const T *__restrict__ ghost) {
+    constexpr int S = 8 + 2 * HW, S2 = S * S, S3 = S2 * S;
+    for (int task = threadIdx.x; task < NC * S2; task += blockDim.x) {
+        const int c = task / S2, rr = task - c * S2;
+        const int tj = rr % S, tk = rr / S;
+        const int lj = tj - HW, lk = tk - HW;
+        const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int sj = lj - 8 * dj, sk = lk - 8 * dk;
+        T *dst = tile + c * S3 + rr * S;
+        const int dcent = (dk + 1) * 9 + (dj + 1) * 3;
+        const int src = snb[dcent + 1];
+        if (src >= 0) {
+            const Row8<T> row = load_row8(F + ((size_t)src * NC + c) * B3 + (sk * 8 + sj) * 8);
+#pragma unroll
+            for (int q = 0; q < 8; q++) dst[HW + q] = row.v[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++) dst[HW + q] = ghost ? ghost[c * T3 + rr * S + HW + q] : T(0);
+        }
+        const int slo = snb[dcent], shi = snb[dcent + 2];
+#pragma unroll
+        for (int h = 0; h < HW; h++) {
+            // low end: cells 8-HW+h of the x- neighbour; high end: cells h of the x+ neighbour
+            dst[h] = slo >= 0 ? F[((size_t)slo * NC + c) * B3 + (sk * 8 + sj) * 8 + 8 - HW + h]
+                              : (ghost ? ghost[c * T3 + rr * S + h] : T(0));
+            dst[HW + 8 + h] = shi >= 0 ? F[((size_t)shi * NC + c) * B3 + (sk * 8 + sj) * 8 + h]
+                                       : (ghost ? ghost[c * T3 + rr * S + HW + 8 + h] : T(0));
+        }
+    }
+}
+
+// neighbour ids of block b into shared memory (call before stage_rows, then __syncthreads)
+__device__ __forceinline__ void stage_nbr(int *snb, const int *__restrict__ nbr, int b) {
+    if (threadIdx.x < 27) snb[threadIdx.x] = __ldg(nbr + b * 27 + threadIdx.x);
+}
+
 // Phi for the face between tile cells p (low) and p + sa.  Components b1 < b2 are the two
 // axes other than a, with tile strides s1, s2.
 template <typename T>
@@ -100,6 +168,40 @@ __device__ __forceinline__ void all_faces(const T *__restrict__ tB, const T *__r
         }
         phi[(ax * 2 + 0) * 576 + r] = p1;
         phi[(ax * 2 + 1) * 576 + r] = p2;
+    }
+}
+
+// Same result as all_faces for 512-thread blocks: thread (i,j,k) computes the low x, y and z
+// faces of its cell, then threads 0..191 compute the 3 x 64 faces of the high boundary planes.
+template <typename T>
+__device__ __forceinline__ void all_faces_512(const T *__restrict__ tB, const T *__restrict__ tE, T *__restrict__ phi) {
+    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    const int p = tix(i + 1, j + 1, k + 1);
+    T p1, p2;
+    face_phi(tB, tE, p - 1, 0, 1, 1, TS, 2, TS * TS, p1, p2);
+    phi[0 * 576 + (k * 8 + j) * 9 + i] = p1;
+    phi[1 * 576 + (k * 8 + j) * 9 + i] = p2;
+    face_phi(tB, tE, p - TS, 1, TS, 0, 1, 2, TS * TS, p1, p2);
+    phi[2 * 576 + (k * 9 + j) * 8 + i] = p1;
+    phi[3 * 576 + (k * 9 + j) * 8 + i] = p2;
+    face_phi(tB, tE, p - TS * TS, 2, TS * TS, 0, 1, 1, TS, p1, p2);
+    phi[4 * 576 + (k * 8 + j) * 8 + i] = p1;
+    phi[5 * 576 + (k * 8 + j) * 8 + i] = p2;
+    if (t < 192) {
+        const int ax = t >> 6, u = t & 7, v = (t >> 3) & 7;
+        if (ax == 0) {  // x = 8 plane: (j, k) = (u, v)
+            face_phi(tB, tE, tix(8, u + 1, v + 1), 0, 1, 1, TS, 2, TS * TS, p1, p2);
+            phi[0 * 576 + (v * 8 + u) * 9 + 8] = p1;
+            phi[1 * 576 + (v * 8 + u) * 9 + 8] = p2;
+        } else if (ax == 1) {  // y = 8 plane: (i, k) = (u, v)
+            face_phi(tB, tE, tix(u + 1, 8, v + 1), 1, TS, 0, 1, 2, TS * TS, p1, p2);
+            phi[2 * 576 + (v * 9 + 8) * 8 + u] = p1;
+            phi[3 * 576 + (v * 9 + 8) * 8 + u] = p2;
+        } else {  // z = 8 plane: (i, j) = (u, v)
+            face_phi(tB, tE, tix(u + 1, v + 1, 8), 2, TS * TS, 0, 1, 1, TS, p1, p2);
+            phi[4 * 576 + (8 * 8 + v) * 8 + u] = p1;
+            phi[5 * 576 + (8 * 8 + v) * 8 + u] = p2;
+        }
     }
 }
 
@@ -168,16 +270,19 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
     TC *tE = tB + 3 * T3;
     TC *phi = tE + T3;
     __shared__ TC red[32];
+    __shared__ int snb[27];
     const int b = blockIdx.x;
     if (g.covered && g.covered[b]) {
         if (partials && threadIdx.x < 3) partials[b * 3 + threadIdx.x] = 0.0;
         return;
     }
     const int slot = g.gslot ? g.gslot[b] : -1;
-    load_tile<TC, 3>(tB, X, b, g.nbr, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
-    load_tile<TC, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    all_faces(tB, tE, phi);
+    stage_rows<TC, 3, 1>(tB, X, snb, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
+    stage_rows<TC, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    __syncthreads();
+    all_faces_512(tB, tE, phi);
     __syncthreads();
     const double inv2h = 0.5 / g.h;
     // flux registers: faces with no same-level neighbour publish F = Phi / (2h)
@@ -274,10 +379,13 @@ __global__ void __launch_bounds__(256) k_smooth(GridDev g, const T *__restrict__
                                                 const T *__restrict__ Geta, T coef, int colour) {
     __shared__ __align__(16) T tB[3 * T3];
     __shared__ __align__(16) T tE[T3];
+    __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
-    load_tile<T, 3>(tB, e_in, b, g.nbr, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
-    load_tile<T, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_nbr(snb, g.nbr, b);
+    __syncthreads();
+    stage_rows<T, 3, 1>(tB, e_in, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    stage_rows<T, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     const int t = threadIdx.x;
     const int k = t >> 5, j = (t >> 2) & 7;
@@ -330,6 +438,10 @@ template cudaError_t launch_smooth<float>(const GridDev &, const float *, float 
 // from eta (Eqs. 21-23).  e_in and e_out are distinct buffers.
 constexpr int RS = 12, R3 = RS * RS * RS;
 __device__ __forceinline__ int rix(int i, int j, int k) { return (k * RS + j) * RS + i; }
+// smoother division: the hardware reciprocal in float32 (a smoothing weight needs no
+// correctly rounded quotient), exact division in float64
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 template <typename T>
 __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
@@ -351,7 +463,7 @@ __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__r
     for (int c = 0; c < 3; c++) {
         T ev = tB[c * R3 + p];
         T res = rr[c] - ev - coef * dv[c];
-        out[c] = ev + res / (T(1) + al[c]);
+        out[c] = ev + fast_div(res, T(1) + al[c]);
     }
 }
 
@@ -361,32 +473,27 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tB = reinterpret_cast<T *>(smem_raw);  // [3][12^3]
     T *tE = tB + 3 * R3;                      // [12^3]
+    __shared__ int snb[27];
     const int b = blockIdx.x;
-    for (int idx = threadIdx.x; idx < R3; idx += blockDim.x) {
-        const int ti = idx % RS, tj = (idx / RS) % RS, tk = idx / (RS * RS);
-        const int li = ti - 2, lj = tj - 2, lk = tk - 2;
-        const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
-        const int src = (di | dj | dk) ? __ldg(g.nbr + b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1)) : b;
-        const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
-        const T *p = e_in + (size_t)src * 3 * B3 + off;
-        tB[idx] = p[0];
-        tB[R3 + idx] = p[B3];
-        tB[2 * R3 + idx] = p[2 * B3];
-        tE[idx] = eta[(size_t)src * B3 + off];
-    }
+    stage_nbr(snb, g.nbr, b);
+    __syncthreads();
+    stage_rows<T, 3, 2>(tB, e_in, snb, nullptr);
+    stage_rows<T, 1, 2>(tE, eta, snb, nullptr);
     __syncthreads();
     // red cells ((i+j+k) even) of the block and its face/edge ring: the 10^3 box without corners
-    // each of the 256 threads owns box positions q = t + 256 s, s = 0..3 (launch uses 256)
-    T nv[4][3];
-    int np[4];
+    // The 500 red positions of the 10^3 box, 5 per x-row, enumerated densely: thread t owns
+    // red positions t and t + 256 (launch uses 256); the 4 red box corners are skipped.
+    T nv[2][3];
+    int np[2];
 #pragma unroll
-    for (int s4 = 0; s4 < 4; s4++) {
+    for (int s4 = 0; s4 < 2; s4++) {
         np[s4] = -1;
         const int q = threadIdx.x + 256 * s4;
-        if (q >= T3) continue;
-        const int ti = q % TS, tj = (q / TS) % TS, tk = q / (TS * TS);
+        if (q >= 500) continue;
+        const int row = q / 5, pos = q - row * 5;
+        const int tj = row % TS, tk = row / TS;
+        const int ti = 2 * pos + ((tj + tk + 1) & 1);
         const int li = ti - 1, lj = tj - 1, lk = tk - 1;
-        if (((li + lj + lk) & 1) != 0) continue;
         const int nout = (li < 0 || li > 7) + (lj < 0 || lj > 7) + (lk < 0 || lk > 7);
         if (nout == 3) continue;
         const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
@@ -398,7 +505,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     }
     __syncthreads();
 #pragma unroll
-    for (int s4 = 0; s4 < 4; s4++)
+    for (int s4 = 0; s4 < 2; s4++)
         if (np[s4] >= 0)
             for (int c = 0; c < 3; c++) tB[c * R3 + np[s4]] = nv[s4][c];
     __syncthreads();
@@ -444,9 +551,12 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict__ eta, const T *__restrict__ Geta,
                                                  double lh2, T *__restrict__ inv) {
     __shared__ T tE[T3];
+    __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
-    load_tile<T, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_nbr(snb, g.nbr, b);
+    __syncthreads();
+    stage_rows<T, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
     const int p = tix(i + 1, j + 1, k + 1);
@@ -483,12 +593,15 @@ __global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__re
     T *tE = tB + 3 * T3;
     T *phi = tE + T3;
     T *tt = phi + 6 * 576;
+    __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
-    load_tile<T, 3>(tB, e, b, g.nbr, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
-    load_tile<T, 1>(tE, eta, b, g.nbr, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    all_faces(tB, tE, phi);
+    stage_rows<T, 3, 1>(tB, e, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    stage_rows<T, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    __syncthreads();
+    all_faces_512(tB, tE, phi);
     __syncthreads();
     {
         const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
@@ -870,30 +983,41 @@ template cudaError_t launch_convert<double, double>(const double *, double *, si
 // ------------------------------------------------------------------ Krylov vector kernels
 // Vectors are block fields [nblk][3][512]; inner products are volume weighted over leaf
 // blocks (weight w_b = h^3, 0 for covered blocks), the norm of the convergence tests.
+// Thread block c folds the 8^3 blocks [c*per, (c+1)*per): per block, each thread forms 6
+// float32 products per column and adds them, times the block weight, to float64 totals;
+// per-thread-block results go to part[c][col] (fixed order: deterministic).
 __global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
-                                              double *__restrict__ part) {
-    __shared__ float red[32];
-    const int b = blockIdx.x;
+                                              int nblk, double *__restrict__ part) {
+    __shared__ double red[32];
     const int ncol = V.k + 1;
-    const double wt = wb[b];
-    const size_t base = (size_t)b * 1536;
-    float acc[KMAX + 1];
+    const int per = (nblk + gridDim.x - 1) / gridDim.x;
+    const int b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
+    double acc[KMAX + 1];
 #pragma unroll
-    for (int i = 0; i <= KMAX; i++) acc[i] = 0.f;
-    if (wt != 0.0) {
-        for (int q = threadIdx.x; q < 1536; q += blockDim.x) {
-            const float x = w[base + q];
-            acc[KMAX] += x * x;
+    for (int i = 0; i <= KMAX; i++) acc[i] = 0.0;
+    for (int b = b0; b < b1; b++) {
+        const double wt = wb[b];
+        if (wt == 0.0) continue;
+        const size_t base = (size_t)b * 1536 + threadIdx.x;
+        float f[KMAX + 1];
+#pragma unroll
+        for (int i = 0; i <= KMAX; i++) f[i] = 0.f;
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const float x = w[base + 256 * s];
+            f[KMAX] += x * x;
 #pragma unroll
             for (int i = 0; i < KMAX; i++)
-                if (i < V.k) acc[i] += x * V.v[i][base + q];
+                if (i < V.k) f[i] += x * V.v[i][base + 256 * s];
         }
+#pragma unroll
+        for (int i = 0; i <= KMAX; i++) acc[i] += (double)f[i] * wt;
     }
 #pragma unroll
     for (int i = 0; i <= KMAX; i++) {
         if (i > V.k) break;
-        float s = block_sum(i == V.k ? acc[KMAX] : acc[i < KMAX ? i : KMAX], red);
-        if (threadIdx.x == 0) part[(size_t)b * ncol + i] = (double)s * wt;
+        double s = block_sum(i == V.k ? acc[KMAX] : acc[i < KMAX ? i : KMAX], red);
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * ncol + i] = s;
     }
 }
 
@@ -909,8 +1033,9 @@ __global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part,
 
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
                         cudaStream_t s) {
-    k_mdot<<<nblk, 256, 0, s>>>(w, V, wb, part);
-    k_colsum<<<V.k + 1, 256, 0, s>>>(part, nblk, V.k + 1, out);
+    const int grid = std::min(nblk, 152 * 4);
+    k_mdot<<<grid, 256, 0, s>>>(w, V, wb, nblk, part);
+    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out);
     return cudaGetLastError();
 }
 
