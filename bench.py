@@ -146,14 +146,21 @@ def dist():
 
 
 def barrier_max(ws, value):
+    """Barrier, then the maximum of `value` over all ranks (the slowest replica's time)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as td
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if td.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     td.barrier()
     td.all_reduce(t, op=td.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ws, cells, steps, elapsed_ms):
+    """Whole-job cell-steps/s of ws replicas: all cells of all ranks over the slowest rank's time."""
+    return ws * cells * steps / (barrier_max(ws, elapsed_ms) * 1e-3)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -327,7 +334,7 @@ def run_ours(args):
     gm = make(ohm.OHM_MIXED, KRYLOV)
     mixed = timed(gm, ohm.OHM_MIXED)
     t_max = barrier_max(ws, mixed["total_ms"])
-    value = ws * cells * args.steps / (t_max * 1e-3)
+    value = job_throughput(ws, cells, args.steps, mixed["total_ms"])
     # the same without Krylov acceleration (inner defect correction), and plain FP64 (the
     # paper's scheme: float64 V-cycles in float64 defect correction)
     others = {}

@@ -8,10 +8,11 @@
  * CPU-baseline leg of the benchmark load this file; the CUDA solver library shares no code
  * with it and never calls it.
  *
- * Storage is deliberately different from the GPU path: every AMR level is a dense array
- * over its whole periodic domain, with a per-8^3-block "present" mask, and every stencil
- * value is fetched through one accessor (at()) that wraps periodically and, for a cell the
- * level does not have, interpolates from the parent level.  No halos, no neighbour tables.
+ * Storage is deliberately different from the GPU path: every grid is addressed by global
+ * cell indices through one accessor (at()) that wraps periodically and, for a cell the
+ * level does not have, interpolates from the parent level.  The base grid and its
+ * coarsenings are dense arrays; refined levels store their present 8^3 blocks behind a
+ * block-position lookup.  No halos, no neighbour tables.
  *
  * What is computed (paper passages in brackets):
  *   face fluxes F_x, F_y, F_z                       [Sec. 2.1, Eqs. 4-6]
@@ -59,6 +60,8 @@ typedef struct {
     int full;                 /* 1: every cell present */
     unsigned char *present;   /* per block, AMR levels only */
     unsigned char *covered;   /* per block, AMR levels only */
+    int *bid;                 /* refined levels: storage index of each block position, -1 absent */
+    long nblk;                /* refined levels: blocks stored */
     int nchunk;               /* loop chunks: blocks (AMR) or z-planes (coarse grids) */
     int (*chunk)[6];          /* lo[3], hi[3] */
     /* dense arrays over the level domain; 3 components unless noted */
@@ -81,12 +84,17 @@ typedef struct orc_hier {
 /* ------------------------------------------------------------------ indexing */
 static inline int wrapi(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 static inline long ncell(const grid_t *g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
-static inline long cidx(const grid_t *g, int c, int i, int j, int k) {
-    return (((long)c * g->n[2] + k) * g->n[1] + j) * g->n[0] + i;
-}
 static inline long bidx(const grid_t *g, int i, int j, int k) {
     return ((long)(k / BS) * g->nb[1] + (j / BS)) * g->nb[0] + (i / BS);
 }
+/* Storage index of component c at cell (i,j,k): dense [c][z][y][x] for the base grid and
+ * its coarsenings; [c][block][8][8][8] over the present blocks for refined levels. */
+static inline long cidx(const grid_t *g, int c, int i, int j, int k) {
+    if (g->bid)
+        return (((long)c * g->nblk + g->bid[bidx(g, i, j, k)]) * BS + (k % BS)) * BS * BS + (j % BS) * BS + (i % BS);
+    return (((long)c * g->n[2] + k) * g->n[1] + j) * g->n[0] + i;
+}
+static inline long nstore(const grid_t *g) { return g->bid ? g->nblk * BS * BS * BS : ncell(g); }
 static inline int is_present(const grid_t *g, int i, int j, int k) {
     return g->full || g->present[bidx(g, i, j, k)];
 }
@@ -477,7 +485,7 @@ static void amr_vcycle(orc_hier *H, double lamdt, const mgpar_t *P) {
 
 /* ------------------------------------------------------------------ setup */
 static int alloc_grid(grid_t *g, int amr) {
-    long n = ncell(g);
+    long n = nstore(g);
     g->e = calloc(3 * n, sizeof(double)); g->r = calloc(3 * n, sizeof(double));
     g->t = calloc(3 * n, sizeof(double)); g->d = calloc(3 * n, sizeof(double));
     g->eta = calloc(n, sizeof(double));
@@ -491,7 +499,7 @@ static int alloc_grid(grid_t *g, int amr) {
 
 static void free_grid(grid_t *g) {
     free(g->e); free(g->r); free(g->t); free(g->d); free(g->eta);
-    free(g->B); free(g->S); free(g->R); free(g->present); free(g->covered); free(g->chunk);
+    free(g->B); free(g->S); free(g->R); free(g->present); free(g->covered); free(g->chunk); free(g->bid);
 }
 
 void orc_destroy(orc_hier *H) {
@@ -522,7 +530,7 @@ orc_hier *orc_create(int nx, int ny, int nz, double dx0, int nlev, long nblocks,
         g->full = 0;
         long nbk = (long)g->nb[0] * g->nb[1] * g->nb[2];
         g->present = calloc(nbk, 1); g->covered = calloc(nbk, 1);
-        if (alloc_grid(g, 1)) FAIL("out of memory");
+        if (!g->present || !g->covered) FAIL("out of memory");
     }
     for (long b = 0; b < nblocks; b++) {
         int l = lijk[4 * b], bi = lijk[4 * b + 1], bj = lijk[4 * b + 2], bk = lijk[4 * b + 3];
@@ -562,11 +570,20 @@ orc_hier *orc_create(int nx, int ny, int nz, double dx0, int nlev, long nblocks,
         long nbk = (long)g->nb[0] * g->nb[1] * g->nb[2];
         g->chunk = malloc(sizeof(*g->chunk) * nbk);
         g->nchunk = 0;
+        if (l > 0) {
+            g->bid = malloc(sizeof(int) * nbk);
+            if (!g->bid) FAIL("out of memory");
+            for (long q = 0; q < nbk; q++) g->bid[q] = -1;
+        }
         for (int bk = 0; bk < g->nb[2]; bk++) for (int bj = 0; bj < g->nb[1]; bj++) for (int bi = 0; bi < g->nb[0]; bi++) {
-            if (!g->present[((long)bk * g->nb[1] + bj) * g->nb[0] + bi]) continue;
+            long pos = ((long)bk * g->nb[1] + bj) * g->nb[0] + bi;
+            if (!g->present[pos]) continue;
+            if (g->bid) g->bid[pos] = g->nchunk;
             int *c = g->chunk[g->nchunk++];
             c[0] = bi * BS; c[1] = bj * BS; c[2] = bk * BS; c[3] = c[0] + BS; c[4] = c[1] + BS; c[5] = c[2] + BS;
         }
+        g->nblk = g->nchunk;
+        if (alloc_grid(g, 1)) FAIL("out of memory");
     }
     H->lev[0].full = 1;
     /* base multigrid: halve while every dimension is even and the result stays >= 2 */
@@ -754,7 +771,7 @@ int orc_heun_step(orc_hier *H, double *B_user, double dt) {
     composite_apply(H, arr(H, W_S, ts), 1.0, -dt, 1.0, arr(H, W_B, tb), arr(H, W_R, tr));
     for (int l = 0; l < H->nlev; l++) {
         grid_t *g = &H->lev[l];
-        long n = 3 * ncell(g);
+        long n = 3 * nstore(g);
         for (long i = 0; i < n; i++) g->B[i] = 0.5 * g->R[i];
     }
     sync_down(H, arr(H, W_B, tb));
