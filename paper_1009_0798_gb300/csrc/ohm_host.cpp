@@ -374,7 +374,7 @@ int allocate(ohm_hier *H, std::string &err) {
             for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * sizeof(float));
             for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
             want((void **)&H->wblk, n * sizeof(double));
-            want((void **)&H->kpart, (size_t)152 * 4 * (KMAX + 1) * sizeof(double));
+            want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
             want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
         }
     }

@@ -20,31 +20,28 @@ namespace ohm {
 
 __device__ __forceinline__ int tix(int i, int j, int k) { return (k * TS + j) * TS + i; }
 
-// Stage NC components of block b (grid-local) of field F and its halo into tile[NC][1000].
-// Halo cells of an absent neighbour come from `ghost` (the block's slot, [NC][1000]) or are
-// zero when ghost == nullptr.  Corners of the 10^3 box are skipped.
-template <typename T, int NC>
-__device__ __forceinline__ void load_tile(T *__restrict__ tile, const T *__restrict__ F, int b,
-                                          const int *__restrict__ nbr, const T *__restrict__ ghost) {
-    for (int idx = threadIdx.x; idx < T3; idx += blockDim.x) {
-        int ti = idx % TS, tj = (idx / TS) % TS, tk = idx / (TS * TS);
-        int di = (ti == 0) ? -1 : (ti == TS - 1 ? 1 : 0);
-        int dj = (tj == 0) ? -1 : (tj == TS - 1 ? 1 : 0);
-        int dk = (tk == 0) ? -1 : (tk == TS - 1 ? 1 : 0);
-        int nout = (di != 0) + (dj != 0) + (dk != 0);
-        if (nout == 3) continue;
-        int src = nout == 0 ? b : __ldg(nbr + b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1));
-        if (src >= 0) {
-            int li = ti - 1 - BS * di, lj = tj - 1 - BS * dj, lk = tk - 1 - BS * dk;
-            const T *p = F + (size_t)src * NC * B3 + (lk * BS + lj) * BS + li;
-#pragma unroll
-            for (int c = 0; c < NC; c++) tile[c * T3 + idx] = p[c * B3];
-        } else {
-#pragma unroll
-            for (int c = 0; c < NC; c++) tile[c * T3 + idx] = ghost ? ghost[c * T3 + idx] : T(0);
-        }
-    }
-}
+// Shared-memory geometry of a staged 10^3 tile (block + 1-cell halo).  Rows along x are RS
+// elements apart: for float32 a warp reading 4 rows x 8 cells then hits 32 distinct banks
+// (RS = 24 = 8 mod 16); float64 kernels are bound by the float64 pipe, not by shared memory,
+// and keep the compact stride.  PX is the row stride of the x-face flux array.
+template <typename T>
+struct G10;
+template <>
+struct G10<float> {
+    static constexpr int RS = 24, PX = 24;
+};
+template <>
+struct G10<double> {
+    static constexpr int RS = 10, PX = 9;
+};
+template <typename T>
+struct Geo {
+    static constexpr int RS = G10<T>::RS, PS = TS * RS, CS = TS * PS, PX = G10<T>::PX;
+    static constexpr int PHI_X = 64 * PX;  // x faces per component
+    static constexpr int PHI = 2 * PHI_X + 4 * 576;
+    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RS + i; }
+    __device__ static __forceinline__ int xf(int fi, int j, int k) { return (k * 8 + j) * PX + fi; }
+};
 
 // 8 consecutive values of a block row (16-byte aligned in global memory) as vector loads
 template <typename T>
@@ -70,23 +67,25 @@ __device__ __forceinline__ Row8<double> load_row8(const double *__restrict__ p) 
     return r;
 }
 
-// Row-wise staging of a block and a halo of width HW (tile edge S = 8 + 2 HW), NC components
-// of field F, from the 27 neighbour ids in shared memory (snb, -1 = absent).  One task per
-// (component, tile row along x): the 8 interior values of the row come from one block as
-// vector loads, the HW halo cells at each end from the x-neighbours of that block.  Rows or
-// halo cells of an absent neighbour come from `ghost` ([NC][10^3], HW = 1 only) or are zero.
-// Values at the corners of the box are never read by the stencil and may be left stale.
-template <typename T, int NC, int HW>
+// Row-wise staging of a block and a halo of width HW (tile edge S = 8 + 2 HW; rows along x
+// RS elements apart, planes S*RS, components S*S*RS), NC components of field F, from the 27
+// neighbour ids in shared memory (snb, -1 = absent).  One task per (component, tile row):
+// the 8 interior values of the row come from one block as vector loads, the HW halo cells at
+// each end from the x-neighbours of that block.  Rows or cells of an absent neighbour come
+// from `ghost` ([NC][10^3] compact, HW = 1 only) or are zero.  Values at the corners of the
+// box are never read by the stencil and may be left stale.
+template <typename T, int NC, int HW, int RS>
 __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__restrict__ F, const int *__restrict__ snb,
                                            const T *__restrict__ ghost) {
-    constexpr int S = 8 + 2 * HW, S2 = S * S, S3 = S2 * S;
+    constexpr int S = 8 + 2 * HW, S2 = S * S;
     for (int task = threadIdx.x; task < NC * S2; task += blockDim.x) {
         const int c = task / S2, rr = task - c * S2;
         const int tj = rr % S, tk = rr / S;
         const int lj = tj - HW, lk = tk - HW;
         const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
         const int sj = lj - 8 * dj, sk = lk - 8 * dk;
-        T *dst = tile + c * S3 + rr * S;
+        T *dst = tile + c * (S2 * RS) + rr * RS;
+        const T *gh = ghost ? ghost + c * T3 + rr * S : nullptr;
         const int dcent = (dk + 1) * 9 + (dj + 1) * 3;
         const int src = snb[dcent + 1];
         if (src >= 0) {
@@ -95,16 +94,40 @@ __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__rest
             for (int q = 0; q < 8; q++) dst[HW + q] = row.v[q];
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; q++) dst[HW + q] = ghost ? ghost[c * T3 + rr * S + HW + q] : T(0);
+            for (int q = 0; q < 8; q++) dst[HW + q] = gh ? gh[HW + q] : T(0);
         }
         const int slo = snb[dcent], shi = snb[dcent + 2];
 #pragma unroll
         for (int h = 0; h < HW; h++) {
             // low end: cells 8-HW+h of the x- neighbour; high end: cells h of the x+ neighbour
-            dst[h] = slo >= 0 ? F[((size_t)slo * NC + c) * B3 + (sk * 8 + sj) * 8 + 8 - HW + h]
-                              : (ghost ? ghost[c * T3 + rr * S + h] : T(0));
+            dst[h] = slo >= 0 ? F[((size_t)slo * NC + c) * B3 + (sk * 8 + sj) * 8 + 8 - HW + h] : (gh ? gh[h] : T(0));
             dst[HW + 8 + h] = shi >= 0 ? F[((size_t)shi * NC + c) * B3 + (sk * 8 + sj) * 8 + h]
-                                       : (ghost ? ghost[c * T3 + rr * S + HW + 8 + h] : T(0));
+                                       : (gh ? gh[HW + 8 + h] : T(0));
+        }
+    }
+}
+
+// Element-wise staging, same tile layout as stage_rows: consecutive threads take consecutive
+// cells of a tile row, so global loads are coalesced along x and shared-memory stores of a
+// warp fall on consecutive addresses (stage_rows, one thread per row, stores 32 different
+// rows at the same column at once, which for padded row strides hits few banks).
+template <typename T, int NC, int HW, int RS>
+__device__ __forceinline__ void stage_cells(T *__restrict__ tile, const T *__restrict__ F, const int *__restrict__ snb,
+                                            const T *__restrict__ ghost) {
+    constexpr int S = 8 + 2 * HW, S2 = S * S, S3 = S2 * S;
+    for (int e = threadIdx.x; e < S3; e += blockDim.x) {
+        const int tk = e / S2, rem = e - tk * S2, tj = rem / S, ti = rem - tj * S;
+        const int li = ti - HW, lj = tj - HW, lk = tk - HW;
+        const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int src = snb[(dk + 1) * 9 + (dj + 1) * 3 + (di + 1)];
+        const int dst = (tk * S + tj) * RS + ti;
+        if (src >= 0) {
+            const T *p = F + (size_t)src * NC * B3 + ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
+#pragma unroll
+            for (int c = 0; c < NC; c++) tile[c * S2 * RS + dst] = p[c * B3];
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; c++) tile[c * S2 * RS + dst] = ghost ? ghost[c * T3 + e] : T(0);
         }
     }
 }
@@ -114,25 +137,9 @@ __device__ __forceinline__ void stage_nbr(int *snb, const int *__restrict__ nbr,
     if (threadIdx.x < 27) snb[threadIdx.x] = __ldg(nbr + b * 27 + threadIdx.x);
 }
 
-// Phi for the face between tile cells p (low) and p + sa.  Components b1 < b2 are the two
-// axes other than a, with tile strides s1, s2.
-template <typename T>
-__device__ __forceinline__ void face_phi(const T *__restrict__ tB, const T *__restrict__ tE, int p, int a,
-                                         int sa, int b1, int s1, int b2, int s2, T &phi1, T &phi2) {
-    const T es = tE[p] + tE[p + sa];
-    const T *Ba = tB + a * T3;
-    const T *B1 = tB + b1 * T3;
-    const T *B2 = tB + b2 * T3;
-    T n1 = B1[p + sa] - B1[p];
-    T t1 = (Ba[p + sa + s1] + Ba[p + s1]) - (Ba[p + sa - s1] + Ba[p - s1]);
-    phi1 = es * (T(0.25) * t1 - n1);
-    T n2 = B2[p + sa] - B2[p];
-    T t2 = (Ba[p + sa + s2] + Ba[p + s2]) - (Ba[p + sa - s2] + Ba[p - s2]);
-    phi2 = es * (T(0.25) * t2 - n2);
-}
-
-// Same for a tile whose components are cs elements apart; the two flux components are the
-// axes other than a in ascending order, with tile strides s1 and s2.
+// Phi = 2hF for the face between tile cells p (low) and p + sa, axis a (Eqs. 4-6, 9-11).
+// The two flux components are the axes other than a in ascending order, with tile strides
+// s1 and s2; components of the tile are cs elements apart.
 template <typename T>
 __device__ __forceinline__ void face_phi_s(const T *__restrict__ tB, const T *__restrict__ tE, int p, int a, int sa,
                                            int s1, int s2, int cs, T &phi1, T &phi2) {
@@ -149,58 +156,57 @@ __device__ __forceinline__ void face_phi_s(const T *__restrict__ tB, const T *__
     phi2 = es * (T(0.25) * t2 - n2);
 }
 
-// All 1728 face fluxes of a staged block into phi[3 axes][2 comps][576]:
-//   x faces (k*8+j)*9+fi, y faces (k*9+fj)*8+i, z faces (fk*8+j)*8+i.
+// Faces of a 10^3 tile along axis a from the low tile cell p, in the geometry of T
 template <typename T>
-__device__ __forceinline__ void all_faces(const T *__restrict__ tB, const T *__restrict__ tE, T *__restrict__ phi) {
-    for (int f = threadIdx.x; f < 3 * 576; f += blockDim.x) {
-        int ax = f / 576, r = f - ax * 576;
-        T p1, p2;
-        if (ax == 0) {
-            int fi = r % 9, j = (r / 9) % 8, k = r / 72;
-            face_phi(tB, tE, tix(fi, j + 1, k + 1), 0, 1, 1, TS, 2, TS * TS, p1, p2);
-        } else if (ax == 1) {
-            int i = r % 8, fj = (r / 8) % 9, k = r / 72;
-            face_phi(tB, tE, tix(i + 1, fj, k + 1), 1, TS, 0, 1, 2, TS * TS, p1, p2);
-        } else {
-            int i = r % 8, j = (r / 8) % 8, fk = r / 64;
-            face_phi(tB, tE, tix(i + 1, j + 1, fk), 2, TS * TS, 0, 1, 1, TS, p1, p2);
-        }
-        phi[(ax * 2 + 0) * 576 + r] = p1;
-        phi[(ax * 2 + 1) * 576 + r] = p2;
-    }
+__device__ __forceinline__ void face10(const T *__restrict__ tB, const T *__restrict__ tE, int p, int a, T &p1, T &p2) {
+    using G = Geo<T>;
+    if (a == 0)
+        face_phi_s(tB, tE, p, 0, 1, G::RS, G::PS, G::CS, p1, p2);
+    else if (a == 1)
+        face_phi_s(tB, tE, p, 1, G::RS, 1, G::PS, G::CS, p1, p2);
+    else
+        face_phi_s(tB, tE, p, 2, G::PS, 1, G::RS, G::CS, p1, p2);
 }
 
-// Same result as all_faces for 512-thread blocks: thread (i,j,k) computes the low x, y and z
-// faces of its cell, then threads 0..191 compute the 3 x 64 faces of the high boundary planes.
+// Offsets of the six flux arrays: x faces [2 comps][64 rows][PX] (index xf), y faces
+// [2][8][9][8] ((k*9+fj)*8+i), z faces [2][9][8][8] ((fk*8+j)*8+i).
+template <typename T>
+__device__ __forceinline__ int phi_base(int ax, int comp) {
+    using G = Geo<T>;
+    return ax == 0 ? comp * G::PHI_X : 2 * G::PHI_X + ((ax - 1) * 2 + comp) * 576;
+}
+
+// All 1728 face fluxes of a staged block (512 threads): thread (i,j,k) computes the low x, y
+// and z faces of its cell, then threads 0..191 compute the 3 x 64 faces of the high planes.
 template <typename T>
 __device__ __forceinline__ void all_faces_512(const T *__restrict__ tB, const T *__restrict__ tE, T *__restrict__ phi) {
+    using G = Geo<T>;
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-    const int p = tix(i + 1, j + 1, k + 1);
+    const int p = G::at(i + 1, j + 1, k + 1);
     T p1, p2;
-    face_phi(tB, tE, p - 1, 0, 1, 1, TS, 2, TS * TS, p1, p2);
-    phi[0 * 576 + (k * 8 + j) * 9 + i] = p1;
-    phi[1 * 576 + (k * 8 + j) * 9 + i] = p2;
-    face_phi(tB, tE, p - TS, 1, TS, 0, 1, 2, TS * TS, p1, p2);
-    phi[2 * 576 + (k * 9 + j) * 8 + i] = p1;
-    phi[3 * 576 + (k * 9 + j) * 8 + i] = p2;
-    face_phi(tB, tE, p - TS * TS, 2, TS * TS, 0, 1, 1, TS, p1, p2);
-    phi[4 * 576 + (k * 8 + j) * 8 + i] = p1;
-    phi[5 * 576 + (k * 8 + j) * 8 + i] = p2;
+    face10(tB, tE, p - 1, 0, p1, p2);
+    phi[G::xf(i, j, k)] = p1;
+    phi[G::PHI_X + G::xf(i, j, k)] = p2;
+    face10(tB, tE, p - G::RS, 1, p1, p2);
+    phi[phi_base<T>(1, 0) + (k * 9 + j) * 8 + i] = p1;
+    phi[phi_base<T>(1, 1) + (k * 9 + j) * 8 + i] = p2;
+    face10(tB, tE, p - G::PS, 2, p1, p2);
+    phi[phi_base<T>(2, 0) + (k * 8 + j) * 8 + i] = p1;
+    phi[phi_base<T>(2, 1) + (k * 8 + j) * 8 + i] = p2;
     if (t < 192) {
         const int ax = t >> 6, u = t & 7, v = (t >> 3) & 7;
         if (ax == 0) {  // x = 8 plane: (j, k) = (u, v)
-            face_phi(tB, tE, tix(8, u + 1, v + 1), 0, 1, 1, TS, 2, TS * TS, p1, p2);
-            phi[0 * 576 + (v * 8 + u) * 9 + 8] = p1;
-            phi[1 * 576 + (v * 8 + u) * 9 + 8] = p2;
+            face10(tB, tE, G::at(8, u + 1, v + 1), 0, p1, p2);
+            phi[G::xf(8, u, v)] = p1;
+            phi[G::PHI_X + G::xf(8, u, v)] = p2;
         } else if (ax == 1) {  // y = 8 plane: (i, k) = (u, v)
-            face_phi(tB, tE, tix(u + 1, 8, v + 1), 1, TS, 0, 1, 2, TS * TS, p1, p2);
-            phi[2 * 576 + (v * 9 + 8) * 8 + u] = p1;
-            phi[3 * 576 + (v * 9 + 8) * 8 + u] = p2;
+            face10(tB, tE, G::at(u + 1, 8, v + 1), 1, p1, p2);
+            phi[phi_base<T>(1, 0) + (v * 9 + 8) * 8 + u] = p1;
+            phi[phi_base<T>(1, 1) + (v * 9 + 8) * 8 + u] = p2;
         } else {  // z = 8 plane: (i, j) = (u, v)
-            face_phi(tB, tE, tix(u + 1, v + 1, 8), 2, TS * TS, 0, 1, 1, TS, p1, p2);
-            phi[4 * 576 + (8 * 8 + v) * 8 + u] = p1;
-            phi[5 * 576 + (8 * 8 + v) * 8 + u] = p2;
+            face10(tB, tE, G::at(u + 1, v + 1, 8), 2, p1, p2);
+            phi[phi_base<T>(2, 0) + (8 * 8 + v) * 8 + u] = p1;
+            phi[phi_base<T>(2, 1) + (8 * 8 + v) * 8 + u] = p2;
         }
     }
 }
@@ -208,20 +214,24 @@ __device__ __forceinline__ void all_faces_512(const T *__restrict__ tB, const T 
 // sum_a (Phi_a(+) - Phi_a(-)) at cell (i,j,k) for the three components
 template <typename T>
 __device__ __forceinline__ void cell_div(const T *__restrict__ phi, int i, int j, int k, T &dx, T &dy, T &dz) {
-    const T *px0 = phi + 0 * 576, *px1 = phi + 1 * 576;  // x faces: comps y, z
-    const T *py0 = phi + 2 * 576, *py1 = phi + 3 * 576;  // y faces: comps x, z
-    const T *pz0 = phi + 4 * 576, *pz1 = phi + 5 * 576;  // z faces: comps x, y
-    int xl = (k * 8 + j) * 9 + i, yl = (k * 9 + j) * 8 + i, zl = (k * 8 + j) * 8 + i;
+    using G = Geo<T>;
+    const T *px0 = phi, *px1 = phi + G::PHI_X;                                // x faces: comps y, z
+    const T *py0 = phi + phi_base<T>(1, 0), *py1 = phi + phi_base<T>(1, 1);  // y faces: comps x, z
+    const T *pz0 = phi + phi_base<T>(2, 0), *pz1 = phi + phi_base<T>(2, 1);  // z faces: comps x, y
+    const int xl = G::xf(i, j, k), yl = (k * 9 + j) * 8 + i, zl = (k * 8 + j) * 8 + i;
     dx = (py0[yl + 8] - py0[yl]) + (pz0[zl + 64] - pz0[zl]);
     dy = (px0[xl + 1] - px0[xl]) + (pz1[zl + 64] - pz1[zl]);
     dz = (px1[xl + 1] - px1[xl]) + (py1[yl + 8] - py1[yl]);
 }
 
-// index of face-plane value (u, v) of side s = 2a + hi in the phi array
-__device__ __forceinline__ int plane_face(int a, int hi, int u, int v) {
-    if (a == 0) return (v * 8 + u) * 9 + (hi ? 8 : 0);
-    if (a == 1) return (v * 9 + (hi ? 8 : 0)) * 8 + u;
-    return ((hi ? 8 : 0) * 8 + v) * 8 + u;
+// index in the flux arrays of the boundary-plane face (u, v) of side s = 2a + hi, where
+// (u, v) run over the two axes other than a in ascending order
+template <typename T>
+__device__ __forceinline__ int plane_face(int a, int hi, int comp, int u, int v) {
+    using G = Geo<T>;
+    if (a == 0) return phi_base<T>(0, comp) + G::xf(hi ? 8 : 0, u, v);
+    if (a == 1) return phi_base<T>(1, comp) + (v * 9 + (hi ? 8 : 0)) * 8 + u;
+    return phi_base<T>(2, comp) + ((hi ? 8 : 0) * 8 + v) * 8 + u;
 }
 
 // Block-wide sum / max in a fixed order (deterministic); the result is valid in thread 0.
@@ -265,10 +275,11 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
                                                    TO *__restrict__ out, TO *__restrict__ out2,
                                                    double *__restrict__ reg, const int *__restrict__ rsrc_tab,
                                                    double *__restrict__ partials, double vol) {
+    using G = Geo<TC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC *tB = reinterpret_cast<TC *>(smem_raw);
-    TC *tE = tB + 3 * T3;
-    TC *phi = tE + T3;
+    TC *tE = tB + 3 * G::CS;
+    TC *phi = tE + G::CS;
     __shared__ TC red[32];
     __shared__ int snb[27];
     const int b = blockIdx.x;
@@ -279,8 +290,8 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_rows<TC, 3, 1>(tB, X, snb, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
-    stage_rows<TC, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_cells<TC, 3, 1, G::RS>(tB, X, snb, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
+    stage_cells<TC, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     all_faces_512(tB, tE, phi);
     __syncthreads();
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
             int ax = s >> 1, hi = s & 1;
             for (int q = threadIdx.x; q < 128; q += blockDim.x) {
                 int comp = q >> 6, uv = q & 63;
-                reg[(size_t)slotr * 128 + q] = (double)phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, uv & 7, uv >> 3)] * inv2h;
+                reg[(size_t)slotr * 128 + q] = (double)phi[plane_face<TC>(ax, hi, comp, uv & 7, uv >> 3)] * inv2h;
             }
         }
     }
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
                 const double *R = reg + (size_t)fslot * 128 + comp * 64;
                 int fu = 2 * (u & 3), fv = 2 * (v & 3);
                 double m = 0.25 * ((R[fv * 8 + fu] + R[fv * 8 + fu + 1]) + (R[(fv + 1) * 8 + fu] + R[(fv + 1) * 8 + fu + 1]));
-                phi[(ax * 2 + comp) * 576 + plane_face(ax, hi, u, v)] = (TC)(m * (2.0 * g.h));
+                phi[plane_face<TC>(ax, hi, comp, u, v)] = (TC)(m * (2.0 * g.h));
             }
         }
     }
@@ -318,12 +329,12 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
     TC dv[3];
     cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
     TC sr = 0, ss = 0, mx = 0;
-    const int p = tix(i + 1, j + 1, k + 1);
+    const int p = G::at(i + 1, j + 1, k + 1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         size_t id = ((size_t)b * 3 + c) * B3 + t;
         TC y = Y ? Y[id] : TC(0);
-        TC o = a * tB[c * T3 + p] + coef * dv[c] + d * y;
+        TC o = a * tB[c * G::CS + p] + coef * dv[c] + d * y;
         out[id] = (TO)o;
         if (out2) out2[id] = (TO)o;
         if (partials) {
@@ -349,7 +360,7 @@ cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const T
                              double a, double c, double d, TO *out, TO *out2, double *reg, const int *rsrc_tab,
                              double *partials, double vol, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
-    const size_t sm = (4 * T3 + 6 * 576) * sizeof(TC);
+    const size_t sm = (4 * Geo<TC>::CS + Geo<TC>::PHI) * sizeof(TC);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_composite<TC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -377,41 +388,42 @@ __global__ void __launch_bounds__(256) k_smooth(GridDev g, const T *__restrict__
                                                 const T *__restrict__ r, const T *__restrict__ eta,
                                                 const T *__restrict__ inv, const T *__restrict__ Ge,
                                                 const T *__restrict__ Geta, T coef, int colour) {
-    __shared__ __align__(16) T tB[3 * T3];
-    __shared__ __align__(16) T tE[T3];
+    using G = Geo<T>;
+    __shared__ __align__(16) T tB[3 * G::CS];
+    __shared__ __align__(16) T tE[G::CS];
     __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_rows<T, 3, 1>(tB, e_in, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
-    stage_rows<T, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_cells<T, 3, 1, G::RS>(tB, e_in, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    stage_cells<T, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     const int t = threadIdx.x;
     const int k = t >> 5, j = (t >> 2) & 7;
-    const int ic = 2 * (t & 3) + ((j + k + colour) & 1);  // colour cell
+    const int ic = 2 * (t & 3) + ((j + k + colour) & 1);      // colour cell
     const int io = 2 * (t & 3) + ((j + k + colour + 1) & 1);  // other colour
-    const int p = tix(ic + 1, j + 1, k + 1);
+    const int p = G::at(ic + 1, j + 1, k + 1);
     T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
-    face_phi(tB, tE, p - 1, 0, 1, 1, TS, 2, TS * TS, xl1, xl2);
-    face_phi(tB, tE, p, 0, 1, 1, TS, 2, TS * TS, xh1, xh2);
-    face_phi(tB, tE, p - TS, 1, TS, 0, 1, 2, TS * TS, yl1, yl2);
-    face_phi(tB, tE, p, 1, TS, 0, 1, 2, TS * TS, yh1, yh2);
-    face_phi(tB, tE, p - TS * TS, 2, TS * TS, 0, 1, 1, TS, zl1, zl2);
-    face_phi(tB, tE, p, 2, TS * TS, 0, 1, 1, TS, zh1, zh2);
+    face10(tB, tE, p - 1, 0, xl1, xl2);
+    face10(tB, tE, p, 0, xh1, xh2);
+    face10(tB, tE, p - G::RS, 1, yl1, yl2);
+    face10(tB, tE, p, 1, yh1, yh2);
+    face10(tB, tE, p - G::PS, 2, zl1, zl2);
+    face10(tB, tE, p, 2, zh1, zh2);
     T dv[3];
     dv[0] = (yh1 - yl1) + (zh1 - zl1);
     dv[1] = (xh1 - xl1) + (zh2 - zl2);
     dv[2] = (xh2 - xl2) + (yh2 - yl2);
     const int cc = (k * 8 + j) * 8 + ic, co = (k * 8 + j) * 8 + io;
-    const int po = tix(io + 1, j + 1, k + 1);
+    const int po = G::at(io + 1, j + 1, k + 1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         size_t base = ((size_t)b * 3 + c) * B3;
-        T ev = tB[c * T3 + p];
+        T ev = tB[c * G::CS + p];
         T res = r[base + cc] - ev - coef * dv[c];
         e_out[base + cc] = ev + res * inv[base + cc];
-        e_out[base + co] = tB[c * T3 + po];
+        e_out[base + co] = tB[c * G::CS + po];
     }
 }
 
@@ -436,8 +448,13 @@ template cudaError_t launch_smooth<float>(const GridDev &, const float *, float 
 // the ones the neighbouring blocks compute, in the same order with the same arithmetic, so
 // the result equals two global colour passes.  The inverse diagonal is formed on the fly
 // from eta (Eqs. 21-23).  e_in and e_out are distinct buffers.
-constexpr int RS = 12, R3 = RS * RS * RS;
-__device__ __forceinline__ int rix(int i, int j, int k) { return (k * RS + j) * RS + i; }
+// Rows of the 12^3 tile are RRS elements apart: for float32, 8 rows of 4 same-colour cells
+// (stride 2, the black-phase warp pattern) then fall on 32 distinct banks.
+template <typename T>
+struct G12 {
+    static constexpr int S = 12, RRS = sizeof(T) == 4 ? 20 : 12, PS = S * RRS, CS = S * PS;
+    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i; }
+};
 // smoother division: the hardware reciprocal in float32 (a smoothing weight needs no
 // correctly rounded quotient), exact division in float64
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
@@ -446,22 +463,23 @@ __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 template <typename T>
 __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
                                           const T rr[3], T out[3]) {
+    using G = G12<T>;
     T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
-    face_phi_s(tB, tE, p - 1, 0, 1, RS, RS * RS, R3, xl1, xl2);
-    face_phi_s(tB, tE, p, 0, 1, RS, RS * RS, R3, xh1, xh2);
-    face_phi_s(tB, tE, p - RS, 1, RS, 1, RS * RS, R3, yl1, yl2);
-    face_phi_s(tB, tE, p, 1, RS, 1, RS * RS, R3, yh1, yh2);
-    face_phi_s(tB, tE, p - RS * RS, 2, RS * RS, 1, RS, R3, zl1, zl2);
-    face_phi_s(tB, tE, p, 2, RS * RS, 1, RS, R3, zh1, zh2);
+    face_phi_s(tB, tE, p - 1, 0, 1, G::RRS, G::PS, G::CS, xl1, xl2);
+    face_phi_s(tB, tE, p, 0, 1, G::RRS, G::PS, G::CS, xh1, xh2);
+    face_phi_s(tB, tE, p - G::RRS, 1, G::RRS, 1, G::PS, G::CS, yl1, yl2);
+    face_phi_s(tB, tE, p, 1, G::RRS, 1, G::PS, G::CS, yh1, yh2);
+    face_phi_s(tB, tE, p - G::PS, 2, G::PS, 1, G::RRS, G::CS, zl1, zl2);
+    face_phi_s(tB, tE, p, 2, G::PS, 1, G::RRS, G::CS, zh1, zh2);
     const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
     const T e0 = tE[p];
     const T sx = e0 + T(0.5) * (tE[p + 1] + tE[p - 1]);
-    const T sy = e0 + T(0.5) * (tE[p + RS] + tE[p - RS]);
-    const T sz = e0 + T(0.5) * (tE[p + RS * RS] + tE[p - RS * RS]);
+    const T sy = e0 + T(0.5) * (tE[p + G::RRS] + tE[p - G::RRS]);
+    const T sz = e0 + T(0.5) * (tE[p + G::PS] + tE[p - G::PS]);
     const T al[3] = {lh2 * (sy + sz), lh2 * (sz + sx), lh2 * (sx + sy)};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        T ev = tB[c * R3 + p];
+        T ev = tB[c * G::CS + p];
         T res = rr[c] - ev - coef * dv[c];
         out[c] = ev + fast_div(res, T(1) + al[c]);
     }
@@ -470,17 +488,17 @@ __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__r
 template <typename T>
 __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restrict__ e_in, T *__restrict__ e_out,
                                                    const T *__restrict__ r, const T *__restrict__ eta, T coef, T lh2) {
+    using G = G12<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tB = reinterpret_cast<T *>(smem_raw);  // [3][12^3]
-    T *tE = tB + 3 * R3;                      // [12^3]
+    T *tB = reinterpret_cast<T *>(smem_raw);  // [3][12 planes][12 rows][RRS]
+    T *tE = tB + 3 * G::CS;
     __shared__ int snb[27];
     const int b = blockIdx.x;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_rows<T, 3, 2>(tB, e_in, snb, nullptr);
-    stage_rows<T, 1, 2>(tE, eta, snb, nullptr);
+    stage_cells<T, 3, 2, G::RRS>(tB, e_in, snb, nullptr);
+    stage_cells<T, 1, 2, G::RRS>(tE, eta, snb, nullptr);
     __syncthreads();
-    // red cells ((i+j+k) even) of the block and its face/edge ring: the 10^3 box without corners
     // The 500 red positions of the 10^3 box, 5 per x-row, enumerated densely: thread t owns
     // red positions t and t + 256 (launch uses 256); the 4 red box corners are skipped.
     T nv[2][3];
@@ -497,17 +515,17 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
         const int nout = (li < 0 || li > 7) + (lj < 0 || lj > 7) + (lk < 0 || lk > 7);
         if (nout == 3) continue;
         const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
-        const int src = (di | dj | dk) ? __ldg(g.nbr + b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1)) : b;
+        const int src = snb[(dk + 1) * 9 + (dj + 1) * 3 + (di + 1)];
         const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
         const T rr[3] = {r[(size_t)src * 3 * B3 + off], r[(size_t)src * 3 * B3 + B3 + off], r[(size_t)src * 3 * B3 + 2 * B3 + off]};
-        np[s4] = rix(li + 2, lj + 2, lk + 2);
+        np[s4] = G::at(li + 2, lj + 2, lk + 2);
         rb_update(tB, tE, np[s4], coef, lh2, rr, nv[s4]);
     }
     __syncthreads();
 #pragma unroll
     for (int s4 = 0; s4 < 2; s4++)
         if (np[s4] >= 0)
-            for (int c = 0; c < 3; c++) tB[c * R3 + np[s4]] = nv[s4][c];
+            for (int c = 0; c < 3; c++) tB[c * G::CS + np[s4]] = nv[s4][c];
     __syncthreads();
     // black cells of the block, one per thread, then the whole block is written out
     const int t = threadIdx.x;
@@ -516,12 +534,12 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     const int cb = (k * 8 + j) * 8 + ib, cr = (k * 8 + j) * 8 + ir;
     const T rr[3] = {r[(size_t)b * 3 * B3 + cb], r[(size_t)b * 3 * B3 + B3 + cb], r[(size_t)b * 3 * B3 + 2 * B3 + cb]};
     T out[3];
-    const int pb = rix(ib + 2, j + 2, k + 2), pr = rix(ir + 2, j + 2, k + 2);
+    const int pb = G::at(ib + 2, j + 2, k + 2), pr = G::at(ir + 2, j + 2, k + 2);
     rb_update(tB, tE, pb, coef, lh2, rr, out);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         e_out[((size_t)b * 3 + c) * B3 + cb] = out[c];
-        e_out[((size_t)b * 3 + c) * B3 + cr] = tB[c * R3 + pr];
+        e_out[((size_t)b * 3 + c) * B3 + cr] = tB[c * G::CS + pr];
     }
 }
 
@@ -529,7 +547,7 @@ template <typename T>
 cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta, double lamdt,
                              cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
-    const size_t sm = 4 * R3 * sizeof(T);
+    const size_t sm = 4 * G12<T>::CS * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_smooth_rb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -550,20 +568,21 @@ template cudaError_t launch_smooth_rb<double>(const GridDev &, const double *, d
 template <typename T>
 __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict__ eta, const T *__restrict__ Geta,
                                                  double lh2, T *__restrict__ inv) {
-    __shared__ T tE[T3];
+    using G = Geo<T>;
+    __shared__ T tE[G::CS];
     __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_rows<T, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_cells<T, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-    const int p = tix(i + 1, j + 1, k + 1);
+    const int p = G::at(i + 1, j + 1, k + 1);
     const double e0 = (double)tE[p];
     const double sa[3] = {0.5 * (e0 + (double)tE[p + 1]) + 0.5 * (e0 + (double)tE[p - 1]),
-                          0.5 * (e0 + (double)tE[p + TS]) + 0.5 * (e0 + (double)tE[p - TS]),
-                          0.5 * (e0 + (double)tE[p + TS * TS]) + 0.5 * (e0 + (double)tE[p - TS * TS])};
+                          0.5 * (e0 + (double)tE[p + G::RS]) + 0.5 * (e0 + (double)tE[p - G::RS]),
+                          0.5 * (e0 + (double)tE[p + G::PS]) + 0.5 * (e0 + (double)tE[p - G::PS])};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         double al = 0.0;
@@ -588,18 +607,19 @@ __global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__re
                                                         const T *__restrict__ eta, const T *__restrict__ Ge,
                                                         const T *__restrict__ Geta, T coef, T *__restrict__ t_out,
                                                         T *__restrict__ coarse, T *__restrict__ lex, int3 ld) {
+    using G = Geo<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tB = reinterpret_cast<T *>(smem_raw);
-    T *tE = tB + 3 * T3;
-    T *phi = tE + T3;
-    T *tt = phi + 6 * 576;
+    T *tE = tB + 3 * G::CS;
+    T *phi = tE + G::CS;
+    T *tt = phi + G::PHI;
     __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_rows<T, 3, 1>(tB, e, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
-    stage_rows<T, 1, 1>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_cells<T, 3, 1, G::RS>(tB, e, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    stage_cells<T, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     all_faces_512(tB, tE, phi);
     __syncthreads();
@@ -607,11 +627,11 @@ __global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__re
         const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
         T dv[3];
         cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
-        const int p = tix(i + 1, j + 1, k + 1);
+        const int p = G::at(i + 1, j + 1, k + 1);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             size_t id = ((size_t)b * 3 + c) * B3 + t;
-            T v = r[id] - tB[c * T3 + p] - coef * dv[c];
+            T v = r[id] - tB[c * G::CS + p] - coef * dv[c];
             tt[c * B3 + t] = v;
             if (t_out) t_out[id] = v;
         }
@@ -641,7 +661,7 @@ template <typename T>
 cudaError_t launch_resid_restrict(const GridDev &g, const T *e, const T *r, const T *eta, const T *Ge, const T *Geta,
                                   double lamdt, T *t_out, T *coarse, T *lex, const int *ldims, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
-    const size_t sm = (4 * T3 + 6 * 576 + 3 * B3) * sizeof(T);
+    const size_t sm = (4 * Geo<T>::CS + Geo<T>::PHI + 3 * B3) * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_resid_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -983,76 +1003,92 @@ template cudaError_t launch_convert<double, double>(const double *, double *, si
 // ------------------------------------------------------------------ Krylov vector kernels
 // Vectors are block fields [nblk][3][512]; inner products are volume weighted over leaf
 // blocks (weight w_b = h^3, 0 for covered blocks), the norm of the convergence tests.
-// Thread block c folds the 8^3 blocks [c*per, (c+1)*per): per block, each thread forms 6
-// float32 products per column and adds them, times the block weight, to float64 totals;
-// per-thread-block results go to part[c][col] (fixed order: deterministic).
+// One warp per 8^3 block: each lane forms 12 float4 products per column in float32, the warp
+// reduces them by shuffles, the sum is weighted in float64; the 8 warps of a thread block are
+// folded in warp order into part[blockIdx][col] (fixed order: deterministic).
 __global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
                                               int nblk, double *__restrict__ part) {
-    __shared__ double red[32];
+    __shared__ double sred[8][KMAX + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
     const int ncol = V.k + 1;
-    const int per = (nblk + gridDim.x - 1) / gridDim.x;
-    const int b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
-    double acc[KMAX + 1];
+    float f[KMAX + 1];
 #pragma unroll
-    for (int i = 0; i <= KMAX; i++) acc[i] = 0.0;
-    for (int b = b0; b < b1; b++) {
-        const double wt = wb[b];
-        if (wt == 0.0) continue;
-        const size_t base = (size_t)b * 1536 + threadIdx.x;
-        float f[KMAX + 1];
-#pragma unroll
-        for (int i = 0; i <= KMAX; i++) f[i] = 0.f;
-#pragma unroll
-        for (int s = 0; s < 6; s++) {
-            const float x = w[base + 256 * s];
-            f[KMAX] += x * x;
+    for (int i = 0; i <= KMAX; i++) f[i] = 0.f;
+    const double wt = b < nblk ? wb[b] : 0.0;
+    if (wt != 0.0) {
+        const float4 *w4 = reinterpret_cast<const float4 *>(w + (size_t)b * 1536);
+#pragma unroll 4
+        for (int s = 0; s < 12; s++) {
+            const float4 x = w4[lane + 32 * s];
+            f[KMAX] += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
 #pragma unroll
             for (int i = 0; i < KMAX; i++)
-                if (i < V.k) f[i] += x * V.v[i][base + 256 * s];
+                if (i < V.k) {
+                    const float4 v = reinterpret_cast<const float4 *>(V.v[i] + (size_t)b * 1536)[lane + 32 * s];
+                    f[i] += x.x * v.x + x.y * v.y + x.z * v.z + x.w * v.w;
+                }
         }
-#pragma unroll
-        for (int i = 0; i <= KMAX; i++) acc[i] += (double)f[i] * wt;
     }
 #pragma unroll
     for (int i = 0; i <= KMAX; i++) {
         if (i > V.k) break;
-        double s = block_sum(i == V.k ? acc[KMAX] : acc[i < KMAX ? i : KMAX], red);
-        if (threadIdx.x == 0) part[(size_t)blockIdx.x * ncol + i] = s;
+        float s = i == V.k ? f[KMAX] : f[i < KMAX ? i : KMAX];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sred[warp][i] = (double)s * wt;
+    }
+    __syncthreads();
+    if (threadIdx.x < ncol) {
+        double a = 0.0;
+        for (int q = 0; q < 8; q++) a += sred[q][threadIdx.x];
+        part[(size_t)blockIdx.x * ncol + threadIdx.x] = a;
     }
 }
 
-// column sums of part[nblk][ncol] in a fixed order (one thread block per column)
-__global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part, int nblk, int ncol, double *__restrict__ out) {
+// column sums of part[nrow][ncol] in a fixed order (one thread block per column)
+__global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part, int nrow, int ncol, double *__restrict__ out) {
     __shared__ double red[32];
     const int c = blockIdx.x;
     double a = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += part[(size_t)b * ncol + c];
+    for (int b = threadIdx.x; b < nrow; b += blockDim.x) a += part[(size_t)b * ncol + c];
     double s = block_sum(a, red);
     if (threadIdx.x == 0) out[c] = s;
 }
 
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
                         cudaStream_t s) {
-    const int grid = std::min(nblk, 152 * 4);
+    const int grid = (nblk + 7) / 8;
     k_mdot<<<grid, 256, 0, s>>>(w, V, wb, nblk, part);
     k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out);
     return cudaGetLastError();
 }
 
-// dst = (src - sum_i c_i v_i) * scale   (dst may equal src)
-__global__ void k_maxpy(float *dst, const float *src, VecSet V, float scale, size_t n) {
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        float x = src[q];
+// dst = (src - sum_i c_i v_i) * scale (dst may equal src); float4 over n/4 groups
+__global__ void __launch_bounds__(256) k_maxpy(float4 *dst, const float4 *src, VecSet V, float scale, size_t n4) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
+        float4 x = src[q];
 #pragma unroll
         for (int i = 0; i < KMAX; i++)
-            if (i < V.k) x -= V.c[i] * V.v[i][q];
-        dst[q] = x * scale;
+            if (i < V.k) {
+                const float4 v = reinterpret_cast<const float4 *>(V.v[i])[q];
+                const float c = V.c[i];
+                x.x -= c * v.x;
+                x.y -= c * v.y;
+                x.z -= c * v.z;
+                x.w -= c * v.w;
+            }
+        x.x *= scale;
+        x.y *= scale;
+        x.z *= scale;
+        x.w *= scale;
+        dst[q] = x;
     }
 }
 
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s) {
-    int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-    k_maxpy<<<grid, 256, 0, s>>>(dst, src, V, scale, n);
+    const size_t n4 = n / 4;  // fields are whole 8^3 blocks: n is a multiple of 1536
+    int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
+    k_maxpy<<<grid, 256, 0, s>>>(reinterpret_cast<float4 *>(dst), reinterpret_cast<const float4 *>(src), V, scale, n4);
     return cudaGetLastError();
 }
 
