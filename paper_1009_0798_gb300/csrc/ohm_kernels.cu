@@ -24,22 +24,24 @@ __device__ __forceinline__ int tix(int i, int j, int k) { return (k * TS + j) * 
 // elements apart: for float32 a warp reading 4 rows x 8 cells then hits 32 distinct banks
 // (RS = 24 = 8 mod 16); float64 kernels are bound by the float64 pipe, not by shared memory,
 // and keep the compact stride.  PX is the row stride of the x-face flux array.
+// Tile x index ti sits at row offset OFF + ti, so that the 8 interior cells of a float32 row
+// start on a 16-byte boundary (stored as two 128-bit words when the tile is staged).
 template <typename T>
 struct G10;
 template <>
 struct G10<float> {
-    static constexpr int RS = 24, PX = 24;
+    static constexpr int RS = 24, PX = 24, OFF = 3;
 };
 template <>
 struct G10<double> {
-    static constexpr int RS = 10, PX = 9;
+    static constexpr int RS = 10, PX = 9, OFF = 0;
 };
 template <typename T>
 struct Geo {
-    static constexpr int RS = G10<T>::RS, PS = TS * RS, CS = TS * PS, PX = G10<T>::PX;
+    static constexpr int RS = G10<T>::RS, PS = TS * RS, CS = TS * PS, PX = G10<T>::PX, OFF = G10<T>::OFF;
     static constexpr int PHI_X = 64 * PX;  // x faces per component
     static constexpr int PHI = 2 * PHI_X + 4 * 576;
-    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RS + i; }
+    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RS + i + OFF; }
     __device__ static __forceinline__ int xf(int fi, int j, int k) { return (k * 8 + j) * PX + fi; }
 };
 
@@ -74,24 +76,36 @@ __device__ __forceinline__ Row8<double> load_row8(const double *__restrict__ p) 
 // each end from the x-neighbours of that block.  Rows or cells of an absent neighbour come
 // from `ghost` ([NC][10^3] compact, HW = 1 only) or are zero.  Values at the corners of the
 // box are never read by the stencil and may be left stale.
-template <typename T, int NC, int HW, int RS>
+template <typename T>
+__device__ __forceinline__ void store_row8(T *dst, const Row8<T> &row, bool aligned16) {
+    if (sizeof(T) == 4 && aligned16) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        d4[0] = make_float4((float)row.v[0], (float)row.v[1], (float)row.v[2], (float)row.v[3]);
+        d4[1] = make_float4((float)row.v[4], (float)row.v[5], (float)row.v[6], (float)row.v[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) dst[q] = row.v[q];
+    }
+}
+
+template <typename T, int NC, int HW, int RS, int OFF = 0>
 __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__restrict__ F, const int *__restrict__ snb,
                                            const T *__restrict__ ghost) {
     constexpr int S = 8 + 2 * HW, S2 = S * S;
+    constexpr bool A16 = sizeof(T) == 4 && (OFF + HW) % 4 == 0 && RS % 4 == 0;
     for (int task = threadIdx.x; task < NC * S2; task += blockDim.x) {
         const int c = task / S2, rr = task - c * S2;
         const int tj = rr % S, tk = rr / S;
         const int lj = tj - HW, lk = tk - HW;
         const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
         const int sj = lj - 8 * dj, sk = lk - 8 * dk;
-        T *dst = tile + c * (S2 * RS) + rr * RS;
+        T *dst = tile + c * (S2 * RS) + rr * RS + OFF;
         const T *gh = ghost ? ghost + c * T3 + rr * S : nullptr;
         const int dcent = (dk + 1) * 9 + (dj + 1) * 3;
         const int src = snb[dcent + 1];
         if (src >= 0) {
             const Row8<T> row = load_row8(F + ((size_t)src * NC + c) * B3 + (sk * 8 + sj) * 8);
-#pragma unroll
-            for (int q = 0; q < 8; q++) dst[HW + q] = row.v[q];
+            store_row8(dst + HW, row, A16);
         } else {
 #pragma unroll
             for (int q = 0; q < 8; q++) dst[HW + q] = gh ? gh[HW + q] : T(0);
@@ -290,8 +304,8 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_cells<TC, 3, 1, G::RS>(tB, X, snb, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
-    stage_cells<TC, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_rows<TC, 3, 1, G::RS, G::OFF>(tB, X, snb, slot >= 0 && Gx ? Gx + (size_t)slot * 3 * T3 : nullptr);
+    stage_rows<TC, 1, 1, G::RS, G::OFF>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     all_faces_512(tB, tE, phi);
     __syncthreads();
@@ -396,8 +410,8 @@ __global__ void __launch_bounds__(256) k_smooth(GridDev g, const T *__restrict__
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_cells<T, 3, 1, G::RS>(tB, e_in, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
-    stage_cells<T, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_rows<T, 3, 1, G::RS, G::OFF>(tB, e_in, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    stage_rows<T, 1, 1, G::RS, G::OFF>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     const int t = threadIdx.x;
     const int k = t >> 5, j = (t >> 2) & 7;
@@ -452,8 +466,8 @@ template cudaError_t launch_smooth<float>(const GridDev &, const float *, float 
 // (stride 2, the black-phase warp pattern) then fall on 32 distinct banks.
 template <typename T>
 struct G12 {
-    static constexpr int S = 12, RRS = sizeof(T) == 4 ? 20 : 12, PS = S * RRS, CS = S * PS;
-    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i; }
+    static constexpr int S = 12, RRS = sizeof(T) == 4 ? 20 : 12, PS = S * RRS, CS = S * PS, OFF = sizeof(T) == 4 ? 2 : 0;
+    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
 };
 // smoother division: the hardware reciprocal in float32 (a smoothing weight needs no
 // correctly rounded quotient), exact division in float64
@@ -496,24 +510,47 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     const int b = blockIdx.x;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_cells<T, 3, 2, G::RRS>(tB, e_in, snb, nullptr);
-    stage_cells<T, 1, 2, G::RRS>(tE, eta, snb, nullptr);
+    stage_rows<T, 3, 2, G::RRS, G::OFF>(tB, e_in, snb, nullptr);
+    stage_rows<T, 1, 2, G::RRS, G::OFF>(tE, eta, snb, nullptr);
     __syncthreads();
-    // The 500 red positions of the 10^3 box, 5 per x-row, enumerated densely: thread t owns
-    // red positions t and t + 256 (launch uses 256); the 4 red box corners are skipped.
+    // Red cells ((i+j+k) even): the block's 256, one per thread in the same pattern as the black
+    // phase (a warp reads 8 rows x 4 cells of one plane: distinct banks), then the 240 of the
+    // ring (faces and edges of the 10^3 box, corners excluded), one per thread t < 240:
+    // t < 192: face slab f = t/32 (axis f/2 at -1 or 8), 8 lines x 4 red cells;
+    // t >= 192: edge e = (t-192)/4 (two axes out), 4 red cells along the third axis.
     T nv[2][3];
     int np[2];
 #pragma unroll
     for (int s4 = 0; s4 < 2; s4++) {
         np[s4] = -1;
-        const int q = threadIdx.x + 256 * s4;
-        if (q >= 500) continue;
-        const int row = q / 5, pos = q - row * 5;
-        const int tj = row % TS, tk = row / TS;
-        const int ti = 2 * pos + ((tj + tk + 1) & 1);
-        const int li = ti - 1, lj = tj - 1, lk = tk - 1;
-        const int nout = (li < 0 || li > 7) + (lj < 0 || lj > 7) + (lk < 0 || lk > 7);
-        if (nout == 3) continue;
+        const int t = threadIdx.x;
+        int li, lj, lk;
+        if (s4 == 0) {
+            lk = t >> 5;
+            lj = (t >> 2) & 7;
+            li = 2 * (t & 3) + ((lj + lk) & 1);
+        } else {
+            if (t >= 240) continue;
+            int c[3];
+            if (t < 192) {
+                const int f = t >> 5, ax = f >> 1, q = t & 31;
+                const int v = q >> 2, u2 = q & 3;
+                const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+                c[ax] = (f & 1) ? 8 : -1;
+                c[a2] = v;
+                c[a1] = 2 * u2 + ((c[ax] + v) & 1);
+            } else {
+                const int e = (t - 192) >> 2, w2 = (t - 192) & 3;
+                const int pr = e >> 2, sg = e & 3;  // axis pair (0,1), (0,2), (1,2) and its sign combination
+                const int a1 = pr == 2 ? 1 : 0, a2 = pr == 0 ? 1 : 2, af = 3 - a1 - a2;
+                c[a1] = (sg & 1) ? 8 : -1;
+                c[a2] = (sg & 2) ? 8 : -1;
+                c[af] = 2 * w2 + ((c[a1] + c[a2]) & 1);
+            }
+            li = c[0];
+            lj = c[1];
+            lk = c[2];
+        }
         const int di = li < 0 ? -1 : (li > 7 ? 1 : 0), dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
         const int src = snb[(dk + 1) * 9 + (dj + 1) * 3 + (di + 1)];
         const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
@@ -569,13 +606,13 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict__ eta, const T *__restrict__ Geta,
                                                  double lh2, T *__restrict__ inv) {
     using G = Geo<T>;
-    __shared__ T tE[G::CS];
+    __shared__ __align__(16) T tE[G::CS];
     __shared__ int snb[27];
     const int b = blockIdx.x;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_cells<T, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_rows<T, 1, 1, G::RS, G::OFF>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
     const int p = G::at(i + 1, j + 1, k + 1);
@@ -618,8 +655,8 @@ __global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__re
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
-    stage_cells<T, 3, 1, G::RS>(tB, e, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
-    stage_cells<T, 1, 1, G::RS>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
+    stage_rows<T, 3, 1, G::RS, G::OFF>(tB, e, snb, slot >= 0 && Ge ? Ge + (size_t)slot * 3 * T3 : nullptr);
+    stage_rows<T, 1, 1, G::RS, G::OFF>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
     all_faces_512(tB, tE, phi);
     __syncthreads();
