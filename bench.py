@@ -44,6 +44,9 @@ def args_parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--only", choices=["fgmres", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
+    p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
+    p.add_argument("--n-coarse", type=int, default=16, help="sweeps on the coarsest grid")
+    p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
     return p.parse_args()
 
 
@@ -276,11 +279,13 @@ def run_ours(args):
     eta = torch.from_numpy(np.ascontiguousarray(wl.eta)).cuda()
     B = torch.empty_like(B0)
     hbm_peak, peak_src = peaks()
+    nu = tuple(int(v) for v in args.nu.split(","))
+    KRYLOV = args.krylov
 
     def make(precision, krylov=0):
         g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam,
-                                     precision=precision, nu_pre=2, nu_post=2, n_coarse=16, max_outer=400,
-                                     stream=stream, krylov=krylov)
+                                     precision=precision, nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse,
+                                     max_outer=400, stream=stream, krylov=krylov)
         ohm.ohm_set_eta(g, eta)
         return g
 
@@ -322,12 +327,14 @@ def run_ours(args):
         g1 = make(prec, KRYLOV if args.only == "fgmres" else 0)
         for _ in range(args.warmup):
             run_steps(ohm, g1, B, B0, eta, wl, 1, stream)
-        t0 = time.perf_counter()
-        infos = run_steps(ohm, g1, B, B0, eta, wl, args.steps, stream)
-        dt_s = time.perf_counter() - t0
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        infos = run_steps(ohm, g1, B, B0, eta, wl, args.steps, stream, evs)
+        ms = evs[0].elapsed_time(evs[args.steps])
         if rank == 0:
-            print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "host_seconds": dt_s,
-                              "cycles_per_step": [s["cycles"] for s in infos]}), flush=True)
+            print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "nu": nu,
+                              "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only == "fgmres" else 0,
+                              "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos]}),
+                  flush=True)
         return
 
     # headline: float32 multigrid, FGMRES-accelerated, inside float64 iterative refinement
@@ -408,7 +415,7 @@ def run_ours(args):
             "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
             "config": {"workload": f"resistive_bump_{args.size}^3", "cells": cells, "tol": wl.tol,
                        "dt_over_explicit_limit": 100, "cn_steps_per_run": args.steps, "precision": "mixed",
-                       "multigrid": f"V(2,2), 16 coarsest sweeps; float32 inner solve FGMRES({KRYLOV}) "
+                       "multigrid": f"V({nu[0]},{nu[1]}), {args.n_coarse} coarsest sweeps; float32 inner solve FGMRES({KRYLOV}) "
                                     "right-preconditioned by the V-cycle; float64 iterative refinement",
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (402 MB per float64 field vs 129 MB L2), no flush"},
