@@ -47,6 +47,8 @@ def args_parse():
     p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
     p.add_argument("--n-coarse", type=int, default=16, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
+    p.add_argument("--inner-tol", type=float, default=1e-5,
+                   help="residual reduction asked of each float32 inner solve (mixed precision)")
     return p.parse_args()
 
 
@@ -285,7 +287,8 @@ def run_ours(args):
     def make(precision, krylov=0):
         g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam,
                                      precision=precision, nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse,
-                                     max_outer=400, stream=stream, krylov=krylov)
+                                     max_outer=400, stream=stream, krylov=krylov,
+                                     inner_tol=args.inner_tol if precision == ohm.OHM_MIXED else 0.0)
         ohm.ohm_set_eta(g, eta)
         return g
 
@@ -333,6 +336,7 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "nu": nu,
                               "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only == "fgmres" else 0,
+                              "inner_tol": args.inner_tol,
                               "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos]}),
                   flush=True)
         return

@@ -62,6 +62,10 @@ typedef struct {
                                    FGMRES(m) right-preconditioned by the same V-cycle (not in
                                    the paper; same converged solution, fewer cycles).  Must be
                                    0 for OHM_FP64.                                              */
+    double inner_tol;           /* OHM_MIXED: each float32 inner solve reduces its residual by
+                                   max(inner_tol, 0.3 tol / current ||R||/||S||); 0 selects
+                                   1e-5.  Values below ~1e-6 ask more than float32 can give: the
+                                   inner solve then stops when it stagnates.                   */
     void *stream;               /* cudaStream_t used for all work, NULL = legacy default      */
 } ohm_hier_desc;
 

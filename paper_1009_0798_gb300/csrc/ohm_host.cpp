@@ -785,9 +785,11 @@ int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *
 // Mixed precision as iterative refinement around Eqs. 16-18: the float64 residual
 // R = S - L B is handed to a float32 multigrid solve of L e = R (V-cycles, each followed by
 // the float32 composite residual of the correction equation) until that inner residual has
-// dropped by max(1e-4, 0.3 tol / ||R||/||S||), then B += e in float64.  max_outer bounds the
-// total number of V-cycles of the step.
-constexpr double INNER_FLOOR = 1e-4;
+// dropped by max(inner_tol, 0.3 tol / ||R||/||S||) (inner_tol 1e-5 unless the descriptor sets
+// it), then B += e in float64.  max_outer bounds the total number of V-cycles of the step.
+constexpr double INNER_FLOOR_DEFAULT = 1e-5;
+
+double inner_floor(const ohm_hier *H) { return H->d.inner_tol > 0 ? H->d.inner_tol : INNER_FLOOR_DEFAULT; }
 
 // Weighted inner products <w, v_i> (i < S.k) and <w, w>, read back to the host.
 int mdot(ohm_hier *H, const float *w, const VecSet &S, double *out) {
@@ -811,7 +813,8 @@ int apply_L32(ohm_hier *H, float *x, const float *y, double a, double c, double 
 // Float32 inner solve of L x = rout by FGMRES(m) (Saad 1993), right-preconditioned by one
 // V-cycle per Arnoldi step, classical Gram-Schmidt in the leaf-volume inner product, Givens
 // rotations on the host, restarts from the true residual.  Stops when the residual has
-// dropped by `target` or the step's V-cycle budget is used.  x is left in eacc.
+// dropped by `target`, when a whole restart cycle gained less than a factor 2 (float32 has
+// nothing more to give), or when the step's V-cycle budget is used.  x is left in eacc.
 int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
     const int m = H->d.krylov;
     const size_t nel = (size_t)H->nblocks * 3 * B3;
@@ -824,7 +827,7 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
     if ((st = mdot(H, rhs, none, nn))) return st;
     const double beta0 = std::sqrt(nn[0]);
     if (!(beta0 > 0) || !std::isfinite(beta0)) return OHM_OK;
-    double beta = beta0;
+    double beta = beta0, beta_restart = beta0;
     CK(launch_maxpy(H->kv[0], rhs, none, (float)(1.0 / beta), nel, H->s));
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     auto h = [&](int i, int j) -> double & { return Hm[(size_t)i * m + j]; };
@@ -910,7 +913,8 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
         if ((st = apply_L32(H, x, rhs, -1.0, -lamdt, 1.0, H->kv[0], lamdt))) return st;
         if ((st = mdot(H, H->kv[0], none, nn))) return st;
         beta = std::sqrt(std::max(nn[0], 0.0));
-        if (beta <= target * beta0 || !(beta > 0)) break;
+        if (beta <= target * beta0 || !(beta > 0) || beta > 0.5 * beta_restart) break;
+        beta_restart = beta;
         CK(launch_maxpy(H->kv[0], H->kv[0], none, (float)(1.0 / beta), nel, H->s));
     }
     return OHM_OK;
@@ -946,11 +950,13 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
             result = tol >= 0 ? OHM_ERR_NOT_CONVERGED : OHM_OK;
             break;
         }
-        const double target = tol >= 0 ? std::max(INNER_FLOOR, 0.3 * tol / std::max(nr[0], 1e-300)) : INNER_FLOOR;
+        const double fl = inner_floor(H);
+        const double target = tol >= 0 ? std::max(fl, 0.3 * tol / std::max(nr[0], 1e-300)) : fl;
         if (H->d.krylov > 0) {
             if ((st = inner_fgmres(H, lamdt, target, &cycles))) return st;
         } else {
         CK(cudaMemsetAsync(eacc, 0, nbytes, H->s));
+        double prev = 1.0;
         while (cycles < H->d.max_outer) {
             if ((st = vcycle<T>(H, lamdt))) return st;
             for (auto &g : H->amr)
@@ -963,7 +969,9 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
                 return st;
             double ni[4];
             if ((st = read_norms(H, ni, &ef))) return st;
-            if (!std::isfinite(ni[0]) || ni[0] <= target) break;
+            // stop at the target, or when a cycle gains less than 10% (float32 stagnation)
+            if (!std::isfinite(ni[0]) || ni[0] <= target || ni[0] > 0.9 * prev) break;
+            prev = ni[0];
         }
         }
         if ((st = update_all<T>(H, B, eacc))) return st;
@@ -994,6 +1002,7 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
         err = "krylov must be 0, or 1..11 with OHM_MIXED";
         return false;
     }
+    if (!(d->inner_tol >= 0 && d->inner_tol < 1)) { err = "inner_tol must be in [0, 1)"; return false; }
     for (int a = 0; a < 3; a++)
         if (((int64_t)d->base_cells[a] << (d->nlevels - 1)) >= (1 << 20)) { err = "level too fine"; return false; }
     return true;

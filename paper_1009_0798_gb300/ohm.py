@@ -35,7 +35,7 @@ class HierDesc(C.Structure):
     _fields_ = [("base_cells", C.c_int32 * 3), ("dx0", C.c_double), ("nlevels", C.c_int32), ("nblocks", C.c_int64),
                 ("block_lijk", C.POINTER(C.c_int32)), ("lam", C.c_double), ("precision", C.c_int32),
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32), ("max_outer", C.c_int32),
-                ("krylov", C.c_int32), ("stream", C.c_void_p)]
+                ("krylov", C.c_int32), ("inner_tol", C.c_double), ("stream", C.c_void_p)]
 
 
 class StepStats(C.Structure):
@@ -129,7 +129,7 @@ class Hierarchy:
 
 def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
                          nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50,
-                         stream=None, krylov: int = 0) -> Hierarchy:
+                         stream=None, krylov: int = 0, inner_tol: float = 0.0) -> Hierarchy:
     """blocks: int32 [nblocks, 4] rows (level, bi, bj, bk) sorted by level.
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None for torch's current stream."""
     import torch
@@ -147,6 +147,7 @@ def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, preci
     d.precision = int(precision)
     d.nu_pre, d.nu_post, d.n_coarse, d.max_outer = int(nu_pre), int(nu_post), int(n_coarse), int(max_outer)
     d.krylov = int(krylov)
+    d.inner_tol = float(inner_tol)
     d.stream = C.c_void_p(raw)
     h = C.c_void_p()
     _check(lib().ohm_create_hierarchy(C.byref(d), C.byref(h)), "ohm_create_hierarchy")
