@@ -47,6 +47,14 @@ def args_parse():
     p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
     p.add_argument("--n-coarse", type=int, default=16, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
+    p.add_argument("--workload", choices=["resistive_bump", "batched512", "serving"], default="resistive_bump",
+                   help="resistive_bump: the headline 256^3 line; batched512: 512 independent instances "
+                        "(edges 16..64) in batched hierarchies; serving: Poisson request stream through "
+                        "the continuous-batching service")
+    p.add_argument("--instances", type=int, default=512, help="batched512: number of instances")
+    p.add_argument("--no-autotune", action="store_true", help="batched512: keep the default schedule")
+    p.add_argument("--requests", type=int, default=600, help="serving: requests in the stream")
+    p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     p.add_argument("--inner-tol", type=float, default=1e-5,
                    help="residual reduction asked of each float32 inner solve (mixed precision)")
     return p.parse_args()
@@ -433,10 +441,374 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batches
+def run_batched(args):
+    """512 independent periodic instances (edges 16..64), one CN step each to 1e-9: one
+    batched hierarchy per edge length (every launch covers all its instances, CUDA-graph
+    inner iterations, autotuned schedule), the five classes stepped concurrently from five
+    host threads on five streams.  A bench step solves every instance once from its initial
+    field."""
+    import concurrent.futures as cf
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_1009_0798_gb300 import ohm
+    from paper_1009_0798_gb300 import workloads as W
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    ge.build()
+    tol = 1e-9
+    inst = W.batched_instances(args.instances, seed=4)
+    nu = tuple(int(v) for v in args.nu.split(","))
+    groups = {}
+    for i in inst:
+        groups.setdefault(i.n, []).append(i)
+    cells = sum(i.n ** 3 for i in inst)
+    C = []
+    for n in sorted(groups):
+        lst = groups[n]
+        s = torch.cuda.Stream()
+        h = lst[0].hier
+        c = {"n": n, "K": len(lst), "s": s, "dts": [i.dt for i in lst], "hier": h}
+        with torch.cuda.stream(s):
+            c["B0"] = torch.from_numpy(np.concatenate([i.B for i in lst]).reshape(-1)).cuda()
+            c["eta"] = torch.from_numpy(np.concatenate([i.eta for i in lst]).reshape(-1)).cuda()
+            c["B"] = torch.empty_like(c["B0"])
+            c["g"] = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_MIXED,
+                                              nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse, max_outer=400,
+                                              stream=s, n_instances=len(lst), use_graphs=True)
+            ohm.ohm_set_eta(c["g"], c["eta"])
+        C.append(c)
+    torch.cuda.synchronize()
+    tuned = {}
+    if not args.no_autotune:
+        for c in C:
+            with torch.cuda.stream(c["s"]):
+                tuned[c["n"]] = ohm.ohm_autotune(c["g"], c["B0"], c["dts"], tol)
+        torch.cuda.synchronize()
+
+    def step(c):
+        with torch.cuda.stream(c["s"]):
+            c["B"].copy_(c["B0"])
+            status, st = ohm.ohm_cn_step_batch(c["g"], c["B"], c["dts"], tol)
+        if status != ohm.OHM_OK:
+            raise RuntimeError(f"class {c['n']}: not converged")
+        return st
+
+    pool = cf.ThreadPoolExecutor(len(C))
+    main_s = torch.cuda.current_stream()
+
+    def one_round(timed=False):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main_s)
+        for c in C:
+            c["s"].wait_event(e0)
+        res = list(pool.map(step, C))
+        for c in C:
+            ev = torch.cuda.Event()
+            ev.record(c["s"])
+            main_s.wait_event(ev)
+        e1.record(main_s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    for _ in range(args.warmup):
+        one_round()
+    n0 = sum(ohm.ohm_launch_count(c["g"]) for c in C)
+    per, cyc = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            ms, res = one_round(True)
+            per.append(ms)
+            cyc.append(sum(x["cycles"] for st in res for x in st) / len(inst))
+    launches = sum(ohm.ohm_launch_count(c["g"]) for c in C) - n0
+    total = sum(per)
+    t_max = barrier_max(ws, total)
+    value = ws * cells * args.steps / (t_max * 1e-3)
+
+    # the smoother of the largest class, timed with events in one more (untimed) round
+    big = max(C, key=lambda c: c["n"])
+    nfine = big["hier"].nblocks * big["K"]
+    ohm.ohm_prof_enable(big["g"], ohm.OHM_K_SMOOTH, min_blocks=nfine, max_launches=4096)
+    step(big)
+    torch.cuda.synchronize()
+    prof = ohm.ohm_prof_read(big["g"])
+    ohm.ohm_prof_enable(big["g"], -1)
+    hbm_peak, peak_src = peaks()
+    sec = prof["ms"] * 1e-3
+    ach = ALGO[("smooth", 4)]["bytes"] * prof["cells"] / max(sec, 1e-12) * 1e-9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)", "kernel": f"smooth ({big['n']}^3 class)",
+            "launches": prof["launches"], "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
+            "algorithmic_bytes_per_launch": ALGO[("smooth", 4)]["bytes"] * prof["cells"] / max(prof["launches"], 1),
+            "traffic": None}
+
+    # comparisons: every instance alone through the single-problem API (FGMRES(6), the
+    # headline path), one after another; and the batched plain-FP64 scheme
+    comp = {}
+    if not args.no_fp64 and rank == 0:
+        t = time.perf_counter()
+        cyc1 = 0
+        for n in sorted(groups):
+            lst = groups[n]
+            h = lst[0].hier
+            g = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_MIXED, max_outer=400,
+                                         krylov=KRYLOV)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            B = torch.empty(h.nblocks * 1536, dtype=torch.float64, device="cuda")
+            eta = torch.empty(h.nblocks * 512, dtype=torch.float64, device="cuda")
+            ms = 0.0
+            for i in lst:
+                B.copy_(torch.from_numpy(i.B.reshape(-1)))
+                eta.copy_(torch.from_numpy(i.eta.reshape(-1)))
+                e0.record()
+                st = ohm.ohm_cn_step(g, B, eta, i.dt, tol)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                cyc1 += st["cycles"]
+            comp.setdefault("unbatched_ms", 0.0)
+            comp["unbatched_ms"] += ms
+            g.close()
+        comp = {"one_at_a_time_fgmres": {"value": cells / (comp["unbatched_ms"] * 1e-3),
+                                         "ms_per_step": comp["unbatched_ms"],
+                                         "mean_cycles": cyc1 / len(inst),
+                                         "note": "each instance alone through ohm_cn_step (eta upload excluded)"}}
+        ms64 = 0.0
+        for n in sorted(groups):
+            c = next(x for x in C if x["n"] == n)
+            h = c["hier"]
+            g = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_FP64,
+                                         max_outer=400, n_instances=c["K"])
+            ohm.ohm_set_eta(g, c["eta"])
+            B = c["B0"].clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ohm.ohm_cn_step_batch(g, B, c["dts"], tol)
+            e1.record()
+            torch.cuda.synchronize()
+            ms64 += e0.elapsed_time(e1)
+            g.close()
+        comp["fp64_plain_batched"] = {"value": cells / (ms64 * 1e-3), "ms_per_step": ms64,
+                                      "note": "classes one after another"}
+
+    # end to end: host fields in, results out, every step
+    e2e = None
+    if not args.no_e2e:
+        hosts = [(torch.from_numpy(np.concatenate([i.B for i in groups[c["n"]]]).reshape(-1)).pin_memory(),
+                  torch.from_numpy(np.concatenate([i.eta for i in groups[c["n"]]]).reshape(-1)).pin_memory()) for c in C]
+        outs = [torch.empty_like(hb).pin_memory() for hb, _ in hosts]
+
+        def step_e2e(k):
+            c, (hb, he), out = C[k], hosts[k], outs[k]
+            with torch.cuda.stream(c["s"]):
+                c["B"].copy_(hb, non_blocking=True)
+                c["eta"].copy_(he, non_blocking=True)
+                ohm.ohm_set_eta(c["g"], c["eta"])
+                ohm.ohm_cn_step_batch(c["g"], c["B"], c["dts"], tol)
+                out.copy_(c["B"], non_blocking=True)
+            c["s"].synchronize()
+
+        step_e2e_all = lambda: list(pool.map(step_e2e, range(len(C))))  # noqa: E731
+        step_e2e_all()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e_all()
+        et = barrier_max(ws, (time.perf_counter() - t) * 1e3)
+        e2e = {"value": ws * cells * args.steps / (et * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": sum(hb.numel() * 8 + he.numel() * 8 for hb, he in hosts),
+               "d2h_bytes_per_step": sum(o.numel() * 8 for o in outs),
+               "timing": "host wall clock around all classes' threads (copies, eta set, step, copy back)"}
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline and rank == 0:
+        try:
+            from oracle import build as obuild
+            from oracle.oracle import Oracle
+            obuild.build()
+            i = next(x for x in inst if x.n == 32)
+            o = Oracle(i.hier, 0.5, i.eta)
+            t = time.perf_counter()
+            o.cn_step(i.B, i.dt, tol, 2, 2, 16, 400)
+            sec_o = time.perf_counter() - t
+            cpu = {"value": i.n ** 3 / sec_o, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                   "kind": "oracle", "sample": f"one 32^3 instance of the batch, one CN step to 1e-9 ({sec_o:.1f} s)"}
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
+    if rank != 0:
+        return
+    lat = sorted(per)
+    p99 = lat[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)]
+    line = {"metric": "cell-steps/s, 512 independent instances to rel. residual 1e-9", "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
+            "config": {"workload": f"batched_{len(inst)}", "cells": cells,
+                       "classes": {str(c["n"]): c["K"] for c in C}, "tol": tol,
+                       "multigrid": "per-instance float64 iterative refinement, float32 defect-correction V-cycles",
+                       "autotuned": {str(k): v for k, v in tuned.items()}, "graphs": True,
+                       "parallelism": f"replicas x{ws}; 5 size classes on 5 streams",
+                       "l2": "working set 3 GB (> 129 MB L2), no flush"},
+            "solves_per_s": ws * len(inst) * args.steps / (t_max * 1e-3),
+            "latency_ms": {"p50": statistics.median(lat), "p99": p99},
+            "mean_cycles_per_instance": cyc, **comp,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- serving
+SERVE_EDGES = (32, 40, 48, 64, 80, 96, 128)  # multiples of 8 in 32..128 whose coarsest grid fits one block
+
+
+def serving_requests(count, rate, seed=5):
+    """Seeded Poisson request stream: arrival times at `rate` per second; 70% uniform periodic
+    boxes with edge from SERVE_EDGES, 30% two-level AMR (base 32^3, blocks meeting the sphere
+    r < 0.2 about the centre refined); each request has its own eta (a pooled smooth 2-decade
+    field times its own factor 10^U(-1,1)), its own B (pooled k^-2 field times U(0.5, 2)),
+    dt = 10^U(1,3) times the explicit limit at its finest level, 1-5 steps."""
+    import numpy as np
+
+    from paper_1009_0798_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    c = np.array([0.5, 0.5, 0.5])
+
+    def sphere(lo, hi):
+        nearest = np.clip(c, lo, hi)
+        return float(np.sum((nearest - c) ** 2)) < 0.2 ** 2
+
+    pool = {}
+
+    def fields(key, n_variant):
+        if (key, n_variant) not in pool:
+            if key == "amr":
+                h = W.refined(32, 32, 32, 1.0 / 32, [sphere])
+                dense_b = W.random_potential_field((64, 64, 64), 1.0 / 64, 900 + n_variant, 1.0)
+                dense_e = W.smooth_lognormal_eta(64, 950 + n_variant)
+                # level 0 from the mean of 2^3 fine cells, level 1 from the fine field
+                def lv0(f):
+                    return f.reshape(f.shape[0], 32, 2, 32, 2, 32, 2).mean(axis=(2, 4, 6))
+                B = np.concatenate([W.dense_to_blocks(h, lv0(dense_b), 0), W.dense_to_blocks(h, dense_b, 1)])
+                E = np.concatenate([W.dense_to_blocks(h, lv0(dense_e), 0), W.dense_to_blocks(h, dense_e, 1)])
+            else:
+                n = key
+                h = W.uniform(n, n, n, 1.0 / n)
+                B = W.dense_to_blocks(h, W.random_potential_field((n, n, n), 1.0 / n, 700 + n + n_variant, 1.0))
+                E = W.dense_to_blocks(h, W.smooth_lognormal_eta(n, 800 + n + n_variant))
+            pool[(key, n_variant)] = (h, B, E)
+        return pool[(key, n_variant)]
+
+    reqs = []
+    for i in range(count):
+        key = "amr" if rng.uniform() < 0.3 else int(rng.choice(SERVE_EDGES))
+        h, B, E = fields(key, int(rng.integers(0, 2)))
+        fe = 10.0 ** rng.uniform(-1.0, 1.0)
+        fb = rng.uniform(0.5, 2.0)
+        dxf = h.dx(h.nlevels - 1)
+        dt = 10.0 ** rng.uniform(1.0, 3.0) * dxf * dxf / (6.0 * float(E.max()) * fe)
+        reqs.append({"t": float(t[i]), "key": key, "hier": h, "B": B, "eta": E, "fb": fb, "fe": fe, "dt": dt,
+                     "steps": int(rng.integers(1, 6))})
+    return reqs
+
+
+def run_serving(args):
+    """Poisson stream of CN-solve requests through the continuous-batching service: requests
+    are submitted at their arrival times (host clock) with host arrays; latency = completion
+    minus submission on the service clock.  Throughput = solved cell-steps over the span from
+    the first submission to the last completion."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_1009_0798_gb300 import server
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    ge.build()
+    torch.cuda.init()
+    reqs = serving_requests(args.requests, args.rate)
+    budget = 60 << 30
+    cfg = dict(hbm_budget_bytes=budget, max_batch=8, n_workers=6, precision=1, tol=1e-9, use_graphs=True,
+               n_coarse=args.n_coarse, max_outer=400)
+    # warm-up service: one request per class (kernels loaded, batches of each class built once)
+    with server.Server(**cfg) as s:
+        seen = {}
+        for r in reqs:
+            seen.setdefault(r["key"], r)
+        ids = [s.submit(r["hier"], r["B"] * r["fb"], r["eta"] * r["fe"], r["dt"], 1) for r in seen.values()]
+        for i in ids:
+            s.wait(i)
+    inputs = [(r["B"] * r["fb"], r["eta"] * r["fe"]) for r in reqs]
+    results = [None] * len(reqs)
+    with server.Server(**cfg) as s, ClockSampler(local) as clk:
+        ids = [None] * len(reqs)
+        ready = threading.Event()
+
+        def collector():
+            ready.wait()
+            for k in range(len(reqs)):
+                while ids[k] is None:
+                    time.sleep(0.0005)
+                results[k] = s.wait(ids[k])
+
+        th = threading.Thread(target=collector)
+        th.start()
+        t0 = time.perf_counter()
+        ready.set()
+        for k, r in enumerate(reqs):
+            delay = r["t"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = s.submit(r["hier"], inputs[k][0], inputs[k][1], r["dt"], r["steps"])
+        th.join()
+        stats = s.stats()
+    lat = sorted((res[1]["t_done"] - res[1]["t_submit"]) * 1e3 for res in results)
+    span = max(res[1]["t_done"] for res in results) - min(res[1]["t_submit"] for res in results)
+    cell_steps = sum(r["hier"].leaf_cells() * r["steps"] for r in reqs)
+    ok = sum(1 for res in results if res[1]["status"] == 0)
+    # alone versus in the mix: a few requests again, each alone on a fresh service
+    same = []
+    for k in range(0, len(reqs), max(1, len(reqs) // 4))[:4]:
+        r = reqs[k]
+        with server.Server(**cfg) as s1:
+            out, res = s1.wait(s1.submit(r["hier"], inputs[k][0], inputs[k][1], r["dt"], r["steps"]))
+        same.append(bool(np.array_equal(out, results[k][0])))
+    p = lambda q: lat[min(len(lat) - 1, max(0, math.ceil(q * len(lat)) - 1))]  # noqa: E731
+    value = cell_steps / span
+    line = {"metric": "served cell-steps/s, Poisson request stream to rel. residual 1e-9", "value": value,
+            "unit": UNIT, "n_gpus": ws, "steps": len(reqs), "warmup": len(seen), "ms_per_step": span * 1e3 / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
+            "config": {"workload": f"serving_poisson_{args.rate:g}_per_s", "requests": len(reqs),
+                       "mix": "70% uniform 32^3-128^3 (edges " + ",".join(map(str, SERVE_EDGES)) + "), 30% 2-level AMR",
+                       "hbm_budget_gb": budget / 2 ** 30, "max_batch": cfg["max_batch"], "n_workers": cfg["n_workers"],
+                       "graphs": True, "tol": 1e-9, "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
+            "solves_per_s": len(reqs) / span, "offered_rate_per_s": args.rate,
+            "span_s": span, "converged": ok, "alone_vs_mix_identical": same,
+            "service": stats,
+            "e2e": {"value": value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(np.mean([a.nbytes + b.nbytes for a, b in inputs])),
+                    "d2h_bytes_per_step": int(np.mean([a.nbytes for a, _ in inputs])),
+                    "timing": "host clock, submit to result in host memory"},
+            "clocks": clk.summary(), "gpu_launches": None, "roofline": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = args_parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched512":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -66,6 +66,17 @@ typedef struct {
                                    max(inner_tol, 0.3 tol / current ||R||/||S||); 0 selects
                                    1e-5.  Values below ~1e-6 ask more than float32 can give: the
                                    inner solve then stops when it stagnates.                   */
+    int32_t n_instances;        /* 0: one problem, stepped by ohm_cn_step.  K >= 1: a batch of K
+                                   independent problems with the block structure above (each
+                                   its own eta, dt and convergence), stepped together by
+                                   ohm_cn_step_batch; every kernel launch covers all K.  Field
+                                   arrays then hold, level by level, the K instances' blocks
+                                   of that level one instance after another (for one-level
+                                   hierarchies: instance after instance).  Batches need
+                                   krylov = 0.                                                  */
+    int32_t use_graphs;         /* batches only: 1 = the inner iteration (V-cycle, update and
+                                   residual) is captured once into a CUDA graph and replayed.
+                                   Needs a non-NULL stream; ignored otherwise.                  */
     void *stream;               /* cudaStream_t used for all work, NULL = legacy default      */
 } ohm_hier_desc;
 
@@ -102,6 +113,42 @@ int ohm_cn_step(ohm_hier *h, double *B_dev, const double *eta_dev, double dt, do
  * ||R||_2/||S||_2 over leaf cells (volume weighted), *max_abs the largest |R| component.
  * B_dev is read only (its covered cells are not used).  OHM_ERR_INVALID before any step. */
 int ohm_residual_norm(ohm_hier *h, const double *B_dev, double *rel_l2, double *max_abs);
+
+/* Batched step (n_instances = K >= 1; not in the paper, which solves one hierarchy): the step
+ * of ohm_cn_step for every instance q with active[q] != 0 (active NULL = all), instance q
+ * with its own dt[q] (host array of K) on the same tol.  Each instance is iterated and
+ * stopped on its own residual norms (volume weighted over its own leaf cells), and its
+ * result does not depend on which other instances are in the batch or active: the work of
+ * every launch is per block and every reduction is per instance in a fixed order, so an
+ * instance gives the same bits alone (K = 1) as in any batch.  Inactive instances are left
+ * untouched.  stats (host array of K, may be NULL) receives each instance's statistics
+ * (inactive ones zeroed).  Returns OHM_OK when every active instance converged (or tol < 0),
+ * OHM_ERR_NOT_CONVERGED / OHM_ERR_NONFINITE when one did not, OHM_ERR_INVALID for a bad
+ * argument, a hierarchy that is not a batch or no eta set. */
+int ohm_cn_step_batch(ohm_hier *h, double *B_dev, const double *dt, double tol, const uint8_t *active,
+                      ohm_step_stats *stats);
+
+/* Device bytes that ohm_create_hierarchy would allocate for d (tables and scratch; the
+ * caller's B and eta not included), without allocating.  OHM_ERR_INVALID as for create. */
+int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes);
+
+/* ---------------------------------------------------------------------------------------
+ * Autotuner (not in the paper): picks the multigrid schedule of a hierarchy by timing real
+ * steps.  Candidates: (nu_pre, nu_post) in {(1,1), (2,1), (2,2), (3,3), (4,4)} (the paper's
+ * Table 1 uses 2/2 on the base grid and 4/4 on AMR levels) x n_coarse in {4, 16} x smoother
+ * in {fused red+black sweep, two colour passes} (the fused sweep stages a 12^3 tile, the
+ * two-pass smoother a 10^3 tile).  Each candidate runs one step of ohm_cn_step (batches:
+ * ohm_cn_step_batch with dt) from B_dev on a private copy (B_dev is not modified), timed
+ * with CUDA events; candidates that do not converge are discarded.  The fastest is kept in
+ * the hierarchy and reported.  Allocates one copy of B for the duration of the call.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t nu_pre, nu_post, n_coarse;
+    int32_t smoother;           /* 0 = fused red+black sweep, 1 = two colour passes            */
+    double ms;                  /* time of the chosen candidate's step                         */
+    int32_t candidates;         /* candidates timed                                            */
+} ohm_tune_result;
+int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol, ohm_tune_result *res);
 
 void ohm_destroy(ohm_hier *h);
 const char *ohm_status_string(int status);

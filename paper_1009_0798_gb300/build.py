@@ -1,6 +1,6 @@
 """Compile libohm.so (CUDA kernels + host orchestration) for sm_103a, in-tree.
 
-The two translation units are compiled in parallel with nvcc and linked against the shared
+The translation units are compiled in parallel with nvcc and linked against the shared
 CUDA runtime; the result lands in paper_1009_0798_gb300/_build/libohm.so.
 """
 from __future__ import annotations
@@ -15,8 +15,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libohm.so")
-SOURCES = ["ohm_kernels.cu", "ohm_host.cpp", "ohm_static.cu"]
-HEADERS = ["ohm_internal.h", os.path.join("..", "..", "include", "ohm.h")]
+SOURCES = ["ohm_kernels.cu", "ohm_host.cpp", "ohm_static.cu", "ohm_server.cpp"]
+HEADERS = ["ohm_internal.h", os.path.join("..", "..", "include", "ohm.h"),
+           os.path.join("..", "..", "include", "ohm_server.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

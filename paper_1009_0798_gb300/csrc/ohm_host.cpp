@@ -49,6 +49,7 @@ struct HGrid {
     std::vector<int> nbr, parent, child, origin, freg, rsrc, gslot, slot_block;
     std::vector<uint8_t> covered, octant;
     int slot0 = 0, nslot = 0;
+    int inst_nblk = 0;          // batches: blocks per instance
     GridDev dev;
     int find(int i, int j, int k) const {
         auto it = index.find(key3(wrapi(i, nb[0]), wrapi(j, nb[1]), wrapi(k, nb[2])));
@@ -97,6 +98,24 @@ struct ohm_hier {
     double inv_dt = NAN;
     bool has_S = false;
     double last_dt = 0;
+
+    // batches (n_instances >= 1): K instances of one block structure, stacked level by level
+    bool batched = false;
+    int K = 1;
+    int64_t nblk_inst = 0;        // blocks of one instance
+    double *eta_user = nullptr;   // eta as set (the operator uses eta * dt per instance)
+    double *bscale = nullptr;     // per-block eta scale (the instance's dt)
+    double *dnormK = nullptr;     // [K][4] per-instance norm sums
+    double *hnormK = nullptr;     // pinned copy
+    uint8_t *imask_d = nullptr, *imask_h = nullptr;  // per-instance update mask (device, pinned)
+    std::vector<double> cur_scale;
+    bool eta_dirty = false;
+    InstRanges ranges;
+    int smoother = 0;             // 0: fused red+black sweep where possible, 1: two colour passes
+    // CUDA graph of the batched inner iteration
+    cudaGraphExec_t graph = nullptr;
+    bool graph_warm = false, graph_failed = false;
+    int64_t graph_launches = 0;
 
     // instrumentation: kernel launches issued, and CUDA-event timing of one kernel kind
     int64_t nlaunch = 0;
@@ -320,6 +339,77 @@ int build_tables(ohm_hier *H, std::string &err) {
     return OHM_OK;
 }
 
+// Batches: the tables of one instance (built above) repeated K times.  Every grid keeps its
+// blocks instance after instance; block, slot, register and reflux-source indices of copy k
+// are shifted by k times the per-instance count of the grid they point into.
+void replicate(ohm_hier *H) {
+    const int K = H->K;
+    auto rep = [K](std::vector<int> &v, int per_block, int nb, int shift) {
+        std::vector<int> o;
+        o.reserve(v.size() * K);
+        for (int k = 0; k < K; k++)
+            for (size_t i = 0; i < (size_t)nb * per_block; i++) o.push_back(v[i] >= 0 ? v[i] + k * shift : -1);
+        v.swap(o);
+    };
+    auto rep8 = [K](std::vector<uint8_t> &v) {
+        std::vector<uint8_t> o;
+        for (int k = 0; k < K; k++) o.insert(o.end(), v.begin(), v.end());
+        v.swap(o);
+    };
+    const int nreg = H->nreg, nrsrc = H->nrsrc;
+    std::vector<int> nb_amr, nb_mg, slot0_old, nslot_old;
+    for (auto &g : H->amr) nb_amr.push_back(g.n());
+    for (auto &g : H->mg) nb_mg.push_back(g.n());
+    int slot_base = 0;
+    for (size_t l = 0; l < H->amr.size(); l++) {
+        HGrid &g = H->amr[l];
+        const int nb = nb_amr[l];
+        const int nb_child = l + 1 < H->amr.size() ? nb_amr[l + 1] : 0;
+        const int nb_par = l > 0 ? nb_amr[l - 1] : (nb_mg.empty() ? 0 : nb_mg[0]);
+        // ghost slots: copy k of local slot s is slot_base + k * nslot + s
+        std::vector<int> gs;
+        for (int k = 0; k < K; k++)
+            for (int b = 0; b < nb; b++) gs.push_back(g.gslot[b] >= 0 ? slot_base + k * g.nslot + (g.gslot[b] - g.slot0) : -1);
+        g.gslot.swap(gs);
+        rep(g.slot_block, 1, g.nslot, nb);
+        g.slot0 = slot_base;
+        g.nslot *= K;
+        slot_base += g.nslot;
+        rep(g.nbr, 27, nb, nb);
+        rep(g.child, 8, nb, nb_child);
+        rep(g.parent, 1, nb, nb_par);
+        rep(g.freg, 6, nb, nreg);
+        rep(g.rsrc, 6, nb, nrsrc);
+        rep(g.origin, 3, nb, 0);
+        rep(g.bijk, 3, nb, 0);
+        rep8(g.covered);
+        rep8(g.octant);
+        g.off *= K;
+        g.inst_nblk = nb;
+    }
+    for (size_t m = 0; m < H->mg.size(); m++) {
+        HGrid &g = H->mg[m];
+        const int nb = nb_mg[m];
+        const int nb_par = m + 1 < H->mg.size() ? nb_mg[m + 1] : 0;
+        rep(g.nbr, 27, nb, nb);
+        rep(g.parent, 1, nb, nb_par);
+        rep(g.origin, 3, nb, 0);
+        rep(g.bijk, 3, nb, 0);
+        rep8(g.octant);
+        g.inst_nblk = nb;
+    }
+    rep(H->rsrc_tab, 1, nrsrc * 4, nreg);
+    H->nslot = slot_base;
+    H->nreg = nreg * K;
+    H->nrsrc = nrsrc * K;
+    H->nblocks *= K;
+    H->ranges.nlev = (int)H->amr.size();
+    for (size_t l = 0; l < H->amr.size(); l++) {
+        H->ranges.off[l] = H->amr[l].off;
+        H->ranges.n[l] = nb_amr[l];
+    }
+}
+
 template <typename V>
 void push_table(std::vector<char> &blob, std::vector<size_t> &offs, const std::vector<V> &v) {
     size_t o = align256(blob.size());
@@ -328,7 +418,7 @@ void push_table(std::vector<char> &blob, std::vector<size_t> &offs, const std::v
     offs.push_back(o);
 }
 
-int allocate(ohm_hier *H, std::string &err) {
+int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
     const size_t tsz = H->mixed ? sizeof(float) : sizeof(double);
     const size_t n = (size_t)H->nblocks;
     // tables
@@ -391,8 +481,14 @@ int allocate(ohm_hier *H, std::string &err) {
         want(&H->mgbuf[m].inv, nb * 3 * B3 * tsz);
         want(&H->mgbuf[m].eta, nb * B3 * tsz);
     }
+    if (H->batched) {
+        want((void **)&H->eta_user, n * B3 * 8);
+        want((void **)&H->bscale, n * 8);
+        want((void **)&H->dnormK, (size_t)H->K * 4 * 8);
+        want((void **)&H->imask_d, (size_t)H->K * 2);  // outer and inner masks
+    }
     for (size_t q = 0; q < H->small.size(); q++) {
-        size_t nc = (size_t)H->small[q][0] * H->small[q][1] * H->small[q][2];
+        size_t nc = (size_t)H->K * H->small[q][0] * H->small[q][1] * H->small[q][2];
         want(&H->smallbuf[q].r, nc * 3 * tsz);
         want(&H->smallbuf[q].e, nc * 3 * tsz);
         want(&H->smallbuf[q].e2, nc * 3 * tsz);
@@ -403,6 +499,10 @@ int allocate(ohm_hier *H, std::string &err) {
     for (auto &p : plan) {
         doff.push_back(total);
         total += align256(p.second);
+    }
+    if (dry_bytes) {
+        *dry_bytes = (int64_t)total;
+        return OHM_OK;
     }
     if (cudaMalloc(&H->pool, total) != cudaSuccess) {
         cudaGetLastError();
@@ -426,6 +526,13 @@ int allocate(ohm_hier *H, std::string &err) {
         return OHM_ERR_OOM;
     }
     H->hdots = H->hnorm + 8;
+    if (H->batched) {
+        if (cudaMallocHost((void **)&H->hnormK, (size_t)H->K * 4 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost((void **)&H->imask_h, (size_t)H->K * 2) != cudaSuccess) {
+            err = "pinned allocation failed";
+            return OHM_ERR_OOM;
+        }
+    }
     if (H->wblk) {  // inner-product weights: h^3 on leaf blocks, 0 on covered ones
         std::vector<double> w((size_t)H->nblocks, 0.0);
         for (auto &g : H->amr)
@@ -456,6 +563,7 @@ int allocate(ohm_hier *H, std::string &err) {
         dv.slot_block = (const int *)ptr(offs[k + 9], !g->slot_block.empty());
         dv.nslot = g->nslot;
         dv.slot0 = g->slot0;
+        dv.inst_nblk = g->inst_nblk;
         k += 10;
     }
     H->d_rsrc = (int *)(H->rsrc_tab.empty() ? nullptr : base + offs[k]);
@@ -501,6 +609,7 @@ template <typename T>
 SmallDev<T> small_dev(ohm_hier *H) {
     SmallDev<T> sm;
     sm.n = (int)H->small.size();
+    sm.ninst = H->K;
     double h = H->d.dx0 * std::pow(2.0, (double)(H->mg.size() + 1));
     for (int q = 0; q < sm.n; q++) {
         for (int a = 0; a < 3; a++) sm.dims[q][a] = H->small[q][a];
@@ -585,7 +694,7 @@ GridRef base_ref(ohm_hier *H, int m) {  // m = 0: AMR level 0
 
 template <typename T>
 int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
-    if (std::is_same<T, float>::value && G.g->nslot == 0) {
+    if (std::is_same<T, float>::value && G.g->nslot == 0 && H->smoother == 0) {
         // float32 grids with every neighbour: one fused red+black launch per sweep
         for (int i = 0; i < n; i++) {
             const T *src = (const T *)((i & 1) ? G.e2 : G.e);
@@ -688,7 +797,12 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
                                          dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
                                          norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s)));
     }
-    if (norms) LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->redscr, H->dnorm, H->s));
+    if (norms) {
+        if (H->batched)
+            LAUNCH(H, OHM_K_NORM, 0, launch_norm_inst(H->partials, H->ranges, H->K, H->dnormK, H->s));
+        else
+            LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->redscr, H->dnorm, H->s));
+    }
     return OHM_OK;
 }
 
@@ -731,9 +845,9 @@ int read_norms(ohm_hier *H, double out[4], int *err_flag) {
 }
 
 template <typename T>
-int update_all(ohm_hier *H, double *B, const T *e) {
+int update_all(ohm_hier *H, double *B, const T *e, const uint8_t *imask = nullptr) {
     for (auto &g : H->amr)
-        LAUNCH(H, OHM_K_UPDATE, g.n(), launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>((void *)e, g, 3), H->s));
+        LAUNCH(H, OHM_K_UPDATE, g.n(), launch_update<T>(g.dev, amr_ptr<double>(B, g, 3), amr_ptr<T>((void *)e, g, 3), imask, H->s));
     return OHM_OK;
 }
 
@@ -960,7 +1074,7 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
         while (cycles < H->d.max_outer) {
             if ((st = vcycle<T>(H, lamdt))) return st;
             for (auto &g : H->amr)
-                LAUNCH(H, OHM_K_UPDATE, g.n(), launch_axpy_leaf<T>(g.dev, amr_ptr<T>(eacc, g, 3), amr_ptr<T>(e, g, 3), H->s));
+                LAUNCH(H, OHM_K_UPDATE, g.n(), launch_axpy_leaf<T>(g.dev, amr_ptr<T>(eacc, g, 3), amr_ptr<T>(e, g, 3), nullptr, H->s));
             cycles++;
             if ((st = sync_down_t<T>(H, eacc))) return st;
             if ((st = fill_ghosts_t<T>(H, eacc, (T *)H->ghostE))) return st;
@@ -988,6 +1102,197 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
     return result;
 }
 
+// ---------------------------------------------------------------- batches of instances
+// Per-instance norms, enqueued by composite_t into dnormK, copied to the host with the error
+// word; the caller synchronises (read_norms_batch) or the copies end a captured graph.
+int enqueue_norm_copy(ohm_hier *H) {
+    CK(cudaMemcpyAsync(H->hnormK, H->dnormK, (size_t)H->K * 4 * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    CK(cudaMemcpyAsync(H->hnorm + 4, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+    return OHM_OK;
+}
+
+int read_norms_batch(ohm_hier *H, std::vector<double> &rel, std::vector<double> &mx, int *err_flag) {
+    CK(cudaStreamSynchronize(H->s));
+    rel.resize(H->K);
+    mx.resize(H->K);
+    for (int q = 0; q < H->K; q++) {
+        const double sr = H->hnormK[4 * q], ss = H->hnormK[4 * q + 1];
+        rel[q] = ss > 0 ? std::sqrt(sr / ss) : std::sqrt(sr);
+        mx[q] = H->hnormK[4 * q + 2];
+    }
+    int e;
+    memcpy(&e, &H->hnorm[4], sizeof(int));
+    *err_flag = e;
+    return OHM_OK;
+}
+
+// Runs `enqueue` (stream work only, no synchronisation) eagerly, or, with use_graphs on a
+// non-default stream, replays a CUDA graph captured from it on its second use.
+template <class F>
+int run_iteration(ohm_hier *H, F enqueue) {
+    const bool want = H->d.use_graphs && H->s != nullptr && !H->graph_failed && H->prof_kind < 0;
+    if (!want) return enqueue();
+    if (!H->graph) {
+        if (!H->graph_warm) {  // first use eager: lazy per-kernel attributes are set outside capture
+            H->graph_warm = true;
+            return enqueue();
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(H->s, cudaStreamCaptureModeThreadLocal));
+        const int64_t n0 = H->nlaunch;
+        const int st = enqueue();
+        const cudaError_t ec = cudaStreamEndCapture(H->s, &g);
+        cudaError_t ei = cudaErrorUnknown;
+        if (st == OHM_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&H->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st != OHM_OK || ec != cudaSuccess || ei != cudaSuccess) {
+            cudaGetLastError();
+            H->graph = nullptr;
+            H->graph_failed = true;
+            H->nlaunch = n0;
+            return enqueue();  // nothing was executed by the capture: run eagerly
+        }
+        H->graph_launches = H->nlaunch - n0;
+        H->nlaunch = n0;
+    }
+    H->nlaunch += H->graph_launches;
+    CK(cudaGraphLaunch(H->graph, H->s));
+    return OHM_OK;
+}
+
+// eta * dt[q] on every block of instance q, then the derived eta arrays
+template <typename T>
+int batch_scale(ohm_hier *H, const double *dt) {
+    bool same = !H->eta_dirty && (int)H->cur_scale.size() == H->K;
+    for (int q = 0; same && q < H->K; q++) same = H->cur_scale[q] == dt[q];
+    if (same) return OHM_OK;
+    std::vector<double> bs((size_t)H->nblocks);
+    for (int l = 0; l < H->ranges.nlev; l++)
+        for (int q = 0; q < H->K; q++)
+            for (int b = 0; b < H->ranges.n[l]; b++) bs[(size_t)H->ranges.off[l] + (size_t)q * H->ranges.n[l] + b] = dt[q];
+    CK(cudaMemcpyAsync(H->bscale, bs.data(), bs.size() * sizeof(double), cudaMemcpyHostToDevice, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    CK(launch_scale_blocks(H->eta_user, H->eta64, H->bscale, (int)H->nblocks, H->s));
+    int st;
+    if ((st = eta_derive<T>(H))) return st;
+    H->cur_scale.assign(dt, dt + H->K);
+    H->eta_dirty = false;
+    return OHM_OK;
+}
+
+// Batched theta step (dt folded into eta per instance, so the operator's lambda dt is lambda):
+// the outer float64 loop of Eqs. 16-18 per instance, with a float32 defect-correction inner
+// solve (mixed) or one float64 V-cycle per outer iteration (FP64).  Instances are stopped and
+// masked out one by one; every launch covers the whole batch.
+template <typename T>
+int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const uint8_t *active,
+                    ohm_step_stats *stats) {
+    const int K = H->K;
+    const double lam = H->d.lambda, lamdt = lam;
+    int st;
+    if ((st = batch_scale<T>(H, dt))) return st;
+    if ((st = prepare_dt<T>(H, 1.0))) return st;
+    CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->s));
+    if ((st = sync_down(H, B))) return st;
+    if ((st = fill_ghosts_B(H, B))) return st;
+    if ((st = composite<double>(H, B, nullptr, 1.0, -(1.0 - lam), 0.0, H->S, false))) return st;
+    H->has_S = true;
+    H->last_dt = 1.0;
+    enum { RUN = 0, DONE = 1, NOCONV = 2, NONFIN = 3, IDLE = 4 };
+    std::vector<int> state(K), cycles(K, 0);
+    std::vector<double> first(K, 0.0), rel, mx, ni, nmx, target(K), prev(K);
+    for (int q = 0; q < K; q++) state[q] = (active && !active[q]) ? IDLE : RUN;
+    uint8_t *omask_h = H->imask_h, *imask_h = H->imask_h + K;
+    uint8_t *omask_d = H->imask_d, *imask_d = H->imask_d + K;
+    T *r = (T *)H->amrbuf.r, *e = (T *)H->amrbuf.e;
+    T *rout = (T *)H->rout, *eacc = (T *)H->eacc;
+    const size_t nbytes = (size_t)H->nblocks * 3 * B3 * sizeof(T);
+    const double fl = inner_floor(H);
+    for (int outer = 0;; outer++) {
+        if ((st = composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, H->mixed ? rout : (T *)nullptr))) return st;
+        if ((st = enqueue_norm_copy(H))) return st;
+        int ef = 0;
+        if ((st = read_norms_batch(H, rel, mx, &ef))) return st;
+        if (ef) return OHM_ERR_INVALID;
+        bool any = false;
+        for (int q = 0; q < K; q++) {
+            omask_h[q] = 0;
+            if (state[q] != RUN) continue;
+            if (outer == 0) first[q] = rel[q];
+            if (!std::isfinite(rel[q]) || !std::isfinite(mx[q])) state[q] = NONFIN;
+            else if (tol >= 0 && rel[q] <= tol) state[q] = DONE;
+            else if (cycles[q] >= H->d.max_outer) state[q] = tol >= 0 ? NOCONV : DONE;
+            else {
+                omask_h[q] = 1;
+                any = true;
+            }
+        }
+        if (!any) break;
+        CK(cudaMemcpyAsync(omask_d, omask_h, K, cudaMemcpyHostToDevice, H->s));
+        if (!H->mixed) {
+            // one float64 V-cycle for every running instance
+            if ((st = vcycle<T>(H, lamdt))) return st;
+            if ((st = update_all<T>(H, B, e, omask_d))) return st;
+            for (int q = 0; q < K; q++) cycles[q] += omask_h[q];
+        } else {
+            CK(cudaMemsetAsync(eacc, 0, nbytes, H->s));
+            for (int q = 0; q < K; q++) {
+                imask_h[q] = omask_h[q];
+                target[q] = tol >= 0 ? std::max(fl, 0.3 * tol / std::max(rel[q], 1e-300)) : fl;
+                prev[q] = 1.0;
+            }
+            bool inner = true;
+            while (inner) {
+                CK(cudaMemcpyAsync(imask_d, imask_h, K, cudaMemcpyHostToDevice, H->s));
+                st = run_iteration(H, [&]() -> int {
+                    int s2;
+                    if ((s2 = vcycle<T>(H, lamdt))) return s2;
+                    for (auto &g : H->amr)
+                        LAUNCH(H, OHM_K_UPDATE, g.n(), launch_axpy_leaf<T>(g.dev, amr_ptr<T>(eacc, g, 3), amr_ptr<T>(e, g, 3), imask_d, H->s));
+                    if ((s2 = sync_down_t<T>(H, eacc))) return s2;
+                    if ((s2 = fill_ghosts_t<T>(H, eacc, (T *)H->ghostE))) return s2;
+                    if ((s2 = composite_t<T, T>(H, eacc, rout, (const T *)H->amrbuf.eta, (const T *)H->ghostE,
+                                                (const T *)H->ghostEtaT, -1.0, -lamdt, 1.0, r, (T *)nullptr, true)))
+                        return s2;
+                    return enqueue_norm_copy(H);
+                });
+                if (st) return st;
+                if ((st = read_norms_batch(H, ni, nmx, &ef))) return st;
+                inner = false;
+                for (int q = 0; q < K; q++) {
+                    if (!imask_h[q]) continue;
+                    cycles[q]++;
+                    // stop at the target, on float32 stagnation (< 10% gained) or at the budget
+                    if (!std::isfinite(ni[q]) || ni[q] <= target[q] || ni[q] > 0.9 * prev[q] || cycles[q] >= H->d.max_outer)
+                        imask_h[q] = 0;
+                    else {
+                        prev[q] = ni[q];
+                        inner = true;
+                    }
+                }
+            }
+            if ((st = update_all<T>(H, B, eacc, omask_d))) return st;
+        }
+        if ((st = sync_down(H, B))) return st;
+        if ((st = fill_ghosts_B(H, B))) return st;
+    }
+    int result = OHM_OK;
+    for (int q = 0; q < K; q++) {
+        if (state[q] == NONFIN) result = OHM_ERR_NONFINITE;
+        else if (state[q] == NOCONV && result == OHM_OK) result = OHM_ERR_NOT_CONVERGED;
+        if (!stats) continue;
+        ohm_step_stats &o = stats[q];
+        memset(&o, 0, sizeof(o));
+        if (state[q] == IDLE) continue;
+        o.cycles = cycles[q];
+        o.converged = (state[q] == DONE && tol >= 0) ? 1 : 0;
+        o.rel_l2_initial = first[q];
+        o.rel_l2 = rel[q];
+        o.max_abs = mx[q];
+    }
+    return result;
+}
+
 bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     if (!d) { err = "NULL descriptor"; return false; }
     for (int a = 0; a < 3; a++)
@@ -1003,6 +1308,9 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
         return false;
     }
     if (!(d->inner_tol >= 0 && d->inner_tol < 1)) { err = "inner_tol must be in [0, 1)"; return false; }
+    if (d->n_instances < 0 || d->n_instances > (1 << 16)) { err = "n_instances out of range"; return false; }
+    if (d->n_instances > 0 && d->krylov != 0) { err = "batches need krylov = 0"; return false; }
+    if ((int64_t)std::max(1, d->n_instances) * d->nblocks >= (int64_t)1 << 31) { err = "too many blocks"; return false; }
     for (int a = 0; a < 3; a++)
         if (((int64_t)d->base_cells[a] << (d->nlevels - 1)) >= (1 << 20)) { err = "level too fine"; return false; }
     return true;
@@ -1023,6 +1331,7 @@ const char *ohm_status_string(int status) {
         case OHM_ERR_NONFINITE: return "residual became non-finite";
         case OHM_ERR_OOM: return "device allocation failed";
         case OHM_ERR_CUDA: return "CUDA error";
+        case -6: return "timed out (ohm_server_wait)";
         default: return "unknown status";
     }
 }
@@ -1043,7 +1352,11 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
     H->nlev = d->nlevels;
     H->nblocks = d->nblocks;
     H->lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);
+    H->batched = d->n_instances >= 1;
+    H->K = std::max(1, d->n_instances);
+    H->nblk_inst = d->nblocks;
     int st = build_tables(H, err);
+    if (st == OHM_OK && H->batched) replicate(H);
     if (st == OHM_OK) st = allocate(H, err);
     if (st != OHM_OK) {
         g_last_error = err;
@@ -1054,16 +1367,48 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
     return OHM_OK;
 }
 
+int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes) {
+    std::string err;
+    if (!bytes || !valid_desc(d, err)) {
+        g_last_error = bytes ? err : "NULL output";
+        return OHM_ERR_INVALID;
+    }
+    ohm_hier H;
+    H.d = *d;
+    H.d.block_lijk = nullptr;
+    H.mixed = d->precision == OHM_MIXED;
+    H.nlev = d->nlevels;
+    H.nblocks = d->nblocks;
+    H.lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);
+    H.batched = d->n_instances >= 1;
+    H.K = std::max(1, d->n_instances);
+    H.nblk_inst = d->nblocks;
+    int st = build_tables(&H, err);
+    if (st == OHM_OK && H.batched) replicate(&H);
+    if (st == OHM_OK) st = allocate(&H, err, bytes);
+    if (st != OHM_OK) g_last_error = err;
+    return st;
+}
+
 void ohm_destroy(ohm_hier *h) {
     if (!h) return;
     for (auto ev : h->prof_ev) cudaEventDestroy(ev);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->pool) cudaFree(h->pool);
     if (h->hnorm) cudaFreeHost(h->hnorm);
+    if (h->hnormK) cudaFreeHost(h->hnormK);
+    if (h->imask_h) cudaFreeHost(h->imask_h);
     delete h;
 }
 
 int ohm_set_eta(ohm_hier *h, const double *eta_dev) {
     if (!h || !eta_dev) return OHM_ERR_INVALID;
+    if (h->batched) {  // scaled by each instance's dt at the next step
+        CK(cudaMemcpyAsync(h->eta_user, eta_dev, (size_t)h->nblocks * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+        h->eta_dirty = true;
+        h->eta_set = true;
+        return OHM_OK;
+    }
     CK(cudaMemcpyAsync(h->eta64, eta_dev, (size_t)h->nblocks * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     int st = h->mixed ? eta_derive<float>(h) : eta_derive<double>(h);
     if (st) return st;
@@ -1071,8 +1416,97 @@ int ohm_set_eta(ohm_hier *h, const double *eta_dev) {
     return OHM_OK;
 }
 
+int ohm_cn_step_batch(ohm_hier *h, double *B_dev, const double *dt, double tol, const uint8_t *active,
+                      ohm_step_stats *stats) {
+    if (!h || !h->batched || !B_dev || !dt || !h->eta_set) return OHM_ERR_INVALID;
+    for (int q = 0; q < h->K; q++)
+        if ((!active || active[q]) && !(dt[q] > 0 && std::isfinite(dt[q]))) return OHM_ERR_INVALID;
+    // inactive instances keep the scale they had (any positive value)
+    std::vector<double> dts(dt, dt + h->K);
+    for (int q = 0; q < h->K; q++)
+        if (!(dts[q] > 0 && std::isfinite(dts[q]))) dts[q] = (int)h->cur_scale.size() == h->K ? h->cur_scale[q] : 1.0;
+    return h->mixed ? cn_step_batch_t<float>(h, B_dev, dts.data(), tol, active, stats)
+                    : cn_step_batch_t<double>(h, B_dev, dts.data(), tol, active, stats);
+}
+
+static void reset_graph(ohm_hier *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_warm = false;
+}
+
+int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol, ohm_tune_result *res) {
+    if (!h || !B_dev || !dt || !h->eta_set) return OHM_ERR_INVALID;
+    const size_t bytes = (size_t)h->nblocks * 3 * B3 * sizeof(double);
+    double *Bw = nullptr;
+    if (cudaMalloc(&Bw, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return OHM_ERR_OOM;
+    }
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    const ohm_hier_desc saved = h->d;
+    const int saved_sm = h->smoother;
+    auto step = [&]() -> int {
+        if (cudaMemcpyAsync(Bw, B_dev, bytes, cudaMemcpyDeviceToDevice, h->s) != cudaSuccess) return OHM_ERR_CUDA;
+        if (h->batched) return ohm_cn_step_batch(h, Bw, dt, tol, nullptr, nullptr);
+        return h->mixed ? cn_step_mixed(h, Bw, dt[0], tol, nullptr) : cn_step_impl<double>(h, Bw, dt[0], tol, nullptr);
+    };
+    int st = step();  // warm-up: first-use setup outside the timings
+    const int nus[5][2] = {{1, 1}, {2, 1}, {2, 2}, {3, 3}, {4, 4}};
+    const int ncs[2] = {4, 16};
+    double best = INFINITY;
+    ohm_tune_result br{};
+    int ncand = 0;
+    for (int a = 0; a < 5 && (st == OHM_OK || st == OHM_ERR_NOT_CONVERGED); a++)
+        for (int c = 0; c < 2; c++)
+            for (int sm = 0; sm < (h->mixed ? 2 : 1); sm++) {
+                h->d.nu_pre = nus[a][0];
+                h->d.nu_post = nus[a][1];
+                h->d.n_coarse = ncs[c];
+                h->smoother = h->mixed ? sm : 1;
+                reset_graph(h);
+                cudaEventRecord(ev[0], h->s);
+                const int r = step();
+                cudaEventRecord(ev[1], h->s);
+                if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+                    st = OHM_ERR_CUDA;
+                    break;
+                }
+                ncand++;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                if (r == OHM_OK && ms < best) {
+                    best = ms;
+                    br = ohm_tune_result{h->d.nu_pre, h->d.nu_post, h->d.n_coarse, h->smoother, ms, 0};
+                }
+            }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaFree(Bw);
+    reset_graph(h);
+    if (st != OHM_OK && st != OHM_ERR_NOT_CONVERGED) {
+        h->d = saved;
+        h->smoother = saved_sm;
+        return st;
+    }
+    if (!(best < INFINITY)) {  // nothing converged: keep the schedule the hierarchy had
+        h->d = saved;
+        h->smoother = saved_sm;
+        return OHM_ERR_NOT_CONVERGED;
+    }
+    h->d.nu_pre = br.nu_pre;
+    h->d.nu_post = br.nu_post;
+    h->d.n_coarse = br.n_coarse;
+    h->smoother = br.smoother;
+    br.candidates = ncand;
+    if (res) *res = br;
+    return OHM_OK;
+}
+
 int ohm_cn_step(ohm_hier *h, double *B_dev, const double *eta_dev, double dt, double tol, ohm_step_stats *stats) {
-    if (!h || !B_dev || !(dt > 0) || !std::isfinite(dt)) return OHM_ERR_INVALID;
+    if (!h || h->batched || !B_dev || !(dt > 0) || !std::isfinite(dt)) return OHM_ERR_INVALID;
     if (eta_dev) {
         int st = ohm_set_eta(h, eta_dev);
         if (st) return st;
@@ -1082,7 +1516,7 @@ int ohm_cn_step(ohm_hier *h, double *B_dev, const double *eta_dev, double dt, do
 }
 
 int ohm_residual_norm(ohm_hier *h, const double *B_dev, double *rel_l2, double *max_abs) {
-    if (!h || !B_dev || !h->has_S || !h->eta_set) return OHM_ERR_INVALID;
+    if (!h || h->batched || !B_dev || !h->has_S || !h->eta_set) return OHM_ERR_INVALID;
     CK(cudaMemcpyAsync(h->Bscr, B_dev, (size_t)h->nblocks * 3 * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     int st;
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
@@ -1101,7 +1535,7 @@ int ohm_residual_norm(ohm_hier *h, const double *B_dev, double *rel_l2, double *
 }
 
 int ohm_op_sync_down(ohm_hier *h, double *B_dev) {
-    if (!h || !B_dev) return OHM_ERR_INVALID;
+    if (!h || h->batched || !B_dev) return OHM_ERR_INVALID;
     return sync_down(h, B_dev);
 }
 
@@ -1123,23 +1557,23 @@ static int op_composite(ohm_hier *h, const double *X, const double *Y, double a,
 }
 
 int ohm_op_div_flux(ohm_hier *h, const double *B_dev, double *out_dev) {
-    if (!h || !B_dev || !out_dev) return OHM_ERR_INVALID;
+    if (!h || h->batched || !B_dev || !out_dev) return OHM_ERR_INVALID;
     return op_composite(h, B_dev, nullptr, 0.0, 1.0, 0.0, out_dev, nullptr);
 }
 
 int ohm_op_source(ohm_hier *h, const double *b_dev, double dt, double *S_dev) {
-    if (!h || !b_dev || !S_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    if (!h || h->batched || !b_dev || !S_dev || !(dt > 0)) return OHM_ERR_INVALID;
     return op_composite(h, b_dev, nullptr, 1.0, -(1.0 - h->d.lambda) * dt, 0.0, S_dev, nullptr);
 }
 
 int ohm_op_residual(ohm_hier *h, const double *B_dev, const double *S_dev, double dt, double *R_dev, double *norms) {
-    if (!h || !B_dev || !S_dev || !R_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    if (!h || h->batched || !B_dev || !S_dev || !R_dev || !(dt > 0)) return OHM_ERR_INVALID;
     double tmp[4];
     return op_composite(h, B_dev, S_dev, -1.0, -h->d.lambda * dt, 1.0, R_dev, norms ? norms : tmp);
 }
 
 int ohm_op_vcycle(ohm_hier *h, const double *R_dev, double dt, double *e_dev) {
-    if (!h || !R_dev || !e_dev || !(dt > 0) || h->mixed || !h->eta_set) return OHM_ERR_INVALID;
+    if (!h || h->batched || !R_dev || !e_dev || !(dt > 0) || h->mixed || !h->eta_set) return OHM_ERR_INVALID;
     int st;
     if ((st = prepare_dt<double>(h, dt))) return st;
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
@@ -1209,7 +1643,7 @@ int ohm_mg_grid_info(ohm_hier *h, int m, int32_t dims[3], int64_t *nblocks, int3
 // Single-grid steps: copy the caller's arrays into grid m's buffers, run one kernel, copy
 // back.  They overwrite that grid's eta, so ohm_set_eta is required again before a step.
 static int grid_setup(ohm_hier *h, int m, const double *eta_dev, double dt, GridRef &G) {
-    if (!h || h->mixed || m < 0 || m > (int)h->mg.size() || !eta_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    if (!h || h->batched || h->mixed || m < 0 || m > (int)h->mg.size() || !eta_dev || !(dt > 0)) return OHM_ERR_INVALID;
     if (m == 0 && h->nlev > 1) return OHM_ERR_INVALID;
     G = base_ref<double>(h, m);
     const size_t nb = (size_t)G.g->n();
@@ -1251,7 +1685,7 @@ int ohm_op_grid_residual(ohm_hier *h, int m, const double *e_dev, const double *
 }
 
 int ohm_op_grid_restrict(ohm_hier *h, int m, const double *fine_dev, double *coarse_dev, int ncomp) {
-    if (!h || h->mixed || !fine_dev || !coarse_dev || (ncomp != 1 && ncomp != 3)) return OHM_ERR_INVALID;
+    if (!h || h->batched || h->mixed || !fine_dev || !coarse_dev || (ncomp != 1 && ncomp != 3)) return OHM_ERR_INVALID;
     if (m < 0 || m >= (int)h->mg.size() || (m == 0 && h->nlev > 1)) return OHM_ERR_INVALID;
     const HGrid &g = m == 0 ? h->amr[0] : h->mg[m - 1];
     CK(launch_restrict<double>(g.dev, fine_dev, ncomp, coarse_dev, nullptr, nullptr, h->s));
@@ -1260,7 +1694,7 @@ int ohm_op_grid_restrict(ohm_hier *h, int m, const double *fine_dev, double *coa
 }
 
 int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double *fine_dev) {
-    if (!h || h->mixed || !fine_dev || !coarse_dev) return OHM_ERR_INVALID;
+    if (!h || h->batched || h->mixed || !fine_dev || !coarse_dev) return OHM_ERR_INVALID;
     if (m < 0 || m >= (int)h->mg.size() || (m == 0 && h->nlev > 1)) return OHM_ERR_INVALID;
     const HGrid &g = m == 0 ? h->amr[0] : h->mg[m - 1];
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));

@@ -32,6 +32,8 @@ struct GridDev {
     const int *slot_block = nullptr;// [nslot] block owning each ghost slot
     int nslot = 0;
     int slot0 = 0;                  // first ghost slot of this grid in the global slot array
+    int inst_nblk = 0;              // batched hierarchies: blocks per instance (instance of block b
+                                    // = b / inst_nblk); 0 = one instance
 };
 
 // Lexicographic coarse grids below the last blocked grid (solved in one thread block).
@@ -39,6 +41,8 @@ constexpr int MAX_SMALL = 12;
 template <typename T>
 struct SmallDev {
     int n = 0;                      // number of small grids
+    int ninst = 1;                  // instances; the arrays of grid s hold them one after another
+                                    // (instance q at q * ncomp * cells(s)), one thread block each
     int dims[MAX_SMALL][3];
     double h[MAX_SMALL];
     T *e[MAX_SMALL], *r[MAX_SMALL], *t[MAX_SMALL], *eta[MAX_SMALL], *inv[MAX_SMALL];
@@ -91,11 +95,26 @@ cudaError_t launch_ghost_fill(const GridDev &g, const GridDev &gc, const TS *coa
 template <typename T>
 cudaError_t launch_sync_down(const GridDev &gc, T *Bc, const T *Bf, cudaStream_t s);
 
+// x += y / B += e on leaf blocks; with imask, only on blocks of instances whose flag is set
 template <typename T>
-cudaError_t launch_axpy_leaf(const GridDev &g, T *x, const T *y, cudaStream_t s);
+cudaError_t launch_axpy_leaf(const GridDev &g, T *x, const T *y, const uint8_t *imask, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_update(const GridDev &g, double *B, const T *e, cudaStream_t s);
+cudaError_t launch_update(const GridDev &g, double *B, const T *e, const uint8_t *imask, cudaStream_t s);
+
+// Per-instance norms of a batched hierarchy: instance q owns blocks [off[l] + q n[l],
+// off[l] + (q+1) n[l]) of every level l; out[q] = {sum R^2 dV, sum S^2 dV, max |R|, 0},
+// each folded in a fixed order that does not depend on the other instances.
+constexpr int MAX_LEVELS_DEV = 8;
+struct InstRanges {
+    int nlev = 0;
+    int off[MAX_LEVELS_DEV];
+    int n[MAX_LEVELS_DEV];
+};
+cudaError_t launch_norm_inst(const double *partials, const InstRanges &R, int ninst, double *out, cudaStream_t s);
+
+// dst[b][512] = src[b][512] * scale[b] (per-block scale of a block field)
+cudaError_t launch_scale_blocks(const double *src, double *dst, const double *scale, int nblk, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_invdiag(const GridDev &g, const T *eta, const T *Geta, double lamdt, T *inv,

@@ -375,11 +375,9 @@ cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const T
                              double *partials, double vol, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = (4 * Geo<TC>::CS + Geo<TC>::PHI) * sizeof(TC);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_composite<TC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-    }
+    // set once per process (thread-safe static initialisation)
+    static const bool attr = (cudaFuncSetAttribute(k_composite<TC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
+    (void)attr;
     double coef = c / (2.0 * g.h * g.h);
     k_composite<TC, TO><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg, rsrc_tab,
                                                 partials, vol);
@@ -585,11 +583,9 @@ cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T 
                              cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = 4 * G12<T>::CS * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_smooth_rb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-    }
+    // set once per process (thread-safe static initialisation)
+    static const bool attr = (cudaFuncSetAttribute(k_smooth_rb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
+    (void)attr;
     k_smooth_rb<T><<<g.nblk, 256, sm, s>>>(g, e_in, e_out, r, eta, (T)(lamdt / (2.0 * g.h * g.h)),
                                           (T)(lamdt / (g.h * g.h)));
     return cudaGetLastError();
@@ -637,6 +633,16 @@ cudaError_t launch_invdiag(const GridDev &g, const T *eta, const T *Geta, double
 }
 template cudaError_t launch_invdiag<double>(const GridDev &, const double *, const double *, double, double *, cudaStream_t);
 template cudaError_t launch_invdiag<float>(const GridDev &, const float *, const float *, double, float *, cudaStream_t);
+
+// Offset of block b's instance in a lexicographic grid of ld cells and ncomp components
+// (batched hierarchies stack one such grid per instance)
+__device__ __forceinline__ size_t lex_inst_offset(const GridDev &g, int b, int ncomp, int3 ld) {
+    return g.inst_nblk ? (size_t)(b / g.inst_nblk) * ncomp * ((size_t)ld.x * ld.y * ld.z) : 0;
+}
+
+__device__ __forceinline__ bool inst_masked(const GridDev &g, const uint8_t *imask, int b) {
+    return imask && !imask[g.inst_nblk ? b / g.inst_nblk : 0];
+}
 
 // ------------------------------------------------------------------ residual + restriction
 template <typename T>
@@ -689,7 +695,8 @@ __global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__re
             coarse[((size_t)pb * 3 + c) * B3 + (z * 8 + y) * 8 + x] = s;
         } else {
             const int x = 4 * g.origin[b * 3 + 0] + ci, y = 4 * g.origin[b * 3 + 1] + cj, z = 4 * g.origin[b * 3 + 2] + ck;
-            lex[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x] = s;
+            T *lx = lex + lex_inst_offset(g, b, 3, ld);
+            lx[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x] = s;
         }
     }
 }
@@ -699,11 +706,9 @@ cudaError_t launch_resid_restrict(const GridDev &g, const T *e, const T *r, cons
                                   double lamdt, T *t_out, T *coarse, T *lex, const int *ldims, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = (4 * Geo<T>::CS + Geo<T>::PHI + 3 * B3) * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_resid_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-    }
+    // set once per process (thread-safe static initialisation)
+    static const bool attr = (cudaFuncSetAttribute(k_resid_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
+    (void)attr;
     int3 ld = make_int3(ldims ? ldims[0] : 0, ldims ? ldims[1] : 0, ldims ? ldims[2] : 0);
     k_resid_restrict<T><<<g.nblk, 512, sm, s>>>(g, e, r, eta, Ge, Geta, (T)(lamdt / (2.0 * g.h * g.h)), t_out, coarse,
                                                 lex, ld);
@@ -736,7 +741,8 @@ __global__ void __launch_bounds__(512) k_restrict(GridDev g, const T *__restrict
             coarse[((size_t)pb * ncomp + c) * B3 + (z * 8 + y) * 8 + x] = s;
         } else {
             const int x = 4 * g.origin[b * 3 + 0] + ci, y = 4 * g.origin[b * 3 + 1] + cj, z = 4 * g.origin[b * 3 + 2] + ck;
-            lex[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x] = s;
+            T *lx = lex + lex_inst_offset(g, b, ncomp, ld);
+            lx[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x] = s;
         }
     }
 }
@@ -769,7 +775,8 @@ __global__ void __launch_bounds__(512) k_prolong_add(GridDev g, GridDev gc, cons
         if (lex) {
             int x = 4 * g.origin[b * 3 + 0] - 1 + wx, y = 4 * g.origin[b * 3 + 1] - 1 + wy, z = 4 * g.origin[b * 3 + 2] - 1 + wz;
             x = (x + ld.x) % ld.x; y = (y + ld.y) % ld.y; z = (z + ld.z) % ld.z;
-            for (int c = 0; c < 3; c++) win[c * 216 + q] = lex[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x];
+            const T *lx = lex + lex_inst_offset(g, b, 3, ld);
+            for (int c = 0; c < 3; c++) win[c * 216 + q] = lx[(((size_t)c * ld.z + z) * ld.y + y) * ld.x + x];
         } else {
             int cx = 4 * (o & 1) - 1 + wx, cy = 4 * ((o >> 1) & 1) - 1 + wy, cz = 4 * (o >> 2) - 1 + wz;
             int dx = cx < 0 ? -1 : (cx > 7 ? 1 : 0), dy = cy < 0 ? -1 : (cy > 7 ? 1 : 0), dz = cz < 0 ? -1 : (cz > 7 ? 1 : 0);
@@ -916,9 +923,10 @@ template cudaError_t launch_sync_down<float>(const GridDev &, float *, const flo
 
 // x += y on leaf blocks (inner correction accumulation)
 template <typename T>
-__global__ void __launch_bounds__(512) k_axpy_leaf(GridDev g, T *__restrict__ x, const T *__restrict__ y) {
+__global__ void __launch_bounds__(512) k_axpy_leaf(GridDev g, T *__restrict__ x, const T *__restrict__ y,
+                                                   const uint8_t *__restrict__ imask) {
     const int b = blockIdx.x;
-    if (g.covered && g.covered[b]) return;
+    if ((g.covered && g.covered[b]) || inst_masked(g, imask, b)) return;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         size_t id = ((size_t)b * 3 + c) * B3 + threadIdx.x;
@@ -927,18 +935,19 @@ __global__ void __launch_bounds__(512) k_axpy_leaf(GridDev g, T *__restrict__ x,
 }
 
 template <typename T>
-cudaError_t launch_axpy_leaf(const GridDev &g, T *x, const T *y, cudaStream_t s) {
+cudaError_t launch_axpy_leaf(const GridDev &g, T *x, const T *y, const uint8_t *imask, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
-    k_axpy_leaf<T><<<g.nblk, 512, 0, s>>>(g, x, y);
+    k_axpy_leaf<T><<<g.nblk, 512, 0, s>>>(g, x, y, imask);
     return cudaGetLastError();
 }
-template cudaError_t launch_axpy_leaf<float>(const GridDev &, float *, const float *, cudaStream_t);
-template cudaError_t launch_axpy_leaf<double>(const GridDev &, double *, const double *, cudaStream_t);
+template cudaError_t launch_axpy_leaf<float>(const GridDev &, float *, const float *, const uint8_t *, cudaStream_t);
+template cudaError_t launch_axpy_leaf<double>(const GridDev &, double *, const double *, const uint8_t *, cudaStream_t);
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_update(GridDev g, double *__restrict__ B, const T *__restrict__ e) {
+__global__ void __launch_bounds__(512) k_update(GridDev g, double *__restrict__ B, const T *__restrict__ e,
+                                                const uint8_t *__restrict__ imask) {
     const int b = blockIdx.x;
-    if (g.covered && g.covered[b]) return;
+    if ((g.covered && g.covered[b]) || inst_masked(g, imask, b)) return;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         size_t id = ((size_t)b * 3 + c) * B3 + threadIdx.x;
@@ -947,13 +956,13 @@ __global__ void __launch_bounds__(512) k_update(GridDev g, double *__restrict__ 
 }
 
 template <typename T>
-cudaError_t launch_update(const GridDev &g, double *B, const T *e, cudaStream_t s) {
+cudaError_t launch_update(const GridDev &g, double *B, const T *e, const uint8_t *imask, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
-    k_update<T><<<g.nblk, 512, 0, s>>>(g, B, e);
+    k_update<T><<<g.nblk, 512, 0, s>>>(g, B, e, imask);
     return cudaGetLastError();
 }
-template cudaError_t launch_update<double>(const GridDev &, double *, const double *, cudaStream_t);
-template cudaError_t launch_update<float>(const GridDev &, double *, const float *, cudaStream_t);
+template cudaError_t launch_update<double>(const GridDev &, double *, const double *, const uint8_t *, cudaStream_t);
+template cudaError_t launch_update<float>(const GridDev &, double *, const float *, const uint8_t *, cudaStream_t);
 
 __global__ void __launch_bounds__(512) k_zero_covered(GridDev g, double *__restrict__ x) {
     const int b = blockIdx.x;
@@ -1017,6 +1026,50 @@ __global__ void __launch_bounds__(256) k_norm_reduce(const double *__restrict__ 
 cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s) {
     int grid = nblocks < NRED * 64 ? (nblocks + 63) / 64 : NRED;
     k_norm_reduce<<<grid, 256, 0, s>>>(partials, nblocks, scratch, (unsigned int *)(scratch + 3 * NRED), out);
+    return cudaGetLastError();
+}
+
+// One thread block per instance; its level ranges are folded in level order, each range in a
+// fixed thread-strided order, so the result does not depend on the other instances.
+__global__ void __launch_bounds__(256) k_norm_inst(const double *__restrict__ part, InstRanges R,
+                                                   double *__restrict__ out) {
+    __shared__ double red[32];
+    const int q = blockIdx.x;
+    double a = 0.0, b = 0.0, m = 0.0;
+    for (int l = 0; l < R.nlev; l++) {
+        const int lo = R.off[l] + q * R.n[l], hi = lo + R.n[l];
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            a += part[i * 3 + 0];
+            b += part[i * 3 + 1];
+            m = fmax(m, part[i * 3 + 2]);
+        }
+    }
+    const double sa = block_sum(a, red);
+    const double sb = block_sum(b, red);
+    const double sm = block_max(m, red);
+    if (threadIdx.x == 0) {
+        out[q * 4 + 0] = sa;
+        out[q * 4 + 1] = sb;
+        out[q * 4 + 2] = sm;
+        out[q * 4 + 3] = 0.0;
+    }
+}
+
+cudaError_t launch_norm_inst(const double *partials, const InstRanges &R, int ninst, double *out, cudaStream_t s) {
+    if (ninst <= 0) return cudaSuccess;
+    k_norm_inst<<<ninst, 256, 0, s>>>(partials, R, out);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(512) k_scale_blocks(const double *__restrict__ src, double *__restrict__ dst,
+                                                      const double *__restrict__ scale) {
+    const size_t id = (size_t)blockIdx.x * B3 + threadIdx.x;
+    dst[id] = src[id] * scale[blockIdx.x];
+}
+
+cudaError_t launch_scale_blocks(const double *src, double *dst, const double *scale, int nblk, cudaStream_t s) {
+    if (nblk <= 0) return cudaSuccess;
+    k_scale_blocks<<<nblk, 512, 0, s>>>(src, dst, scale);
     return cudaGetLastError();
 }
 
@@ -1130,8 +1183,8 @@ cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float sc
 }
 
 // ------------------------------------------------------------------ coarsest grids
-// Lexicographic periodic grids below the last blocked grid, all handled by one thread block
-// with a barrier between phases.  Face flux and divergence as above, with periodic wrap.
+// Lexicographic periodic grids below the last blocked grid, all handled by one thread block per
+// instance with a barrier between phases.  Face flux and divergence as above, with periodic wrap.
 template <typename T>
 struct LexGrid {
     int nx, ny, nz;
@@ -1206,8 +1259,25 @@ __device__ void lex_sweeps(const SmallDev<T> &sm, int s, double lamdt, int nswee
         }
 }
 
+// the grids of instance blockIdx.x
 template <typename T>
-__global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm, double lamdt, int nu1, int nu2, int nc) {
+__device__ __forceinline__ SmallDev<T> small_instance(const SmallDev<T> &in) {
+    SmallDev<T> sm = in;
+    const size_t q = blockIdx.x;
+    for (int s = 0; s < sm.n; s++) {
+        const size_t cells = (size_t)sm.dims[s][0] * sm.dims[s][1] * sm.dims[s][2];
+        sm.e[s] += q * 3 * cells;
+        sm.r[s] += q * 3 * cells;
+        sm.t[s] += q * 3 * cells;
+        sm.inv[s] += q * 3 * cells;
+        sm.eta[s] += q * cells;
+    }
+    return sm;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm_all, double lamdt, int nu1, int nu2, int nc) {
+    const SmallDev<T> sm = small_instance(sm_all);
     // e on the first small grid starts from zero
     {
         const int n0 = sm.dims[0][0] * sm.dims[0][1] * sm.dims[0][2];
@@ -1270,7 +1340,7 @@ __global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm, double lamdt, i
 template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post, int n_coarse, cudaStream_t s) {
     if (sm.n == 0) return cudaSuccess;
-    k_bottom<T><<<1, 1024, 0, s>>>(sm, lamdt, nu_pre, nu_post, n_coarse);
+    k_bottom<T><<<sm.ninst, 1024, 0, s>>>(sm, lamdt, nu_pre, nu_post, n_coarse);
     return cudaGetLastError();
 }
 template cudaError_t launch_bottom<double>(const SmallDev<double> &, double, int, int, int, cudaStream_t);
@@ -1278,7 +1348,8 @@ template cudaError_t launch_bottom<float>(const SmallDev<float> &, double, int, 
 
 // eta chain over the small grids (optional) and their inverse diagonals
 template <typename T>
-__global__ void __launch_bounds__(1024) k_small_setup(SmallDev<T> sm, double lamdt, int eta_chain) {
+__global__ void __launch_bounds__(1024) k_small_setup(SmallDev<T> sm_all, double lamdt, int eta_chain) {
+    const SmallDev<T> sm = small_instance(sm_all);
     if (eta_chain) {
         for (int s = 1; s < sm.n; s++) {
             LexGrid<T> F{sm.dims[s - 1][0], sm.dims[s - 1][1], sm.dims[s - 1][2]};
@@ -1320,7 +1391,7 @@ __global__ void __launch_bounds__(1024) k_small_setup(SmallDev<T> sm, double lam
 template <typename T>
 cudaError_t launch_small_setup(const SmallDev<T> &sm, double lamdt, bool eta_chain, cudaStream_t s) {
     if (sm.n == 0) return cudaSuccess;
-    k_small_setup<T><<<1, 1024, 0, s>>>(sm, lamdt, eta_chain ? 1 : 0);
+    k_small_setup<T><<<sm.ninst, 1024, 0, s>>>(sm, lamdt, eta_chain ? 1 : 0);
     return cudaGetLastError();
 }
 template cudaError_t launch_small_setup<double>(const SmallDev<double> &, double, bool, cudaStream_t);

@@ -35,12 +35,18 @@ class HierDesc(C.Structure):
     _fields_ = [("base_cells", C.c_int32 * 3), ("dx0", C.c_double), ("nlevels", C.c_int32), ("nblocks", C.c_int64),
                 ("block_lijk", C.POINTER(C.c_int32)), ("lam", C.c_double), ("precision", C.c_int32),
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32), ("max_outer", C.c_int32),
-                ("krylov", C.c_int32), ("inner_tol", C.c_double), ("stream", C.c_void_p)]
+                ("krylov", C.c_int32), ("inner_tol", C.c_double), ("n_instances", C.c_int32),
+                ("use_graphs", C.c_int32), ("stream", C.c_void_p)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("converged", C.c_int32), ("rel_l2_initial", C.c_double),
                 ("rel_l2", C.c_double), ("max_abs", C.c_double)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32), ("smoother", C.c_int32),
+                ("ms", C.c_double), ("candidates", C.c_int32)]
 
 
 _lib = None
@@ -76,6 +82,9 @@ def lib():
         L.ohm_prof_read.argtypes = [vp, C.POINTER(dp), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.ohm_launch_count.argtypes = [vp]
         L.ohm_launch_count.restype = C.c_int64
+        L.ohm_cn_step_batch.argtypes = [vp, vp, C.POINTER(dp), dp, C.POINTER(C.c_uint8), C.POINTER(StepStats)]
+        L.ohm_hierarchy_bytes.argtypes = [C.POINTER(HierDesc), C.POINTER(C.c_int64)]
+        L.ohm_autotune.argtypes = [vp, vp, C.POINTER(dp), dp, C.POINTER(TuneResult)]
         _lib = L
     return _lib
 
@@ -105,11 +114,12 @@ def _check(status: int, what: str, allow=(OHM_OK,)):
 class Hierarchy:
     """Owning handle of an ohm_hier (ohm_create_hierarchy / ohm_destroy)."""
 
-    def __init__(self, handle, nblocks: int, lam: float, mixed: bool):
+    def __init__(self, handle, nblocks: int, lam: float, mixed: bool, n_instances: int = 0):
         self._h = handle
-        self.nblocks = nblocks
+        self.nblocks = nblocks  # all instances of a batch
         self.lam = lam
         self.mixed = mixed
+        self.n_instances = n_instances
 
     @property
     def handle(self):
@@ -127,16 +137,8 @@ class Hierarchy:
             pass
 
 
-def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
-                         nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50,
-                         stream=None, krylov: int = 0, inner_tol: float = 0.0) -> Hierarchy:
-    """blocks: int32 [nblocks, 4] rows (level, bi, bj, bk) sorted by level.
-    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None for torch's current stream."""
-    import torch
-    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+def _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coarse, max_outer, raw_stream, krylov,
+               inner_tol, n_instances, use_graphs):
     d = HierDesc()
     d.base_cells[:] = [int(v) for v in base_cells]
     d.dx0 = float(dx0)
@@ -148,10 +150,67 @@ def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, preci
     d.nu_pre, d.nu_post, d.n_coarse, d.max_outer = int(nu_pre), int(nu_post), int(n_coarse), int(max_outer)
     d.krylov = int(krylov)
     d.inner_tol = float(inner_tol)
-    d.stream = C.c_void_p(raw)
+    d.n_instances = int(n_instances)
+    d.use_graphs = 1 if use_graphs else 0
+    d.stream = C.c_void_p(raw_stream)
+    return d
+
+
+def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
+                         nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50,
+                         stream=None, krylov: int = 0, inner_tol: float = 0.0, n_instances: int = 0,
+                         use_graphs: bool = False) -> Hierarchy:
+    """blocks: int32 [nblocks, 4] rows (level, bi, bj, bk) sorted by level (one instance).
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None for torch's current stream.
+    n_instances >= 1 makes a batch of that many independent instances (ohm_cn_step_batch)."""
+    import torch
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    d = _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coarse, max_outer, raw, krylov,
+                   inner_tol, n_instances, use_graphs)
     h = C.c_void_p()
     _check(lib().ohm_create_hierarchy(C.byref(d), C.byref(h)), "ohm_create_hierarchy")
-    return Hierarchy(h, len(blocks), lam, precision == OHM_MIXED)
+    return Hierarchy(h, len(blocks) * max(1, int(n_instances)), lam, precision == OHM_MIXED, int(n_instances))
+
+
+def ohm_hierarchy_bytes(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
+                        nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50, krylov: int = 0,
+                        inner_tol: float = 0.0, n_instances: int = 0) -> int:
+    """Device bytes ohm_create_hierarchy would allocate for this description (no allocation)."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32)
+    d = _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coarse, max_outer, 0, krylov,
+                   inner_tol, n_instances, False)
+    out = C.c_int64()
+    _check(lib().ohm_hierarchy_bytes(C.byref(d), C.byref(out)), "ohm_hierarchy_bytes")
+    return int(out.value)
+
+
+def ohm_cn_step_batch(h: Hierarchy, B, dt, tol: float, active=None) -> tuple[int, list]:
+    """Batched step in place on B (all instances' blocks, level by level).  dt: one value per
+    instance; active: optional per-instance flags.  Returns (status, per-instance stats); raises
+    on statuses other than OHM_OK / OHM_ERR_NOT_CONVERGED."""
+    K = h.n_instances
+    dts = (C.c_double * K)(*[float(v) for v in dt])
+    act = None
+    if active is not None:
+        act = (C.c_uint8 * K)(*[1 if a else 0 for a in active])
+    st = (StepStats * K)()
+    status = lib().ohm_cn_step_batch(h.handle, _ptr(B, h.nblocks * 1536, "B"), dts, float(tol), act, st)
+    _check(status, "ohm_cn_step_batch", allow=(OHM_OK, OHM_ERR_NOT_CONVERGED))
+    return status, [{"cycles": x.cycles, "converged": bool(x.converged), "rel_l2_initial": x.rel_l2_initial,
+                     "rel_l2": x.rel_l2, "max_abs": x.max_abs} for x in st]
+
+
+def ohm_autotune(h: Hierarchy, B, dt, tol: float) -> dict:
+    """Times the candidate schedules on copies of B and keeps the fastest (see include/ohm.h)."""
+    dts = list(dt) if hasattr(dt, "__len__") else [dt]
+    arr = (C.c_double * len(dts))(*[float(v) for v in dts])
+    r = TuneResult()
+    _check(lib().ohm_autotune(h.handle, _ptr(B, h.nblocks * 1536, "B"), arr, float(tol), C.byref(r)), "ohm_autotune")
+    return {"nu_pre": r.nu_pre, "nu_post": r.nu_post, "n_coarse": r.n_coarse, "smoother": r.smoother, "ms": r.ms,
+            "candidates": r.candidates}
 
 
 def ohm_set_eta(h: Hierarchy, eta) -> None:

@@ -318,3 +318,51 @@ def sinusoid_half_refined(N: int = 8, lam: float = 0.5, dt: float = 1e-4, t_end:
     eta = np.ones((h.nblocks, 1, BS, BS, BS))
     steps = int(round(t_end / dt))
     return Workload(f"sinusoid_half_refined_N{N}", h, B, eta, dt=dt, steps=steps, tol=1e-12, lam=lam)
+
+
+# ----------------------------------------------------------------------------- batches
+BATCH_EDGES = (16, 24, 32, 48, 64)
+
+
+def smooth_lognormal_eta(n: int, seed: int, decades: float = 2.0, eta_min: float = 1e-3,
+                         sigma_cells: float = 2.0) -> np.ndarray:
+    """Dense [1][n][n][n] resistivity eta = eta_min 10^(decades u): u is seeded normal noise
+    smoothed by a periodic Gaussian filter of width sigma_cells (applied as its Fourier
+    transfer function exp(-2 pi^2 sigma^2 k^2), k in cycles per cell) and rescaled to [0, 1]."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal((n, n, n))
+    k = np.fft.fftfreq(n)
+    kr = np.fft.rfftfreq(n)
+    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2
+    u = np.fft.irfftn(np.fft.rfftn(noise) * np.exp(-2.0 * math.pi ** 2 * sigma_cells ** 2 * k2), s=(n, n, n))
+    u = (u - u.min()) / (u.max() - u.min())
+    return (eta_min * 10.0 ** (decades * u))[None]
+
+
+@dataclasses.dataclass
+class Instance:
+    n: int
+    hier: Hierarchy
+    B: np.ndarray      # [nblocks][3][8][8][8]
+    eta: np.ndarray    # [nblocks][1][8][8][8]
+    dt: float
+
+
+def batched_instances(count: int = 512, seed: int = 4, edges=BATCH_EDGES, tol: float = 1e-9) -> list[Instance]:
+    """Independent periodic unit boxes: edge drawn uniformly from `edges` (seeded), eta from
+    smooth_lognormal_eta (2 decades), B = curl of a k^-2 random potential (rms 1), dt = U(10,
+    100) times the explicit limit dx^2/(6 eta_max), one step each to `tol`.  Instance q's fields
+    use seeds derived from (seed, q) only, so any prefix of the list is reproducible alone."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(edges), size=count)
+    hiers = {}
+    out = []
+    for q, n in enumerate(int(v) for v in ns):
+        dx = 1.0 / n
+        h = hiers.setdefault(n, uniform(n, n, n, dx))
+        base = 1_000_003 * seed + 7 * q
+        B = random_potential_field((n, n, n), dx, base + 1, 1.0)
+        eta = smooth_lognormal_eta(n, base + 2)
+        f = float(np.random.default_rng(base + 3).uniform(10.0, 100.0))
+        out.append(Instance(n, h, dense_to_blocks(h, B), dense_to_blocks(h, eta), f * dx * dx / (6.0 * float(eta.max()))))
+    return out

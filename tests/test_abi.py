@@ -1,5 +1,5 @@
-"""CPU-side checks of the C ABI: the library exports every symbol include/ohm.h declares and
-rejects bad descriptors before touching the GPU."""
+"""CPU-side checks of the C ABI: the library exports every symbol the headers under include/
+declare and rejects bad descriptors before touching the GPU."""
 import ctypes as C
 import os
 import re
@@ -11,9 +11,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "ohm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ohm_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", hdr)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ohm_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -84,3 +88,22 @@ def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
     with pytest.raises(libohm.OhmError) as ei:
         libohm.ohm_create_hierarchy(base, 1.0 / base[0], blocks, **kw)
     assert ei.value.status == libohm.OHM_ERR_INVALID
+
+
+def test_batch_bytes_grow_with_instances(libohm):
+    """ohm_hierarchy_bytes: host-only sizing of batched hierarchies (admission control)."""
+    from paper_1009_0798_gb300 import workloads as W
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    one = libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=1)
+    four = libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=4)
+    assert 3.5 * one < four < 4.5 * one
+    with pytest.raises(libohm.OhmError):
+        libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=4, krylov=4)
+
+
+def test_server_rejects_bad_descriptor_without_gpu(libohm):
+    from paper_1009_0798_gb300 import server
+    with pytest.raises(libohm.OhmError):
+        server.Server(hbm_budget_bytes=0)
+    with pytest.raises(libohm.OhmError):
+        server.Server(hbm_budget_bytes=1 << 30, max_batch=0)
