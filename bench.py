@@ -733,8 +733,10 @@ def run_serving(args):
     torch.cuda.init()
     reqs = serving_requests(args.requests, args.rate)
     budget = 60 << 30
+    # V(4,4) with 4 coarsest sweeps: the schedule the autotuner picks for every class of the
+    # batched workload (defect-correction inner solves)
     cfg = dict(hbm_budget_bytes=budget, max_batch=8, n_workers=6, precision=1, tol=1e-9, use_graphs=True,
-               n_coarse=args.n_coarse, max_outer=400)
+               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400)
     # warm-up service: one request per class (kernels loaded, batches of each class built once)
     with server.Server(**cfg) as s:
         seen = {}

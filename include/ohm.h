@@ -220,7 +220,9 @@ int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double
 int ohm_prof_enable(ohm_hier *h, int kernel, int min_blocks, int max_launches);
 
 /* Synchronises the stream, returns the summed event time of the timed launches since the
- * last read, their count and the cells they covered, then resets the counters. */
+ * last read, their count and the cells they covered, then resets the counters.  In a batch,
+ * cells count only the instances the launch iterated (blocks of stopped instances return at
+ * once and are not counted). */
 int ohm_prof_read(ohm_hier *h, double *total_ms, int64_t *launches, int64_t *cells);
 
 /* Kernel launches this hierarchy has issued since creation (all kinds). */

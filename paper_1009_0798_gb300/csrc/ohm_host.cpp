@@ -112,6 +112,8 @@ struct ohm_hier {
     bool eta_dirty = false;
     InstRanges ranges;
     int smoother = 0;             // 0: fused red+black sweep where possible, 1: two colour passes
+    const uint8_t *cmask = nullptr;  // compute mask of batched iterations (null: every instance)
+    double active_frac = 1.0;        // share of instances the compute mask lets through (timing)
     // CUDA graph of the batched inner iteration
     cudaGraphExec_t graph = nullptr;
     bool graph_warm = false, graph_failed = false;
@@ -590,7 +592,7 @@ inline void prof_end(ohm_hier *H, int i, int nblk) {
     cudaEventRecord(H->prof_ev[i + 1], H->s);
     H->prof_used += 2;
     H->prof_launches++;
-    H->prof_cells += (int64_t)nblk * B3;
+    H->prof_cells += (int64_t)std::llround((double)nblk * B3 * (H->cmask ? H->active_frac : 1.0));
 }
 #define LAUNCH(H, kind, nblk, call)            \
     do {                                       \
@@ -610,6 +612,7 @@ SmallDev<T> small_dev(ohm_hier *H) {
     SmallDev<T> sm;
     sm.n = (int)H->small.size();
     sm.ninst = H->K;
+    sm.imask = H->cmask;
     double h = H->d.dx0 * std::pow(2.0, (double)(H->mg.size() + 1));
     for (int q = 0; q < sm.n; q++) {
         for (int a = 0; a < 3; a++) sm.dims[q][a] = H->small[q][a];
@@ -666,6 +669,13 @@ int prepare_dt(ohm_hier *H, double dt) {
     return OHM_OK;
 }
 
+// the grid's device tables with the current compute mask (batched inner iterations)
+GridDev gdev(const ohm_hier *H, const HGrid &g) {
+    GridDev d = g.dev;
+    d.imask = H->cmask;
+    return d;
+}
+
 struct GridRef {
     const HGrid *g;
     void *e, *e2, *r, *eta, *inv;
@@ -699,15 +709,15 @@ int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
         for (int i = 0; i < n; i++) {
             const T *src = (const T *)((i & 1) ? G.e2 : G.e);
             T *dst = (T *)((i & 1) ? G.e : G.e2);
-            LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb<T>(G.g->dev, src, dst, (const T *)G.r, (const T *)G.eta, lamdt, H->s));
+            LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb<T>(gdev(H, *G.g), src, dst, (const T *)G.r, (const T *)G.eta, lamdt, H->s));
         }
         if (n & 1) CK(cudaMemcpyAsync(G.e, G.e2, (size_t)G.g->n() * 3 * B3 * sizeof(T), cudaMemcpyDeviceToDevice, H->s));
         return OHM_OK;
     }
     for (int i = 0; i < n; i++) {
-        LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(G.g->dev, (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
+        LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(gdev(H, *G.g), (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
                             (const T *)G.Ge, (const T *)G.Geta, lamdt, 0, H->s));
-        LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(G.g->dev, (const T *)G.e2, (T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
+        LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(gdev(H, *G.g), (const T *)G.e2, (T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
                             (const T *)G.Ge, (const T *)G.Geta, lamdt, 1, H->s));
     }
     return OHM_OK;
@@ -723,17 +733,17 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const bool next_blocked = m < (int)H->mg.size();
     if (next_blocked) {
         GridRef C = base_ref<T>(H, m + 1);
-        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
+        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, (T *)C.r, nullptr, nullptr, H->s));
         CK(cudaMemsetAsync(C.e, 0, (size_t)C.g->n() * 3 * B3 * sizeof(T), H->s));
         if ((st = base_vcycle<T>(H, m + 1, lamdt))) return st;
-        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
     } else {
-        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(G.g->dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
+        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, nullptr, (T *)H->smallbuf[0].r, H->small[0].data(), H->s));
         SmallDev<T> sm = small_dev<T>(H);
         LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(sm, lamdt, d.nu_pre, d.nu_post, d.n_coarse, H->s));
-        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(G.g->dev, nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
+        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
                                  H->d_err, H->s));
     }
     return sweeps<T>(H, G, d.nu_post, lamdt);
@@ -752,7 +762,7 @@ int vcycle(ohm_hier *H, double lamdt) {
         if (g.nslot) CK(cudaMemsetAsync((T *)H->ghostE + (size_t)g.slot0 * 3 * T3, 0, (size_t)g.nslot * 3 * T3 * sizeof(T), H->s));
         if ((st = sweeps<T>(H, G, d.nu_pre, lamdt))) return st;
         GridRef C = amr_ref<T>(H, l - 1, true);
-        LAUNCH(H, OHM_K_RESID_RESTRICT, g.n(), launch_resid_restrict<T>(g.dev, (const T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.Ge,
+        LAUNCH(H, OHM_K_RESID_RESTRICT, g.n(), launch_resid_restrict<T>(gdev(H, g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.Ge,
                                     (const T *)G.Geta, lamdt, nullptr, (T *)C.r, nullptr, nullptr, H->s));
     }
     {
@@ -763,8 +773,8 @@ int vcycle(ohm_hier *H, double lamdt) {
     for (int l = 1; l < H->nlev; l++) {
         GridRef G = amr_ref<T>(H, l, true);
         GridRef C = amr_ref<T>(H, l - 1, true);
-        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(G.g->dev, &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
-        LAUNCH(H, OHM_K_GHOST, G.g->nslot, (launch_ghost_fill<T, T>(G.g->dev, C.g->dev, (const T *)C.e, 3, (T *)H->ghostE, H->d_err, H->s)));
+        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+        LAUNCH(H, OHM_K_GHOST, G.g->nslot, (launch_ghost_fill<T, T>(gdev(H, *G.g), C.g->dev, (const T *)C.e, 3, (T *)H->ghostE, H->d_err, H->s)));
         if ((st = sweeps<T>(H, G, d.nu_post, lamdt))) return st;
     }
     return OHM_OK;
@@ -772,13 +782,13 @@ int vcycle(ohm_hier *H, double lamdt) {
 
 int sync_down(ohm_hier *H, double *B) {
     for (int l = H->nlev - 2; l >= 0; l--)
-        LAUNCH(H, OHM_K_SYNC_DOWN, H->amr[l].n(), launch_sync_down(H->amr[l].dev, amr_ptr<double>(B, H->amr[l], 3), amr_ptr<double>(B, H->amr[l + 1], 3), H->s));
+        LAUNCH(H, OHM_K_SYNC_DOWN, H->amr[l].n(), launch_sync_down(gdev(H, H->amr[l]), amr_ptr<double>(B, H->amr[l], 3), amr_ptr<double>(B, H->amr[l + 1], 3), H->s));
     return OHM_OK;
 }
 
 int fill_ghosts_B(ohm_hier *H, const double *B) {
     for (int l = 1; l < H->nlev; l++)
-        LAUNCH(H, OHM_K_GHOST, H->amr[l].nslot, (launch_ghost_fill<double, double>(H->amr[l].dev, H->amr[l - 1].dev,
+        LAUNCH(H, OHM_K_GHOST, H->amr[l].nslot, (launch_ghost_fill<double, double>(gdev(H, H->amr[l]), H->amr[l - 1].dev,
                                               amr_ptr<double>((void *)B, H->amr[l - 1], 3), 3, H->ghostB, H->d_err, H->s)));
     return OHM_OK;
 }
@@ -793,7 +803,7 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
         double vol = g.h * g.h * g.h;
         const size_t o3 = (size_t)g.off * 3 * B3;
         LAUNCH(H, OHM_K_COMPOSITE, g.n(),
-               (launch_composite<TC, TO>(g.dev, X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta, a, c,
+               (launch_composite<TC, TO>(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta, a, c,
                                          dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
                                          norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s)));
     }
@@ -817,7 +827,7 @@ template <typename T>
 int sync_down_t(ohm_hier *H, T *x) {
     for (int l = H->nlev - 2; l >= 0; l--)
         LAUNCH(H, OHM_K_SYNC_DOWN, H->amr[l].n(),
-               launch_sync_down<T>(H->amr[l].dev, amr_ptr<T>(x, H->amr[l], 3), amr_ptr<T>(x, H->amr[l + 1], 3), H->s));
+               launch_sync_down<T>(gdev(H, H->amr[l]), amr_ptr<T>(x, H->amr[l], 3), amr_ptr<T>(x, H->amr[l + 1], 3), H->s));
     return OHM_OK;
 }
 
@@ -825,7 +835,7 @@ template <typename T>
 int fill_ghosts_t(ohm_hier *H, const T *x, T *ghost) {
     for (int l = 1; l < H->nlev; l++)
         LAUNCH(H, OHM_K_GHOST, H->amr[l].nslot,
-               (launch_ghost_fill<T, T>(H->amr[l].dev, H->amr[l - 1].dev, amr_ptr<T>((void *)x, H->amr[l - 1], 3), 3,
+               (launch_ghost_fill<T, T>(gdev(H, H->amr[l]), H->amr[l - 1].dev, amr_ptr<T>((void *)x, H->amr[l - 1], 3), 3,
                                         ghost, H->d_err, H->s)));
     return OHM_OK;
 }
@@ -1230,8 +1240,12 @@ int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const 
         if (!any) break;
         CK(cudaMemcpyAsync(omask_d, omask_h, K, cudaMemcpyHostToDevice, H->s));
         if (!H->mixed) {
-            // one float64 V-cycle for every running instance
-            if ((st = vcycle<T>(H, lamdt))) return st;
+            // one float64 V-cycle for every running instance (the others' blocks are skipped)
+            H->cmask = omask_d;
+            H->active_frac = (double)std::count(omask_h, omask_h + K, 1) / K;
+            st = vcycle<T>(H, lamdt);
+            H->cmask = nullptr;
+            if (st) return st;
             if ((st = update_all<T>(H, B, e, omask_d))) return st;
             for (int q = 0; q < K; q++) cycles[q] += omask_h[q];
         } else {
@@ -1244,6 +1258,8 @@ int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const 
             bool inner = true;
             while (inner) {
                 CK(cudaMemcpyAsync(imask_d, imask_h, K, cudaMemcpyHostToDevice, H->s));
+                H->cmask = imask_d;  // blocks of instances that stopped iterating are skipped
+                H->active_frac = (double)std::count(imask_h, imask_h + K, 1) / K;
                 st = run_iteration(H, [&]() -> int {
                     int s2;
                     if ((s2 = vcycle<T>(H, lamdt))) return s2;
@@ -1256,6 +1272,7 @@ int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const 
                         return s2;
                     return enqueue_norm_copy(H);
                 });
+                H->cmask = nullptr;
                 if (st) return st;
                 if ((st = read_norms_batch(H, ni, nmx, &ef))) return st;
                 inner = false;

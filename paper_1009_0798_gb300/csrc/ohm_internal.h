@@ -34,6 +34,8 @@ struct GridDev {
     int slot0 = 0;                  // first ghost slot of this grid in the global slot array
     int inst_nblk = 0;              // batched hierarchies: blocks per instance (instance of block b
                                     // = b / inst_nblk); 0 = one instance
+    const uint8_t *imask = nullptr; // batched inner iterations: thread blocks of instances whose
+                                    // flag is 0 return at once (their results are not used)
 };
 
 // Lexicographic coarse grids below the last blocked grid (solved in one thread block).
@@ -43,6 +45,7 @@ struct SmallDev {
     int n = 0;                      // number of small grids
     int ninst = 1;                  // instances; the arrays of grid s hold them one after another
                                     // (instance q at q * ncomp * cells(s)), one thread block each
+    const uint8_t *imask = nullptr; // k_bottom skips instances whose flag is 0
     int dims[MAX_SMALL][3];
     double h[MAX_SMALL];
     T *e[MAX_SMALL], *r[MAX_SMALL], *t[MAX_SMALL], *eta[MAX_SMALL], *inv[MAX_SMALL];

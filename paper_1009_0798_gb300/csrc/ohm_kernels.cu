@@ -20,6 +20,11 @@ namespace ohm {
 
 __device__ __forceinline__ int tix(int i, int j, int k) { return (k * TS + j) * TS + i; }
 
+// batched inner iterations: block b belongs to an instance that is not iterated
+__device__ __forceinline__ bool skip_block(const GridDev &g, int b) {
+    return g.imask && !g.imask[g.inst_nblk ? b / g.inst_nblk : 0];
+}
+
 // Shared-memory geometry of a staged 10^3 tile (block + 1-cell halo).  Rows along x are RS
 // elements apart: for float32 a warp reading 4 rows x 8 cells then hits 32 distinct banks
 // (RS = 24 = 8 mod 16); float64 kernels are bound by the float64 pipe, not by shared memory,
@@ -297,6 +302,7 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
     __shared__ TC red[32];
     __shared__ int snb[27];
     const int b = blockIdx.x;
+    if (skip_block(g, b)) return;
     if (g.covered && g.covered[b]) {
         if (partials && threadIdx.x < 3) partials[b * 3 + threadIdx.x] = 0.0;
         return;
@@ -405,6 +411,7 @@ __global__ void __launch_bounds__(256) k_smooth(GridDev g, const T *__restrict__
     __shared__ __align__(16) T tE[G::CS];
     __shared__ int snb[27];
     const int b = blockIdx.x;
+    if (skip_block(g, b)) return;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
@@ -506,6 +513,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     T *tE = tB + 3 * G::CS;
     __shared__ int snb[27];
     const int b = blockIdx.x;
+    if (skip_block(g, b)) return;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
     stage_rows<T, 3, 2, G::RRS, G::OFF>(tB, e_in, snb, nullptr);
@@ -605,6 +613,7 @@ __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict_
     __shared__ __align__(16) T tE[G::CS];
     __shared__ int snb[27];
     const int b = blockIdx.x;
+    if (skip_block(g, b)) return;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
@@ -658,6 +667,7 @@ __global__ void __launch_bounds__(512) k_resid_restrict(GridDev g, const T *__re
     T *tt = phi + G::PHI;
     __shared__ int snb[27];
     const int b = blockIdx.x;
+    if (skip_block(g, b)) return;
     const int slot = g.gslot ? g.gslot[b] : -1;
     stage_nbr(snb, g.nbr, b);
     __syncthreads();
@@ -768,6 +778,7 @@ __global__ void __launch_bounds__(512) k_prolong_add(GridDev g, GridDev gc, cons
                                                      int *__restrict__ err) {
     __shared__ T win[3 * 216];
     const int b = blockIdx.x;
+    if (skip_block(g, b)) return;
     const int o = lex ? 0 : g.octant[b];
     const int pb = lex ? 0 : g.parent[b];
     for (int q = threadIdx.x; q < 216; q += blockDim.x) {
@@ -833,6 +844,7 @@ __global__ void __launch_bounds__(512) k_ghost_fill(GridDev g, GridDev gc, const
     __shared__ double win[3 * 512];
     const int sl = blockIdx.x;
     const int b = g.slot_block[sl];
+    if (skip_block(g, b)) return;
     const int pb = g.parent[b], o = g.octant[b];
     const int ox = 4 * (o & 1), oy = 4 * ((o >> 1) & 1), oz = 4 * (o >> 2);
     for (int q = threadIdx.x; q < 512; q += blockDim.x) {
@@ -896,7 +908,7 @@ template cudaError_t launch_ghost_fill<float, float>(const GridDev &, const Grid
 template <typename T>
 __global__ void __launch_bounds__(512) k_sync_down(GridDev gc, T *__restrict__ Bc, const T *__restrict__ Bf) {
     const int b = blockIdx.x;
-    if (!gc.covered[b]) return;
+    if (!gc.covered[b] || skip_block(gc, b)) return;
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
     const int oc = (i >> 2) | ((j >> 2) << 1) | ((k >> 2) << 2);
     const int ch = gc.child[b * 8 + oc];
@@ -1277,6 +1289,7 @@ __device__ __forceinline__ SmallDev<T> small_instance(const SmallDev<T> &in) {
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm_all, double lamdt, int nu1, int nu2, int nc) {
+    if (sm_all.imask && !sm_all.imask[blockIdx.x]) return;
     const SmallDev<T> sm = small_instance(sm_all);
     // e on the first small grid starts from zero
     {

@@ -1,0 +1,158 @@
+"""Regression suites of the paper's Sec. 3 experiments run through the CUDA path (FP64 and
+mixed precision), theta = 1/2 (Crank-Nicolson) and theta = 1 (backward Euler):
+
+* Sec. 3.1, Fig. 2: temporal order 2 (CN) and 1 (BE) on the half-refined sinusoid grid;
+* Sec. 3.1, Fig. 3: amplitude 0.45 at t = 4e-3, coarse-half error above fine-half error;
+* Sec. 3.1, Fig. 5: spatial order 2 for both theta with dt = 4e-3 (4/N)^2;
+* Sec. 3.2, Figs. 7-9: Gaussian diffusion on three levels against the exact solution;
+* Sec. 3.3, Figs. 10-11: implicit steps of dt = 0.1 agree with the explicit solution (computed
+  by the oracle's explicit predictor-corrector), and the gap closes at second order.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1009_0798_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+@pytest.fixture(scope="module")
+def ohm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_0798_gb300 import build, ohm as mod
+    build.build()
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def run(ohm, hier, eta, B0, lam, dt, steps, precision=0, tol=1e-12):
+    g = ohm.ohm_create_hierarchy(hier.base_cells, hier.dx0, hier.blocks, lam=lam, precision=precision,
+                                 nu_pre=4, nu_post=4, n_coarse=16, max_outer=200)
+    ohm.ohm_set_eta(g, dev(eta))
+    B = dev(B0)
+    ohm.ohm_op_sync_down(g, B)
+    for _ in range(steps):
+        st = ohm.ohm_cn_step(g, B, None, dt, tol)
+        assert st["converged"], st
+    torch.cuda.synchronize()
+    out = B.cpu().numpy().reshape(B0.shape)
+    g.close()
+    return out
+
+
+def sinusoid_exact(h, t):
+    k = 2 * np.pi * np.array([1.0, 2.0, 0.0])
+    a = math.exp(-float(k @ k) * t)
+    return W.sample_blocks(h, lambda x, y, z: (0 * x, 0 * x, a * np.sin(k[0] * x + k[1] * y)), 3)
+
+
+def leaf_l1(h, B, ref):
+    """Volume-weighted L1 norm of B_z - ref_z over leaf cells (Sec. 3.1)."""
+    leaf = h.is_leaf()
+    lev = h.blocks[:, 0]
+    vol = np.array([h.dx(l) ** 3 for l in lev])
+    d = np.abs(B[:, 2] - ref[:, 2]).reshape(len(lev), -1).sum(axis=1) * vol
+    return float(d[leaf].sum() / (vol[leaf].sum() * 512))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_e1_temporal_orders(ohm, precision):
+    t_end = 2e-3
+    orders = {}
+    for lam in (0.5, 1.0):
+        sols = {}
+        for dt in (4e-4, 2e-4, 5e-5):
+            wl = W.sinusoid_half_refined(N=8, lam=lam, dt=dt, t_end=t_end)
+            sols[dt] = run(ohm, wl.hier, wl.eta, wl.B, lam, dt, wl.steps, precision, 1e-12 if precision == 0 else 1e-11)
+        e1 = np.abs(sols[4e-4] - sols[5e-5]).max()
+        e2 = np.abs(sols[2e-4] - sols[5e-5]).max()
+        orders[lam] = math.log2(e1 / e2)
+    assert orders[0.5] == pytest.approx(GOLD["cn_temporal_order"]["value"], abs=0.25)
+    assert orders[1.0] == pytest.approx(GOLD["be_temporal_order"]["value"], abs=0.25)
+
+
+def test_e1_amplitude_and_coarse_fine_errors(ohm):
+    dt = 2e-4
+    wl = W.sinusoid_half_refined(N=8, lam=0.5, dt=dt, t_end=4e-3)
+    B = run(ohm, wl.hier, wl.eta, wl.B, 0.5, dt, wl.steps)
+    exact = sinusoid_exact(wl.hier, 4e-3)
+    leaf = wl.hier.is_leaf()
+    lev = wl.hier.blocks[:, 0]
+    err_f = np.abs(B - exact)[leaf & (lev == 1)][:, 2].mean()
+    err_c = np.abs(B - exact)[leaf & (lev == 0)][:, 2].mean()
+    assert np.abs(B[leaf][:, 2]).max() == pytest.approx(GOLD["sinusoid_amplitude_t4e-3"]["value"], abs=0.02)
+    assert err_c > 1.5 * err_f
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0])
+def test_e4_spatial_order(ohm, lam):
+    errs = []
+    for N in (8, 16, 32):
+        dt = 4e-3 * (4.0 / N) ** 2
+        wl = W.sinusoid_half_refined(N=N, lam=lam, dt=dt, t_end=4e-3)
+        B = run(ohm, wl.hier, wl.eta, wl.B, lam, dt, wl.steps)
+        errs.append(leaf_l1(wl.hier, B, sinusoid_exact(wl.hier, 4e-3)))
+    o1, o2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+    assert o2 == pytest.approx(GOLD["spatial_order"]["value"], abs=0.3), (errs, o1, o2)
+
+
+def gaussian_hierarchy():
+    """[-16, 16]^3, base 32^3 (dx = 1), refined where |x|, |y| < 8 (dx = 0.5) and < 4 (dx = 0.25)."""
+    def box(r):
+        return lambda lo, hi: max(abs(lo[0]), abs(hi[0])) <= r + 1e-9 and max(abs(lo[1]), abs(hi[1])) <= r + 1e-9
+    return W.refined(32, 32, 32, 1.0, [box(8.0), box(4.0)], origin=(-16.0, -16.0, -16.0))
+
+
+def gaussian_bz(h, t, t0=1.0, eta=1.0):
+    s = 4.0 * eta * (t + t0)
+    return W.sample_blocks(h, lambda x, y, z: (0 * x, 0 * x, np.exp(-(x * x + y * y) / s) / (math.pi * s)), 3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_e6_gaussian_diffusion_three_levels(ohm, precision):
+    h = gaussian_hierarchy()
+    assert h.nlevels == 3
+    eta = np.ones((h.nblocks, 1, 8, 8, 8))
+    B0 = gaussian_bz(h, 0.0)
+    exact = gaussian_bz(h, 4.0)
+    peak = np.abs(exact[:, 2]).max()
+    errs = {}
+    for dt in (2.0, 1.0, 0.5):
+        B = run(ohm, h, eta, B0, 0.5, dt, int(round(4.0 / dt)), precision, 1e-12 if precision == 0 else 1e-11)
+        errs[dt] = np.abs(B - exact)[h.is_leaf()][:, 2].max() / peak
+    # CN: second order in dt while the temporal error dominates (dt = 2 -> 1), still converging
+    # at dt = 0.5 where the spatial error (dx = 1 on the outer level) starts to show
+    assert errs[0.5] < errs[1.0] < errs[2.0], errs
+    assert math.log2(errs[2.0] / errs[1.0]) > 1.5, errs
+    assert errs[1.0] / errs[0.5] > 1.5, errs
+    assert errs[0.5] < 5e-3, errs
+
+
+def test_e7_implicit_agrees_with_explicit(ohm, oracle_mod):
+    n, L = 64, 8.0
+    dx = L / n
+    h = W.uniform(n, n, n, dx, origin=(-4.0, -4.0, -4.0))
+    eta = W.sample_blocks(h, lambda x, y, z: (np.exp(-(x * x + y * y + z * z)),), 1)
+    B0 = W.sample_blocks(h, lambda x, y, z: (0 * x, 0 * x, np.exp(-(x * x + y * y))), 3)
+    o = oracle_mod.Oracle(h, 0.5, eta)
+    Be = B0.copy()
+    for _ in range(500):  # explicit predictor-corrector, dt = 2e-3 (the limit is 2.6e-3), t = 1
+        Be = o.heun_step(Be, 2e-3)
+    gaps = {}
+    for dt, prec in ((0.1, 0), (0.05, 0), (0.1, 1)):
+        B = run(ohm, h, eta, B0, 0.5, dt, int(round(1.0 / dt)), prec, 1e-12 if prec == 0 else 1e-11)
+        gaps[(dt, prec)] = np.abs(B - Be).max() / np.abs(B0).max()
+    assert gaps[(0.1, 0)] < 5e-3
+    assert gaps[(0.1, 0)] / gaps[(0.05, 0)] == pytest.approx(4.0, rel=0.3)
+    assert gaps[(0.1, 1)] == pytest.approx(gaps[(0.1, 0)], rel=1e-3)
