@@ -797,7 +797,7 @@ int fill_ghosts_B(ohm_hier *H, const double *B) {
 // fine fluxes are in the registers before the coarser level reads them), computed in TC.
 template <typename TC, typename TO>
 int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta, double a, double c,
-                double dcoef, TO *out, TO *out2, bool norms) {
+                double dcoef, TO *out, TO *out2, bool norms, double *outS = nullptr, double c2 = 0.0) {
     for (int l = H->nlev - 1; l >= 0; l--) {
         const HGrid &g = H->amr[l];
         double vol = g.h * g.h * g.h;
@@ -805,7 +805,8 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
         LAUNCH(H, OHM_K_COMPOSITE, g.n(),
                (launch_composite<TC, TO>(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta, a, c,
                                          dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
-                                         norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s)));
+                                         norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s,
+                                         outS ? outS + o3 : nullptr, c2)));
     }
     if (norms) {
         if (H->batched)
@@ -821,6 +822,15 @@ template <typename TO>
 int composite(ohm_hier *H, const double *X, const double *Y, double a, double c, double dcoef, TO *out, bool norms,
               TO *out2 = nullptr) {
     return composite_t<double, TO>(H, X, Y, H->eta64, H->ghostB, H->ghostEta64, a, c, dcoef, out, out2, norms);
+}
+
+// The first residual of a step and its source from one flux divergence of b (Eqs. 14, 20):
+// S = b - (1 - lambda) dt divF(b) into H->S, and R = S - L b = -dt divF(b) into out (and out2),
+// with the norms of R against S.
+template <typename TO>
+int source_and_residual(ohm_hier *H, const double *b, double lam, double dt, TO *out, TO *out2) {
+    return composite_t<double, TO>(H, b, nullptr, H->eta64, H->ghostB, H->ghostEta64, 1.0, -(1.0 - lam) * dt, 0.0, out,
+                                   out2, true, H->S, -dt);
 }
 
 template <typename T>
@@ -869,14 +879,16 @@ int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *
     CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->s));
     if ((st = sync_down(H, B))) return st;
     if ((st = fill_ghosts_B(H, B))) return st;
-    if ((st = composite<double>(H, B, nullptr, 1.0, -(1.0 - lam) * dt, 0.0, H->S, false))) return st;
     H->has_S = true;
     H->last_dt = dt;
     int it = 0;
     double nr[4] = {0, 0, 0, 0}, first = 0;
     int result = OHM_OK;
     for (;;) {
-        if ((st = composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, (T *)H->amrbuf.r, true))) return st;
+        // the first residual comes with the source S from one flux divergence of b
+        if ((st = it == 0 ? source_and_residual<T>(H, B, lam, dt, (T *)H->amrbuf.r, (T *)nullptr)
+                          : composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, (T *)H->amrbuf.r, true)))
+            return st;
         int ef = 0;
         if ((st = read_norms(H, nr, &ef))) return st;
         if (ef) return OHM_ERR_INVALID;
@@ -1052,7 +1064,6 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
     CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->s));
     if ((st = sync_down(H, B))) return st;
     if ((st = fill_ghosts_B(H, B))) return st;
-    if ((st = composite<double>(H, B, nullptr, 1.0, -(1.0 - lam) * dt, 0.0, H->S, false))) return st;
     H->has_S = true;
     H->last_dt = dt;
     T *r = (T *)H->amrbuf.r, *e = (T *)H->amrbuf.e, *rout = (T *)H->rout, *eacc = (T *)H->eacc;
@@ -1060,7 +1071,9 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
     int cycles = 0, result = OHM_OK;
     double nr[4] = {0, 0, 0, 0}, first = 0;
     for (int outer = 0;; outer++) {
-        if ((st = composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, rout))) return st;
+        if ((st = outer == 0 ? source_and_residual<T>(H, B, lam, dt, r, rout)
+                             : composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, rout)))
+            return st;
         int ef = 0;
         if ((st = read_norms(H, nr, &ef))) return st;
         if (ef) return OHM_ERR_INVALID;
@@ -1205,7 +1218,6 @@ int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const 
     CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->s));
     if ((st = sync_down(H, B))) return st;
     if ((st = fill_ghosts_B(H, B))) return st;
-    if ((st = composite<double>(H, B, nullptr, 1.0, -(1.0 - lam), 0.0, H->S, false))) return st;
     H->has_S = true;
     H->last_dt = 1.0;
     enum { RUN = 0, DONE = 1, NOCONV = 2, NONFIN = 3, IDLE = 4 };
@@ -1219,7 +1231,10 @@ int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const 
     const size_t nbytes = (size_t)H->nblocks * 3 * B3 * sizeof(T);
     const double fl = inner_floor(H);
     for (int outer = 0;; outer++) {
-        if ((st = composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, H->mixed ? rout : (T *)nullptr))) return st;
+        T *r2 = H->mixed ? rout : (T *)nullptr;
+        if ((st = outer == 0 ? source_and_residual<T>(H, B, lam, 1.0, r, r2)
+                             : composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, r2)))
+            return st;
         if ((st = enqueue_norm_copy(H))) return st;
         int ef = 0;
         if ((st = read_norms_batch(H, rel, mx, &ef))) return st;

@@ -58,11 +58,14 @@ struct SmallDev {
 // registers for faces without a same-level neighbour and reads refluxed fluxes from the
 // finer level for faces next to covered blocks; optional per-block norm partials.
 // Computed in TC; out (and out2 when not null) receive the result as TO.
+// With outS (first residual of a step, Eqs. 14 and 20 from one flux divergence of X = b):
+// outS = a X + c divF(X) (the source S) and out = out2 = c2 divF(X) = S - L X for c2 = -dt;
+// the norm partials are then those of out against S.
 template <typename TC, typename TO>
 cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const TC *eta, const TC *Gx,
                              const TC *Geta, double a, double c, double d, TO *out, TO *out2,
                              double *reg, const int *rsrc_tab, double *partials, double vol,
-                             cudaStream_t s);
+                             cudaStream_t s, double *outS = nullptr, double c2 = 0.0);
 
 template <typename T>
 cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta,

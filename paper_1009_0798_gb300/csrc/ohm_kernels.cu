@@ -82,11 +82,15 @@ __device__ __forceinline__ Row8<double> load_row8(const double *__restrict__ p) 
 // from `ghost` ([NC][10^3] compact, HW = 1 only) or are zero.  Values at the corners of the
 // box are never read by the stencil and may be left stale.
 template <typename T>
-__device__ __forceinline__ void store_row8(T *dst, const Row8<T> &row, bool aligned16) {
+__device__ __forceinline__ void store_row8(T *dst, const Row8<T> &row, bool aligned16, bool aligned8 = false) {
     if (sizeof(T) == 4 && aligned16) {
         float4 *d4 = reinterpret_cast<float4 *>(dst);
         d4[0] = make_float4((float)row.v[0], (float)row.v[1], (float)row.v[2], (float)row.v[3]);
         d4[1] = make_float4((float)row.v[4], (float)row.v[5], (float)row.v[6], (float)row.v[7]);
+    } else if (sizeof(T) == 4 && aligned8) {
+        float2 *d2 = reinterpret_cast<float2 *>(dst);
+#pragma unroll
+        for (int q = 0; q < 4; q++) d2[q] = make_float2((float)row.v[2 * q], (float)row.v[2 * q + 1]);
     } else {
 #pragma unroll
         for (int q = 0; q < 8; q++) dst[q] = row.v[q];
@@ -98,6 +102,7 @@ __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__rest
                                            const T *__restrict__ ghost) {
     constexpr int S = 8 + 2 * HW, S2 = S * S;
     constexpr bool A16 = sizeof(T) == 4 && (OFF + HW) % 4 == 0 && RS % 4 == 0;
+    constexpr bool A8 = sizeof(T) == 4 && (OFF + HW) % 2 == 0 && RS % 2 == 0;
     for (int task = threadIdx.x; task < NC * S2; task += blockDim.x) {
         const int c = task / S2, rr = task - c * S2;
         const int tj = rr % S, tk = rr / S;
@@ -110,12 +115,22 @@ __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__rest
         const int src = snb[dcent + 1];
         if (src >= 0) {
             const Row8<T> row = load_row8(F + ((size_t)src * NC + c) * B3 + (sk * 8 + sj) * 8);
-            store_row8(dst + HW, row, A16);
+            store_row8(dst + HW, row, A16, A8);
         } else {
 #pragma unroll
             for (int q = 0; q < 8; q++) dst[HW + q] = gh ? gh[HW + q] : T(0);
         }
         const int slo = snb[dcent], shi = snb[dcent + 2];
+        if constexpr (sizeof(T) == 4 && HW == 2 && OFF % 2 == 0 && RS % 2 == 0) {
+          if (slo >= 0 && shi >= 0) {
+            // two-cell halos as 8-byte words (cells 6,7 of the x- neighbour, 0,1 of the x+ one)
+            const float2 lo = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)slo * NC + c) * B3 + (sk * 8 + sj) * 8 + 6));
+            const float2 hi = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)shi * NC + c) * B3 + (sk * 8 + sj) * 8));
+            *reinterpret_cast<float2 *>(dst) = lo;
+            *reinterpret_cast<float2 *>(dst + HW + 8) = hi;
+            continue;
+          }
+        }
 #pragma unroll
         for (int h = 0; h < HW; h++) {
             // low end: cells 8-HW+h of the x- neighbour; high end: cells h of the x+ neighbour
@@ -293,7 +308,8 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
                                                    const TC *__restrict__ Geta, TC a, TC coef, TC d,
                                                    TO *__restrict__ out, TO *__restrict__ out2,
                                                    double *__restrict__ reg, const int *__restrict__ rsrc_tab,
-                                                   double *__restrict__ partials, double vol) {
+                                                   double *__restrict__ partials, double vol,
+                                                   double *__restrict__ outS, TC coef2) {
     using G = Geo<TC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC *tB = reinterpret_cast<TC *>(smem_raw);
@@ -355,6 +371,11 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
         size_t id = ((size_t)b * 3 + c) * B3 + t;
         TC y = Y ? Y[id] : TC(0);
         TC o = a * tB[c * G::CS + p] + coef * dv[c] + d * y;
+        if (outS) {  // o is the source; the residual of X against it is coef2 divF(X)
+            outS[id] = (double)o;
+            y = o;
+            o = coef2 * dv[c];
+        }
         out[id] = (TO)o;
         if (out2) out2[id] = (TO)o;
         if (partials) {
@@ -378,7 +399,7 @@ __global__ void __launch_bounds__(512) k_composite(GridDev g, const TC *__restri
 template <typename TC, typename TO>
 cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta,
                              double a, double c, double d, TO *out, TO *out2, double *reg, const int *rsrc_tab,
-                             double *partials, double vol, cudaStream_t s) {
+                             double *partials, double vol, cudaStream_t s, double *outS, double c2) {
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = (4 * Geo<TC>::CS + Geo<TC>::PHI) * sizeof(TC);
     // set once per process (thread-safe static initialisation)
@@ -386,13 +407,13 @@ cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const T
     (void)attr;
     double coef = c / (2.0 * g.h * g.h);
     k_composite<TC, TO><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg, rsrc_tab,
-                                                partials, vol);
+                                                partials, vol, outS, (TC)(c2 / (2.0 * g.h * g.h)));
     return cudaGetLastError();
 }
 #define INST_COMPOSITE(TC, TO)                                                                                        \
     template cudaError_t launch_composite<TC, TO>(const GridDev &, const TC *, const TC *, const TC *, const TC *,     \
                                                   const TC *, double, double, double, TO *, TO *, double *, const int *, \
-                                                  double *, double, cudaStream_t);
+                                                  double *, double, cudaStream_t, double *, double);
 INST_COMPOSITE(double, double)
 INST_COMPOSITE(double, float)
 INST_COMPOSITE(float, float)
@@ -467,11 +488,15 @@ template cudaError_t launch_smooth<float>(const GridDev &, const float *, float 
 // the ones the neighbouring blocks compute, in the same order with the same arithmetic, so
 // the result equals two global colour passes.  The inverse diagonal is formed on the fly
 // from eta (Eqs. 21-23).  e_in and e_out are distinct buffers.
-// Rows of the 12^3 tile are RRS elements apart: for float32, 8 rows of 4 same-colour cells
-// (stride 2, the black-phase warp pattern) then fall on 32 distinct banks.
+// The 12^3 tile is compact (rows 12 elements apart): 8 rows of 4 same-colour cells (stride 2,
+// the warp pattern of the block's cells) still fall on 32 distinct float32 banks, and the
+// tile (4 x 6.75 KB for float32) leaves room for 6 thread blocks per SM.  The sweep is bound by
+// latency more than by shared-memory bandwidth: a padded tile (rows 20 apart, fewer bank
+// conflicts on the ring) measured slower at 256^3 (0.46 ms against 0.43 ms per sweep) because
+// it allows only 4 thread blocks per SM.
 template <typename T>
 struct G12 {
-    static constexpr int S = 12, RRS = sizeof(T) == 4 ? 20 : 12, PS = S * RRS, CS = S * PS, OFF = sizeof(T) == 4 ? 2 : 0;
+    static constexpr int S = 12, RRS = 12, PS = S * RRS, CS = S * PS, OFF = 0;
     __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
 };
 // smoother division: the hardware reciprocal in float32 (a smoothing weight needs no
