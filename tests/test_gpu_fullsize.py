@@ -65,3 +65,53 @@ def test_mixed_fgmres_converged_residual_checked_by_oracle(ohm, case):
     _, norms = o.residual(got, S, wl.dt)
     assert norms["rel_l2"] <= 1.05 * wl.tol
     assert norms["rel_l2"] == pytest.approx(st["rel_l2"], rel=0.05)
+
+
+# ------------------------------------------------------------------ batched 512 instances
+@pytest.fixture(scope="module")
+def batch512():
+    return W.batched_instances(512, seed=4)
+
+
+def test_batched512_every_instance_converges_and_samples_pass_oracle(ohm, batch512, oracle_mod):
+    """The 512-instance workload as bench.py runs it (one mixed-precision batch per edge length,
+    CUDA graphs, V(4,4) with 4 coarsest sweeps): every instance converges, and for two
+    instances per class the oracle re-evaluates the residual of the GPU's answer."""
+    groups = {}
+    for i in batch512:
+        groups.setdefault(i.n, []).append(i)
+    for n, lst in sorted(groups.items()):
+        h = lst[0].hier
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            g = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_MIXED, nu_pre=4,
+                                         nu_post=4, n_coarse=4, max_outer=400, stream=s, n_instances=len(lst),
+                                         use_graphs=True)
+            ohm.ohm_set_eta(g, dev(np.concatenate([i.eta for i in lst])))
+            B = dev(np.concatenate([i.B for i in lst]))
+            status, st = ohm.ohm_cn_step_batch(g, B, [i.dt for i in lst], 1e-9)
+        s.synchronize()
+        assert status == ohm.OHM_OK and all(x["converged"] and x["rel_l2"] <= 1e-9 for x in st), n
+        got = B.cpu().numpy().reshape(len(lst), h.nblocks, 3, 8, 8, 8)
+        for q in (0, len(lst) - 1):
+            o = oracle_mod.Oracle(h, 0.5, lst[q].eta)
+            S = o.source(lst[q].B, lst[q].dt)
+            _, norms = o.residual(got[q], S, lst[q].dt)
+            assert norms["rel_l2"] <= 1.05e-9, (n, q, norms)
+            assert norms["rel_l2"] == pytest.approx(st[q]["rel_l2"], rel=0.05)
+
+
+def test_batched_fp64_fixed_schedule_elementwise_sampled(ohm, batch512, oracle_mod):
+    """FP64 batch of the 24^3 class (lexicographic coarsest grid per instance), 3 V-cycles:
+    sampled instances equal the oracle element by element."""
+    lst = [i for i in batch512 if i.n == 24]
+    h = lst[0].hier
+    g = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, nu_pre=2, nu_post=2, n_coarse=16,
+                                 max_outer=3, n_instances=len(lst))
+    ohm.ohm_set_eta(g, dev(np.concatenate([i.eta for i in lst])))
+    B = dev(np.concatenate([i.B for i in lst]))
+    ohm.ohm_cn_step_batch(g, B, [i.dt for i in lst], -1.0)
+    got = B.cpu().numpy().reshape(len(lst), h.nblocks, 3, 8, 8, 8)
+    for q in (0, len(lst) // 2, len(lst) - 1):
+        want, _ = oracle_mod.Oracle(h, 0.5, lst[q].eta).cn_step(lst[q].B, lst[q].dt, -1.0, 2, 2, 16, 3)
+        assert rel_err(got[q], want) < 1e-12, q

@@ -115,3 +115,25 @@ def test_oversized_request_is_rejected(srv):
         _, b, e, dt = request(h, 600, 0)
         with pytest.raises(ohm.OhmError):
             s.submit(h, b, e, dt, 1)
+
+
+@pytest.mark.slow
+def test_serving_sizes_converge_and_pass_oracle(srv, oracle_mod):
+    """Requests of the serving workload's largest uniform class (128^3) and its AMR class (base
+    32^3, sphere r < 0.2 refined), with the service configuration bench.py times: each converges
+    and the oracle re-evaluates its residual."""
+    import bench
+    reqs = bench.serving_requests(40, 200.0)
+    pick = [next(r for r in reqs if r["key"] == 128), next(r for r in reqs if r["key"] == "amr")]
+    cfg = dict(hbm_budget_bytes=60 << 30, max_batch=8, n_workers=2, precision=1, tol=1e-9, use_graphs=True,
+               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400)
+    with srv.Server(**cfg) as s:
+        ids = [s.submit(r["hier"], r["B"] * r["fb"], r["eta"] * r["fe"], r["dt"], 1) for r in pick]
+        outs = [s.wait(i) for i in ids]
+    for r, (out, res) in zip(pick, outs):
+        assert res["status"] == 0 and res["rel_l2"] <= 1e-9
+        o = oracle_mod.Oracle(r["hier"], 0.5, r["eta"] * r["fe"])
+        b = o.sync_down(r["B"] * r["fb"])
+        S = o.source(b, r["dt"])
+        _, norms = o.residual(out.reshape(b.shape), S, r["dt"])
+        assert norms["rel_l2"] <= 1.05e-9, norms
