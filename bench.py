@@ -53,6 +53,8 @@ def args_parse():
                         "the continuous-batching service")
     p.add_argument("--instances", type=int, default=512, help="batched512: number of instances")
     p.add_argument("--no-autotune", action="store_true", help="batched512: keep the default schedule")
+    p.add_argument("--batch-krylov", type=int, default=6,
+                   help="batched512 / serving: FGMRES restart length of each instance's inner solve (0: defect correction)")
     p.add_argument("--requests", type=int, default=600, help="serving: requests in the stream")
     p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     p.add_argument("--inner-tol", type=float, default=1e-5,
@@ -479,7 +481,8 @@ def run_batched(args):
             c["B"] = torch.empty_like(c["B0"])
             c["g"] = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_MIXED,
                                               nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse, max_outer=400,
-                                              stream=s, n_instances=len(lst), use_graphs=True)
+                                              stream=s, n_instances=len(lst), use_graphs=True,
+                                              krylov=args.batch_krylov)
             ohm.ohm_set_eta(c["g"], c["eta"])
         C.append(c)
     torch.cuda.synchronize()
@@ -648,7 +651,9 @@ def run_batched(args):
             "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
             "config": {"workload": f"batched_{len(inst)}", "cells": cells,
                        "classes": {str(c["n"]): c["K"] for c in C}, "tol": tol,
-                       "multigrid": "per-instance float64 iterative refinement, float32 defect-correction V-cycles",
+                       "multigrid": "per-instance float64 iterative refinement, float32 inner solve: " +
+                                    (f"per-instance FGMRES({args.batch_krylov}) right-preconditioned by the V-cycle"
+                                     if args.batch_krylov else "defect-correction V-cycles"),
                        "autotuned": {str(k): v for k, v in tuned.items()}, "graphs": True,
                        "parallelism": f"replicas x{ws}; 5 size classes on 5 streams",
                        "l2": "working set 3 GB (> 129 MB L2), no flush"},
@@ -736,7 +741,7 @@ def run_serving(args):
     # V(4,4) with 4 coarsest sweeps: the schedule the autotuner picks for every class of the
     # batched workload (defect-correction inner solves)
     cfg = dict(hbm_budget_bytes=budget, max_batch=8, n_workers=6, precision=1, tol=1e-9, use_graphs=True,
-               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400)
+               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400, krylov=args.batch_krylov)
     # warm-up service: one request per class (kernels loaded, batches of each class built once)
     with server.Server(**cfg) as s:
         seen = {}

@@ -72,8 +72,8 @@ typedef struct {
                                    ohm_cn_step_batch; every kernel launch covers all K.  Field
                                    arrays then hold, level by level, the K instances' blocks
                                    of that level one instance after another (for one-level
-                                   hierarchies: instance after instance).  Batches need
-                                   krylov = 0.                                                  */
+                                   hierarchies: instance after instance).  With krylov = m
+                                   each instance runs its own FGMRES(m) recurrence.             */
     int32_t use_graphs;         /* batches only: 1 = the inner iteration (V-cycle, update and
                                    residual) is captured once into a CUDA graph and replayed.
                                    Needs a non-NULL stream; ignored otherwise.                  */

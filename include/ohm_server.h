@@ -43,6 +43,8 @@ typedef struct {
     double lambda;              /* theta parameter (0, 1]                                      */
     double tol;                 /* relative residual of every step (>= 0)                      */
     int32_t use_graphs;         /* 1: batches replay their inner iteration as a CUDA graph     */
+    int32_t krylov;             /* OHM_MIXED: 0 = defect-correction inner solves, m in 1..11 =
+                                   per-instance FGMRES(m) (see ohm_hier_desc)                  */
 } ohm_server_desc;
 
 typedef struct {

@@ -88,6 +88,11 @@ struct ohm_hier {
     // per-block inner-product weights, multi-dot scratch and results (device and pinned host)
     float *kv[KMAX + 1] = {}, *kz[KMAX] = {};
     double *wblk = nullptr, *kpart = nullptr, *kdots = nullptr, *hdots = nullptr;
+    // batched FGMRES: per-instance products (pinned copy), coefficients (device, pinned) and the
+    // instance of every block
+    double *hdotsK = nullptr;
+    float *kcoef = nullptr, *hcoef = nullptr;
+    int *binst = nullptr;
     std::vector<double> wblk_host;
     Buffers amrbuf;               // AMR levels, all blocks
     std::vector<Buffers> mgbuf;   // blocked multigrid grids
@@ -466,8 +471,15 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
             for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * sizeof(float));
             for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
             want((void **)&H->wblk, n * sizeof(double));
-            want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
-            want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
+            if (H->batched) {
+                want((void **)&H->kpart, n * (KMAX + 1) * sizeof(double));
+                want((void **)&H->kdots, (size_t)H->K * (KMAX + 1) * sizeof(double));
+                want((void **)&H->kcoef, (size_t)H->K * (KMAX + 1) * sizeof(float));
+                want((void **)&H->binst, n * sizeof(int));
+            } else {
+                want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
+                want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
+            }
         }
     }
     want(&H->amrbuf.e, n * 3 * B3 * tsz);
@@ -533,6 +545,21 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
             cudaMallocHost((void **)&H->imask_h, (size_t)H->K * 2) != cudaSuccess) {
             err = "pinned allocation failed";
             return OHM_ERR_OOM;
+        }
+        if (H->kcoef) {
+            if (cudaMallocHost((void **)&H->hdotsK, (size_t)H->K * (KMAX + 1) * sizeof(double)) != cudaSuccess ||
+                cudaMallocHost((void **)&H->hcoef, (size_t)H->K * (KMAX + 1) * sizeof(float)) != cudaSuccess) {
+                err = "pinned allocation failed";
+                return OHM_ERR_OOM;
+            }
+            std::vector<int> bi((size_t)H->nblocks, 0);
+            for (int l = 0; l < H->ranges.nlev; l++)
+                for (int q = 0; q < H->K; q++)
+                    for (int b = 0; b < H->ranges.n[l]; b++) bi[(size_t)H->ranges.off[l] + (size_t)q * H->ranges.n[l] + b] = q;
+            if (cudaMemcpy(H->binst, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+                err = "table upload failed";
+                return OHM_ERR_CUDA;
+            }
         }
     }
     if (H->wblk) {  // inner-product weights: h^3 on leaf blocks, 0 on covered ones
@@ -1203,6 +1230,213 @@ int batch_scale(ohm_hier *H, const double *dt) {
     return OHM_OK;
 }
 
+// ---- batched FGMRES: one Arnoldi recurrence per instance, every launch covering the batch
+// Per-instance products <w, v_i> (i < S.k) and <w, w>, read back to the host: out[q][0..k].
+int mdot_inst(ohm_hier *H, const float *w, const VecSet &S, std::vector<double> &out) {
+    LAUNCH(H, OHM_K_NORM, 0,
+           launch_mdot_inst(w, S, H->wblk, (int)H->nblocks, H->ranges, H->K, H->kpart, H->kdots, H->s));
+    CK(cudaMemcpyAsync(H->hdotsK, H->kdots, (size_t)H->K * (KMAX + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    out.assign(H->hdotsK, H->hdotsK + (size_t)H->K * (KMAX + 1));
+    return OHM_OK;
+}
+
+// dst = (src - sum_i c[q][i] v_i) * sc[q] per instance q; c and sc are host arrays
+// ([K][KMAX] and [K]); a zero coefficient skips its vector for that instance.
+int maxpy_inst(ohm_hier *H, float *dst, const float *src, const VecSet &S, const std::vector<float> &c,
+               const std::vector<float> &sc) {
+    const int K = H->K;
+    for (int q = 0; q < K; q++) {
+        for (int i = 0; i < KMAX; i++) H->hcoef[(size_t)q * (KMAX + 1) + i] = i < S.k ? c[(size_t)q * KMAX + i] : 0.f;
+        H->hcoef[(size_t)q * (KMAX + 1) + KMAX] = sc[q];
+    }
+    CK(cudaMemcpyAsync(H->kcoef, H->hcoef, (size_t)K * (KMAX + 1) * sizeof(float), cudaMemcpyHostToDevice, H->s));
+    LAUNCH(H, OHM_K_UPDATE, 0, launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s));
+    // the pinned coefficients are rewritten by the next call: wait for this copy
+    CK(cudaStreamSynchronize(H->s));
+    return OHM_OK;
+}
+
+// compute mask of the batched iteration kernels from a host flag array (uploaded)
+int set_cmask(ohm_hier *H, const uint8_t *flags) {
+    uint8_t *dm = H->imask_d + H->K;  // the inner mask slot
+    memcpy(H->imask_h + H->K, flags, H->K);
+    CK(cudaMemcpyAsync(dm, H->imask_h + H->K, H->K, cudaMemcpyHostToDevice, H->s));
+    CK(cudaStreamSynchronize(H->s));  // the pinned flags are rewritten by the next call
+    H->cmask = dm;
+    H->active_frac = (double)std::count(flags, flags + H->K, 1) / H->K;
+    return OHM_OK;
+}
+
+// Float32 inner solve of L x = rout for every instance q with run[q], by FGMRES(m) right-
+// preconditioned by one V-cycle, as inner_fgmres does for one problem: each instance has its
+// own Arnoldi basis coefficients, Hessenberg matrix, Givens rotations, restarts and stopping
+// test (target[q], stagnation, V-cycle budget), so its iterates do not depend on the others;
+// the V-cycles, operator applications and vector kernels of all running instances share
+// launches, and instances that stopped are skipped by the compute mask.  x is left in eacc.
+int inner_fgmres_batch(ohm_hier *H, double lamdt, const std::vector<double> &target, const uint8_t *run,
+                       std::vector<int> &cycles) {
+    const int K = H->K, m = H->d.krylov;
+    const size_t nel = (size_t)H->nblocks * 3 * B3;
+    float *x = (float *)H->eacc, *rhs = (float *)H->rout;
+    int st;
+    CK(cudaMemsetAsync(x, 0, nel * sizeof(float), H->s));
+    std::vector<double> nn, beta0(K, 0.0), beta(K, 0.0), brest(K, 0.0);
+    std::vector<double> Hm((size_t)K * (m + 1) * m), cs((size_t)K * m), sn((size_t)K * m), g((size_t)K * (m + 1)), y(m);
+    std::vector<uint8_t> live(K, 0), arn(K, 0), act(K, 0), need2(K, 0);
+    std::vector<int> jend(K, 0);
+    std::vector<float> c((size_t)K * KMAX, 0.f), sc(K, 1.f);
+    std::vector<double> hn(K, 0.0);
+    auto h = [&](int q, int i, int j) -> double & { return Hm[((size_t)q * (m + 1) + i) * m + j]; };
+    VecSet none;
+    none.k = 0;
+    if ((st = mdot_inst(H, rhs, none, nn))) return st;
+    for (int q = 0; q < K; q++) {
+        beta0[q] = beta[q] = brest[q] = std::sqrt(std::max(nn[(size_t)q * (KMAX + 1)], 0.0));
+        live[q] = run[q] && beta0[q] > 0 && std::isfinite(beta0[q]);
+        sc[q] = live[q] ? (float)(1.0 / beta0[q]) : 1.f;
+    }
+    if ((st = maxpy_inst(H, H->kv[0], rhs, none, c, sc))) return st;
+    for (;;) {
+        bool any_live = false;
+        for (int q = 0; q < K; q++) {
+            arn[q] = live[q];
+            any_live |= live[q] != 0;
+            jend[q] = 0;
+            std::fill(g.begin() + (size_t)q * (m + 1), g.begin() + (size_t)(q + 1) * (m + 1), 0.0);
+            g[(size_t)q * (m + 1)] = beta[q];
+        }
+        if (!any_live) break;
+        for (int j = 0; j < m; j++) {
+            bool any = false;
+            for (int q = 0; q < K; q++) {
+                act[q] = arn[q] && cycles[q] < H->d.max_outer;
+                any |= act[q] != 0;
+            }
+            if (!any) break;
+            // z_j = V-cycle applied to v_j, w = L z_j, for the active instances
+            if ((st = set_cmask(H, act.data()))) return st;
+            void *r_save = H->amrbuf.r, *e_save = H->amrbuf.e;
+            H->amrbuf.r = H->kv[j];
+            H->amrbuf.e = H->kz[j];
+            st = vcycle<float>(H, lamdt);
+            H->amrbuf.r = r_save;
+            H->amrbuf.e = e_save;
+            if (!st) st = apply_L32(H, H->kz[j], nullptr, 1.0, lamdt, 0.0, H->kv[j + 1], lamdt);
+            H->cmask = nullptr;
+            if (st) return st;
+            for (int q = 0; q < K; q++) cycles[q] += act[q];
+            VecSet S;
+            S.k = j + 1;
+            for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
+            if ((st = mdot_inst(H, H->kv[j + 1], S, nn))) return st;
+            bool any2 = false;
+            for (int q = 0; q < K; q++) {
+                need2[q] = 0;
+                sc[q] = 1.f;
+                for (int i = 0; i < KMAX; i++) c[(size_t)q * KMAX + i] = 0.f;
+                if (!act[q]) continue;
+                const double *d = &nn[(size_t)q * (KMAX + 1)];
+                double proj = 0.0;
+                for (int i = 0; i <= j; i++) {
+                    h(q, i, j) = d[i];
+                    c[(size_t)q * KMAX + i] = (float)d[i];
+                    proj += d[i] * d[i];
+                }
+                const double ww = d[j + 1];
+                if (ww - proj > 0.01 * ww) {  // orthogonalise and normalise in one pass
+                    hn[q] = std::sqrt(ww - proj);
+                    sc[q] = (float)(1.0 / hn[q]);
+                } else {
+                    need2[q] = 1;
+                    any2 = true;
+                }
+            }
+            if ((st = maxpy_inst(H, H->kv[j + 1], H->kv[j + 1], S, c, sc))) return st;
+            if (any2) {  // the norm measured after orthogonalising, where cancellation was large
+                if ((st = mdot_inst(H, H->kv[j + 1], none, nn))) return st;
+                for (int q = 0; q < K; q++) {
+                    sc[q] = 1.f;
+                    if (!need2[q]) continue;
+                    hn[q] = std::sqrt(std::max(nn[(size_t)q * (KMAX + 1)], 0.0));
+                    if (hn[q] > 0) sc[q] = (float)(1.0 / hn[q]);
+                }
+                std::fill(c.begin(), c.end(), 0.f);
+                if ((st = maxpy_inst(H, H->kv[j + 1], H->kv[j + 1], none, c, sc))) return st;
+            }
+            for (int q = 0; q < K; q++) {
+                if (!act[q]) continue;
+                double *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
+                h(q, j + 1, j) = hn[q];
+                for (int i = 0; i < j; i++) {
+                    const double t = cq[i] * h(q, i, j) + sq[i] * h(q, i + 1, j);
+                    h(q, i + 1, j) = -sq[i] * h(q, i, j) + cq[i] * h(q, i + 1, j);
+                    h(q, i, j) = t;
+                }
+                const double den = std::hypot(h(q, j, j), h(q, j + 1, j));
+                cq[j] = den > 0 ? h(q, j, j) / den : 1.0;
+                sq[j] = den > 0 ? h(q, j + 1, j) / den : 0.0;
+                h(q, j, j) = den;
+                h(q, j + 1, j) = 0.0;
+                gq[j + 1] = -sq[j] * gq[j];
+                gq[j] = cq[j] * gq[j];
+                jend[q] = j + 1;
+                if (std::fabs(gq[j + 1]) <= target[q] * beta0[q] || !(hn[q] > 0)) {
+                    arn[q] = 0;
+                    live[q] = 0;  // converged (or breakdown): no restart
+                }
+            }
+        }
+        // x += sum_i y_i z_i per instance (R y = g)
+        int kmax = 0;
+        std::fill(c.begin(), c.end(), 0.f);
+        std::fill(sc.begin(), sc.end(), 1.f);
+        for (int q = 0; q < K; q++) {
+            const int je = jend[q];
+            kmax = std::max(kmax, je);
+            for (int i = je - 1; i >= 0; i--) {
+                double t = g[(size_t)q * (m + 1) + i];
+                for (int k2 = i + 1; k2 < je; k2++) t -= h(q, i, k2) * y[k2];
+                y[i] = h(q, i, i) != 0 ? t / h(q, i, i) : 0.0;
+            }
+            for (int i = 0; i < je; i++) c[(size_t)q * KMAX + i] = (float)(-y[i]);
+        }
+        if (kmax > 0) {
+            VecSet Z;
+            Z.k = kmax;
+            for (int i = 0; i < kmax; i++) Z.v[i] = H->kz[i];
+            if ((st = maxpy_inst(H, x, x, Z, c, sc))) return st;
+        }
+        // restart from the true residual rhs - L x where an instance is still live
+        bool any_restart = false;
+        for (int q = 0; q < K; q++) {
+            if (live[q] && (cycles[q] >= H->d.max_outer || jend[q] == 0)) live[q] = 0;
+            any_restart |= live[q] != 0;
+        }
+        if (!any_restart) break;
+        if ((st = set_cmask(H, live.data()))) return st;
+        st = apply_L32(H, x, rhs, -1.0, -lamdt, 1.0, H->kv[0], lamdt);
+        H->cmask = nullptr;
+        if (st) return st;
+        if ((st = mdot_inst(H, H->kv[0], none, nn))) return st;
+        std::fill(c.begin(), c.end(), 0.f);
+        for (int q = 0; q < K; q++) {
+            sc[q] = 1.f;
+            if (!live[q]) continue;
+            beta[q] = std::sqrt(std::max(nn[(size_t)q * (KMAX + 1)], 0.0));
+            // stop at the target, on breakdown, or when the restart cycle gained less than 2x
+            if (beta[q] <= target[q] * beta0[q] || !(beta[q] > 0) || beta[q] > 0.5 * brest[q]) {
+                live[q] = 0;
+                continue;
+            }
+            brest[q] = beta[q];
+            sc[q] = (float)(1.0 / beta[q]);
+        }
+        if ((st = maxpy_inst(H, H->kv[0], H->kv[0], none, c, sc))) return st;
+    }
+    return OHM_OK;
+}
+
 // Batched theta step (dt folded into eta per instance, so the operator's lambda dt is lambda):
 // the outer float64 loop of Eqs. 16-18 per instance, with a float32 defect-correction inner
 // solve (mixed) or one float64 V-cycle per outer iteration (FP64).  Instances are stopped and
@@ -1271,6 +1505,12 @@ int cn_step_batch_t(ohm_hier *H, double *B, const double *dt, double tol, const 
                 prev[q] = 1.0;
             }
             bool inner = true;
+            if (H->d.krylov > 0) {  // per-instance FGMRES instead of defect correction
+                if constexpr (std::is_same<T, float>::value) {
+                    if ((st = inner_fgmres_batch(H, lamdt, target, omask_h, cycles))) return st;
+                }
+                inner = false;
+            }
             while (inner) {
                 CK(cudaMemcpyAsync(imask_d, imask_h, K, cudaMemcpyHostToDevice, H->s));
                 H->cmask = imask_d;  // blocks of instances that stopped iterating are skipped
@@ -1341,7 +1581,6 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     }
     if (!(d->inner_tol >= 0 && d->inner_tol < 1)) { err = "inner_tol must be in [0, 1)"; return false; }
     if (d->n_instances < 0 || d->n_instances > (1 << 16)) { err = "n_instances out of range"; return false; }
-    if (d->n_instances > 0 && d->krylov != 0) { err = "batches need krylov = 0"; return false; }
     if ((int64_t)std::max(1, d->n_instances) * d->nblocks >= (int64_t)1 << 31) { err = "too many blocks"; return false; }
     for (int a = 0; a < 3; a++)
         if (((int64_t)d->base_cells[a] << (d->nlevels - 1)) >= (1 << 20)) { err = "level too fine"; return false; }
@@ -1430,6 +1669,8 @@ void ohm_destroy(ohm_hier *h) {
     if (h->hnorm) cudaFreeHost(h->hnorm);
     if (h->hnormK) cudaFreeHost(h->hnormK);
     if (h->imask_h) cudaFreeHost(h->imask_h);
+    if (h->hdotsK) cudaFreeHost(h->hdotsK);
+    if (h->hcoef) cudaFreeHost(h->hcoef);
     delete h;
 }
 

@@ -157,4 +157,12 @@ cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float sc
 
 cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s);
 
+// Batched hierarchies: per-instance products out[q][0..k] (layout [ninst][KMAX+1]; part:
+// nblk * (k+1) doubles of block partials), and dst = (src - sum_i coef[q][i] v_i) * coef[q][KMAX]
+// with q = binst[block] (coef: [ninst][KMAX+1] floats on the device).
+cudaError_t launch_mdot_inst(const float *w, const VecSet &V, const double *wb, int nblk, const InstRanges &R, int ninst,
+                             double *part, double *out, cudaStream_t s);
+cudaError_t launch_maxpy_inst(float *dst, const float *src, const VecSet &V, const float *coef, const int *binst,
+                              size_t n, cudaStream_t s);
+
 }  // namespace ohm

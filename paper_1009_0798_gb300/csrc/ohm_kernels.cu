@@ -1221,6 +1221,102 @@ cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float sc
     return cudaGetLastError();
 }
 
+// Per-instance Krylov vector kernels of batched hierarchies.  Block partials: one warp per
+// block writes its weighted products (no folding across blocks, so no sum mixes instances).
+__global__ void __launch_bounds__(256) k_mdot_blocks(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
+                                                     int nblk, double *__restrict__ part) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
+    if (b >= nblk) return;
+    const int ncol = V.k + 1;
+    float f[KMAX + 1];
+#pragma unroll
+    for (int i = 0; i <= KMAX; i++) f[i] = 0.f;
+    const double wt = wb[b];
+    if (wt != 0.0) {
+        const float4 *w4 = reinterpret_cast<const float4 *>(w + (size_t)b * 1536);
+#pragma unroll 4
+        for (int s = 0; s < 12; s++) {
+            const float4 x = w4[lane + 32 * s];
+            f[KMAX] += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+#pragma unroll
+            for (int i = 0; i < KMAX; i++)
+                if (i < V.k) {
+                    const float4 v = reinterpret_cast<const float4 *>(V.v[i] + (size_t)b * 1536)[lane + 32 * s];
+                    f[i] += x.x * v.x + x.y * v.y + x.z * v.z + x.w * v.w;
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i <= KMAX; i++) {
+        if (i > V.k) break;
+        float v = i == V.k ? f[KMAX] : f[i < KMAX ? i : KMAX];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[(size_t)b * ncol + i] = (double)v * wt;
+    }
+}
+
+// out[q][c] = sum of part[b][c] over instance q's blocks of every level, in a fixed order
+__global__ void __launch_bounds__(256) k_colsum_inst(const double *__restrict__ part, InstRanges R, int ncol,
+                                                     double *__restrict__ out) {
+    __shared__ double red[32];
+    const int q = blockIdx.x;
+    for (int c = 0; c < ncol; c++) {
+        double a = 0.0;
+        for (int l = 0; l < R.nlev; l++) {
+            const int lo = R.off[l] + q * R.n[l], hi = lo + R.n[l];
+            for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) a += part[(size_t)b * ncol + c];
+        }
+        const double sum = block_sum(a, red);
+        if (threadIdx.x == 0) out[(size_t)q * (KMAX + 1) + c] = sum;
+    }
+}
+
+cudaError_t launch_mdot_inst(const float *w, const VecSet &V, const double *wb, int nblk, const InstRanges &R, int ninst,
+                             double *part, double *out, cudaStream_t s) {
+    k_mdot_blocks<<<(nblk + 7) / 8, 256, 0, s>>>(w, V, wb, nblk, part);
+    k_colsum_inst<<<ninst, 256, 0, s>>>(part, R, V.k + 1, out);
+    return cudaGetLastError();
+}
+
+// dst = (src - sum_i c[q][i] v_i) * c[q][KMAX] with q the instance of the element's block;
+// terms whose coefficient is 0 are skipped (their vectors may hold anything for that instance)
+__global__ void __launch_bounds__(256) k_maxpy_inst(float4 *dst, const float4 *src, VecSet V,
+                                                    const float *__restrict__ coef, const int *__restrict__ binst,
+                                                    size_t n4) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+        const float *cq = coef + (size_t)binst[e / 384] * (KMAX + 1);
+        float4 x = src[e];
+#pragma unroll
+        for (int i = 0; i < KMAX; i++)
+            if (i < V.k) {
+                const float c = cq[i];
+                if (c != 0.f) {
+                    const float4 v = reinterpret_cast<const float4 *>(V.v[i])[e];
+                    x.x -= c * v.x;
+                    x.y -= c * v.y;
+                    x.z -= c * v.z;
+                    x.w -= c * v.w;
+                }
+            }
+        const float sc = cq[KMAX];
+        x.x *= sc;
+        x.y *= sc;
+        x.z *= sc;
+        x.w *= sc;
+        dst[e] = x;
+    }
+}
+
+cudaError_t launch_maxpy_inst(float *dst, const float *src, const VecSet &V, const float *coef, const int *binst,
+                              size_t n, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
+    k_maxpy_inst<<<grid, 256, 0, s>>>(reinterpret_cast<float4 *>(dst), reinterpret_cast<const float4 *>(src), V, coef,
+                                      binst, n4);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ coarsest grids
 // Lexicographic periodic grids below the last blocked grid, all handled by one thread block per
 // instance with a barrier between phases.  Face flux and divergence as above, with periodic wrap.

@@ -101,7 +101,7 @@ ohm_hier_desc structure_desc(const ohm_server *S, const Req *r, int K, void *str
     d.nu_post = S->d.nu_post;
     d.n_coarse = S->d.n_coarse;
     d.max_outer = S->d.max_outer;
-    d.krylov = 0;
+    d.krylov = S->d.krylov;
     d.inner_tol = 0;
     d.n_instances = K;
     d.use_graphs = S->d.use_graphs;
@@ -371,7 +371,8 @@ int ohm_server_create(const ohm_server_desc *d, ohm_server **out) {
     *out = nullptr;
     if (d->hbm_budget_bytes <= 0 || d->max_batch < 1 || d->max_batch > 4096 || d->n_workers < 1 || d->n_workers > 64 ||
         (d->precision != OHM_FP64 && d->precision != OHM_MIXED) || !(d->lambda > 0 && d->lambda <= 1) || !(d->tol >= 0) ||
-        d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1)
+        d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1 || d->krylov < 0 || d->krylov > 11 ||
+        (d->krylov > 0 && d->precision != OHM_MIXED))
         return OHM_ERR_INVALID;
     ohm_server *S = new ohm_server();
     S->d = *d;

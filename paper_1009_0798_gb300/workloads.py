@@ -334,7 +334,7 @@ def smooth_lognormal_eta(n: int, seed: int, decades: float = 2.0, eta_min: float
     k = np.fft.fftfreq(n)
     kr = np.fft.rfftfreq(n)
     k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2
-    u = np.fft.irfftn(np.fft.rfftn(noise) * np.exp(-2.0 * math.pi ** 2 * sigma_cells ** 2 * k2), s=(n, n, n))
+    u = np.fft.irfftn(np.fft.rfftn(noise) * np.exp(-2.0 * math.pi ** 2 * sigma_cells ** 2 * k2), s=(n, n, n), axes=(0, 1, 2))
     u = (u - u.min()) / (u.max() - u.min())
     return (eta_min * 10.0 ** (decades * u))[None]
 

@@ -97,8 +97,10 @@ def test_batch_bytes_grow_with_instances(libohm):
     one = libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=1)
     four = libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=4)
     assert 3.5 * one < four < 4.5 * one
+    kry = libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=4, krylov=4)
+    assert kry > four  # Krylov basis and per-instance product scratch
     with pytest.raises(libohm.OhmError):
-        libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=4, krylov=4)
+        libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, n_instances=4, krylov=4)  # FP64 has no Krylov
 
 
 def test_server_rejects_bad_descriptor_without_gpu(libohm):

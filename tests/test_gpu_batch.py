@@ -215,3 +215,58 @@ def test_batch_rejects_single_entry_points_and_bad_args(ohm):
         ohm.ohm_cn_step_batch(g, B, [0.1, -1.0], 1e-9)
     status, st = ohm.ohm_cn_step_batch(g, B, [0.1, -1.0], 1e-9, active=[1, 0])  # inactive dt unused
     assert status == ohm.OHM_OK and st[1]["cycles"] == 0
+
+
+@pytest.mark.parametrize("name", ["uniform_16", "amr_2level"])
+def test_fgmres_batch_converges_to_oracle(ohm, orc, name):
+    """Per-instance FGMRES(4) inner solves in one batch reach each instance's FP64 solution."""
+    h = W.uniform(16, 16, 16, 1.0 / 16) if name == "uniform_16" else amr_two_level(16)
+    K = 4
+    bs, etas = instances(h, K, 90)
+    bs = [orc.Oracle(h, 0.5, etas[q]).sync_down(bs[q]) for q in range(K)]
+    dts = [(3.0 + 2.0 * q) * h.dx(h.nlevels - 1) ** 2 for q in range(K)]
+    g = make(ohm, h, K, precision=1, max_outer=120, krylov=4)
+    ohm.ohm_set_eta(g, dev(stack(h, etas)))
+    B = dev(stack(h, bs))
+    status, st = ohm.ohm_cn_step_batch(g, B, dts, 1e-11)
+    assert status == ohm.OHM_OK, st
+    got = unstack(h, host(B).reshape(-1, 1536), K)
+    for q in range(K):
+        assert st[q]["converged"] and st[q]["rel_l2"] <= 1e-11
+        want, _ = orc.Oracle(h, 0.5, etas[q]).cn_step(bs[q], dts[q], 1e-14, 2, 2, 8, 120)
+        assert rel_err(got[q], want.reshape(-1, 1536)) < 1e-9, q
+
+
+def test_fgmres_batch_same_bits_alone_and_in_batch(ohm):
+    h = amr_two_level(16)
+    K = 4
+    bs, etas = instances(h, K, 95)
+    dts = [(2.0 + q) * h.dx(1) ** 2 for q in range(K)]
+    g1 = make(ohm, h, 1, precision=1, krylov=4)
+    ohm.ohm_set_eta(g1, dev(etas[1]))
+    B1 = dev(bs[1])
+    _, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[1]], 1e-9)
+    gK = make(ohm, h, K, precision=1, krylov=4)
+    ohm.ohm_set_eta(gK, dev(stack(h, etas)))
+    BK = dev(stack(h, bs))
+    _, stK = ohm.ohm_cn_step_batch(gK, BK, dts, 1e-9, active=[1, 1, 0, 1])
+    got = unstack(h, host(BK).reshape(-1, 1536), K)
+    assert st1[0]["converged"] and stK[1]["converged"] and st1[0]["cycles"] == stK[1]["cycles"]
+    assert np.array_equal(got[1], host(B1).reshape(-1, 1536))
+    assert stK[2]["cycles"] == 0
+
+
+def test_fgmres_batch_takes_fewer_cycles(ohm):
+    """On the stiff 32^3 resistive bump (3-decade eta, dt = 100x the explicit limit), batched
+    FGMRES(6) needs fewer V-cycles per instance than batched defect correction."""
+    wl = W.resistive_bump_256(n=32)
+    K = 3
+    cyc = {}
+    for kr in (0, 6):
+        g = make(ohm, wl.hier, K, precision=1, max_outer=300, krylov=kr, n_coarse=16)
+        ohm.ohm_set_eta(g, dev(np.concatenate([wl.eta] * K)))
+        B = dev(np.concatenate([wl.B] * K))
+        status, st = ohm.ohm_cn_step_batch(g, B, [wl.dt, 0.5 * wl.dt, 2.0 * wl.dt], 1e-9)
+        assert status == ohm.OHM_OK
+        cyc[kr] = [x["cycles"] for x in st]
+    assert all(a < b for a, b in zip(cyc[6], cyc[0])), cyc
