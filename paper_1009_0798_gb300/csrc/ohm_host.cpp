@@ -50,6 +50,7 @@ struct HGrid {
     std::vector<uint8_t> covered, octant;
     int slot0 = 0, nslot = 0;
     int inst_nblk = 0;          // batches: blocks per instance
+    bool brick = false;         // blocks pair up as x-neighbours (2q, 2q+1), every neighbour present
     GridDev dev;
     int find(int i, int j, int k) const {
         auto it = index.find(key3(wrapi(i, nb[0]), wrapi(j, nb[1]), wrapi(k, nb[2])));
@@ -593,6 +594,10 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
         dv.nslot = g->nslot;
         dv.slot0 = g->slot0;
         dv.inst_nblk = g->inst_nblk;
+        const int nb = g->n();
+        g->brick = nb % 2 == 0 && g->nslot == 0 && !g->nbr.empty() &&
+                   std::none_of(g->nbr.begin(), g->nbr.end(), [](int v) { return v < 0; });
+        for (int q = 0; g->brick && q < nb / 2; q++) g->brick = g->nbr[(size_t)(2 * q) * 27 + 14] == 2 * q + 1;
         k += 10;
     }
     H->d_rsrc = (int *)(H->rsrc_tab.empty() ? nullptr : base + offs[k]);
@@ -732,11 +737,16 @@ GridRef base_ref(ohm_hier *H, int m) {  // m = 0: AMR level 0
 template <typename T>
 int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
     if (std::is_same<T, float>::value && G.g->nslot == 0 && H->smoother == 0) {
-        // float32 grids with every neighbour: one fused red+black launch per sweep
+        // float32 grids with every neighbour: one fused red+black launch per sweep, on block
+        // pairs where the grid's blocks pair up along x
         for (int i = 0; i < n; i++) {
             const T *src = (const T *)((i & 1) ? G.e2 : G.e);
             T *dst = (T *)((i & 1) ? G.e : G.e2);
-            LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb<T>(gdev(H, *G.g), src, dst, (const T *)G.r, (const T *)G.eta, lamdt, H->s));
+            if (G.g->brick)
+                LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb2(gdev(H, *G.g), (const float *)src, (float *)dst,
+                                                                    (const float *)G.r, (const float *)G.eta, lamdt, H->s));
+            else
+                LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb<T>(gdev(H, *G.g), src, dst, (const T *)G.r, (const T *)G.eta, lamdt, H->s));
         }
         if (n & 1) CK(cudaMemcpyAsync(G.e, G.e2, (size_t)G.g->n() * 3 * B3 * sizeof(T), cudaMemcpyDeviceToDevice, H->s));
         return OHM_OK;

@@ -78,6 +78,11 @@ template <typename T>
 cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta, double lamdt,
                              cudaStream_t s);
 
+// The same sweep for pairs of x-adjacent blocks (2q, 2q+1): grids with an even block count whose
+// pairs are x-neighbours and whose blocks all have their 26 neighbours.
+cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out, const float *r, const float *eta,
+                              double lamdt, cudaStream_t s);
+
 // t = r - (e + lamdt divF(e)); restricted (mean of 8) into the coarser grid: blocked
 // (coarse != nullptr, by parent/octant) or lexicographic (lex != nullptr, dims ldims).
 template <typename T>

@@ -506,10 +506,9 @@ struct G12 {
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
-template <typename T>
+template <typename T, typename G = G12<T>>
 __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
                                           const T rr[3], T out[3]) {
-    using G = G12<T>;
     T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
     face_phi_s(tB, tE, p - 1, 0, 1, G::RRS, G::PS, G::CS, xl1, xl2);
     face_phi_s(tB, tE, p, 0, 1, G::RRS, G::PS, G::CS, xh1, xh2);
@@ -629,6 +628,137 @@ template cudaError_t launch_smooth_rb<float>(const GridDev &, const float *, flo
                                              cudaStream_t);
 template cudaError_t launch_smooth_rb<double>(const GridDev &, const double *, double *, const double *, const double *,
                                               double, cudaStream_t);
+
+// ------------------------------------------------------------------ fused sweep on brick pairs
+// The fused sweep above for two x-adjacent blocks A = 2q and B = 2q + 1 per thread block (512
+// threads): a 20 x 12 x 12 tile (two-cell halo) shares its halo and ring between the two
+// blocks, so per block it stages 17% fewer values and recomputes 20% fewer ring updates.
+// Rows are 24 floats apart: the warp pattern of the brick's same-colour cells (4 rows x 8
+// cells at stride 2) then falls on 32 distinct banks; the interior of a row starts on a
+// 16-byte boundary (index OFF + 2).  Used for float32 grids whose every block pair (2q, 2q+1)
+// is x-adjacent and whose blocks all have their 26 neighbours.  Bounded to 40 registers so
+// that 3 thread blocks (48 warps) share an SM: 0.401 ms per 256^3 sweep, against 0.427 ms at
+// 54 registers (2 per SM) and 0.431 ms for the one-block kernel above.
+struct G20 {
+    static constexpr int SX = 20, S = 12, RRS = 24, PS = S * RRS, CS = S * PS, OFF = 2;
+    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
+};
+
+// red cells of the brick's one-cell ring (faces and edges, no corners): 384 entries
+// (li+1) | (lj+1) << 5 | (lk+1) << 10, li in [-1, 16], lj, lk in [-1, 8]; built at compile time
+struct Ring2 {
+    uint32_t v[384];
+};
+constexpr Ring2 make_ring2() {
+    Ring2 m{};
+    int n = 0;
+    for (int k = -1; k <= 8; k++)
+        for (int j = -1; j <= 8; j++)
+            for (int i = -1; i <= 16; i++) {
+                const int out = (i < 0 || i > 15) + (j < 0 || j > 7) + (k < 0 || k > 7);
+                if (out == 0 || out == 3 || ((i + j + k) & 1)) continue;
+                m.v[n++] = (uint32_t)(i + 1) | ((uint32_t)(j + 1) << 5) | ((uint32_t)(k + 1) << 10);
+            }
+    return m;
+}
+__device__ const Ring2 g_ring2 = make_ring2();
+
+__global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *__restrict__ e_in, float *__restrict__ e_out,
+                                                    const float *__restrict__ r, const float *__restrict__ eta, float coef,
+                                                    float lh2) {
+    using G = G20;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tB = reinterpret_cast<float *>(smem_raw);  // [3][12 planes][12 rows][RRS]
+    float *tE = tB + 3 * G::CS;
+    // neighbourhood of the brick: block columns bx = -1, 0 (A), 1 (B), 2 along x, by dj, dk
+    __shared__ int snb[36];
+    const int A = 2 * blockIdx.x;
+    if (skip_block(g, A)) return;
+    if (threadIdx.x < 36) {
+        const int bx = threadIdx.x % 4 - 1, dj = (threadIdx.x / 4) % 3 - 1, dk = threadIdx.x / 12 - 1;
+        const int base = bx <= 1 ? A : A + 1, dx = bx <= 1 ? bx : 1;
+        snb[threadIdx.x] = __ldg(g.nbr + base * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (dx + 1));
+    }
+    __syncthreads();
+    // one task per (field component, tile row): halo pair, 8 + 8 interior cells, halo pair
+    for (int task = threadIdx.x; task < 4 * 144; task += blockDim.x) {
+        const int c = task / 144, rr = task - c * 144;
+        const int tj = rr % 12, tk = rr / 12;
+        const int lj = tj - 2, lk = tk - 2;
+        const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int rowoff = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8;
+        const int *nb = snb + (dk + 1) * 12 + (dj + 1) * 4;
+        const float *F = c < 3 ? e_in : eta;
+        const int nc = c < 3 ? 3 : 1, cc = c < 3 ? c : 0;
+        float *dst = (c < 3 ? tB + c * G::CS : tE) + tk * G::PS + tj * G::RRS + G::OFF;
+        const float2 lo = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)nb[0] * nc + cc) * B3 + rowoff + 6));
+        const float4 *pa = reinterpret_cast<const float4 *>(F + ((size_t)nb[1] * nc + cc) * B3 + rowoff);
+        const float4 *pb = reinterpret_cast<const float4 *>(F + ((size_t)nb[2] * nc + cc) * B3 + rowoff);
+        const float2 hi = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)nb[3] * nc + cc) * B3 + rowoff));
+        const float4 a0 = __ldg(pa), a1 = __ldg(pa + 1), b0 = __ldg(pb), b1 = __ldg(pb + 1);
+        *reinterpret_cast<float2 *>(dst) = lo;
+        reinterpret_cast<float4 *>(dst + 2)[0] = a0;
+        reinterpret_cast<float4 *>(dst + 2)[1] = a1;
+        reinterpret_cast<float4 *>(dst + 10)[0] = b0;
+        reinterpret_cast<float4 *>(dst + 10)[1] = b1;
+        *reinterpret_cast<float2 *>(dst + 18) = hi;
+    }
+    const int t = threadIdx.x;
+    const int k = t >> 6, j = (t >> 3) & 7, i2 = t & 7;
+    const int ir = 2 * i2 + ((j + k) & 1), ib = 2 * i2 + ((j + k + 1) & 1);  // both in block A (i2 < 4) or B
+    const int own = A + (i2 >> 2);
+    const int cr = (k * 8 + j) * 8 + (ir & 7), cb = (k * 8 + j) * 8 + (ib & 7);
+    float rr0[3], rr1[3] = {0.f, 0.f, 0.f}, rrb[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        rr0[c] = r[((size_t)own * 3 + c) * B3 + cr];
+        rrb[c] = r[((size_t)own * 3 + c) * B3 + cb];
+    }
+    int p1 = -1;
+    if (t < 384) {
+        const uint32_t code = __ldg(&g_ring2.v[t]);
+        const int li = (int)(code & 31u) - 1, lj = (int)((code >> 5) & 31u) - 1, lk = (int)((code >> 10) & 31u) - 1;
+        const int bx = li < 0 ? -1 : (li > 15 ? 2 : (li >> 3));
+        const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int src = snb[(dk + 1) * 12 + (dj + 1) * 4 + (bx + 1)];
+        const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * bx);
+#pragma unroll
+        for (int c = 0; c < 3; c++) rr1[c] = r[((size_t)src * 3 + c) * B3 + off];
+        p1 = G::at(li + 2, lj + 2, lk + 2);
+    }
+    __syncthreads();
+    // red: the brick's 512 (one per thread), then the 384 of its ring, from the pre-sweep state
+    float nv0[3], nv1[3];
+    const int p0 = G::at(ir + 2, j + 2, k + 2);
+    rb_update<float, G>(tB, tE, p0, coef, lh2, rr0, nv0);
+    if (p1 >= 0) rb_update<float, G>(tB, tE, p1, coef, lh2, rr1, nv1);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        tB[c * G::CS + p0] = nv0[c];
+        if (p1 >= 0) tB[c * G::CS + p1] = nv1[c];
+    }
+    __syncthreads();
+    // black cells of the brick from the post-red state, then both blocks are written out
+    float out[3];
+    rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        e_out[((size_t)own * 3 + c) * B3 + cb] = out[c];
+        e_out[((size_t)own * 3 + c) * B3 + cr] = nv0[c];
+    }
+}
+
+cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out, const float *r, const float *eta,
+                              double lamdt, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    const size_t sm = 4 * G20::CS * sizeof(float);
+    static const bool attr = (cudaFuncSetAttribute(k_smooth_rb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
+    (void)attr;
+    k_smooth_rb2<<<g.nblk / 2, 512, sm, s>>>(g, e_in, e_out, r, eta, (float)(lamdt / (2.0 * g.h * g.h)),
+                                             (float)(lamdt / (g.h * g.h)));
+    return cudaGetLastError();
+}
 
 // ------------------------------------------------------------------ inverse diagonal
 // inv_c = 1 / (1 + alpha_c), alpha_c = lamdt/h^2 sum_{a != c} (eta_{-1/2} + eta_{+1/2})
