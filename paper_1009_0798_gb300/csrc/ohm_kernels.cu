@@ -634,30 +634,51 @@ template cudaError_t launch_smooth_rb<double>(const GridDev &, const double *, d
 // threads): a 20 x 12 x 12 tile (two-cell halo) shares its halo and ring between the two
 // blocks, so per block it stages 17% fewer values and recomputes 20% fewer ring updates.
 // Rows are 24 floats apart: the warp pattern of the brick's same-colour cells (4 rows x 8
-// cells at stride 2) then falls on 32 distinct banks; the interior of a row starts on a
-// 16-byte boundary (index OFF + 2).  Used for float32 grids whose every block pair (2q, 2q+1)
-// is x-adjacent and whose blocks all have their 26 neighbours.  Bounded to 40 registers so
-// that 3 thread blocks (48 warps) share an SM: 0.401 ms per 256^3 sweep, against 0.427 ms at
-// 54 registers (2 per SM) and 0.431 ms for the one-block kernel above.
+// cells at stride 2) then falls on 32 distinct banks; each tile row starts on a 16-byte
+// boundary and is staged as five 16-byte words.  Used for float32 grids whose every block pair (2q, 2q+1)
+// is x-adjacent and whose blocks all have their 26 neighbours.
 struct G20 {
-    static constexpr int SX = 20, S = 12, RRS = 24, PS = S * RRS, CS = S * PS, OFF = 2;
+    static constexpr int SX = 20, S = 12, RRS = 24, PS = S * RRS + 4, CS = S * PS, OFF = 0;
     __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
 };
 
 // red cells of the brick's one-cell ring (faces and edges, no corners): 384 entries
-// (li+1) | (lj+1) << 5 | (lk+1) << 10, li in [-1, 16], lj, lk in [-1, 8]; built at compile time
+// (li+1) | (lj+1) << 5 | (lk+1) << 10, li in [-1, 16], lj, lk in [-1, 8], ordered for the 12
+// warps that update them so that shared-memory banks (tile offset mod 32) repeat little within a
+// warp: with the strides of G20 a bank holds at most 17 of the 384 cells and at least 8, so 7
+// warps take one cell per bank and 5 warps at most two.  Built at compile time.
 struct Ring2 {
     uint32_t v[384];
 };
+constexpr int ring2_bank(int i, int j, int k) { return ((i + 2 + G20::OFF) + (j + 2) * G20::RRS + (k + 2) * G20::PS) & 31; }
+constexpr bool ring2_cell(int i, int j, int k) {
+    const int out = (i < 0 || i > 15) + (j < 0 || j > 7) + (k < 0 || k > 7);
+    return out != 0 && out != 3 && ((i + j + k) & 1) == 0;
+}
 constexpr Ring2 make_ring2() {
     Ring2 m{};
-    int n = 0;
+    int cnt[32] = {};
+    for (int k = -1; k <= 8; k++)
+        for (int j = -1; j <= 8; j++)
+            for (int i = -1; i <= 16; i++)
+                if (ring2_cell(i, j, k)) cnt[ring2_bank(i, j, k)]++;
+    int maxc = 0;
+    for (int r = 0; r < 32; r++) maxc = cnt[r] > maxc ? cnt[r] : maxc;
+    const int A = 24 - maxc < 12 ? 24 - maxc : 12;  // warps with one cell per bank
+    int fill[12] = {}, seen[32] = {}, two[12][32] = {};
     for (int k = -1; k <= 8; k++)
         for (int j = -1; j <= 8; j++)
             for (int i = -1; i <= 16; i++) {
-                const int out = (i < 0 || i > 15) + (j < 0 || j > 7) + (k < 0 || k > 7);
-                if (out == 0 || out == 3 || ((i + j + k) & 1)) continue;
-                m.v[n++] = (uint32_t)(i + 1) | ((uint32_t)(j + 1) << 5) | ((uint32_t)(k + 1) << 10);
+                if (!ring2_cell(i, j, k)) continue;
+                const int r = ring2_bank(i, j, k), n = seen[r]++;
+                int w = n;
+                if (n >= A) {
+                    w = -1;
+                    for (int c = A; c < 12; c++)
+                        if (two[c][r] < 2 && fill[c] < 32 && (w < 0 || fill[c] < fill[w])) w = c;
+                    two[w][r]++;
+                }
+                m.v[w * 32 + fill[w]++] = (uint32_t)(i + 1) | ((uint32_t)(j + 1) << 5) | ((uint32_t)(k + 1) << 10);
             }
     return m;
 }
@@ -680,28 +701,30 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
         snb[threadIdx.x] = __ldg(g.nbr + base * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (dx + 1));
     }
     __syncthreads();
-    // one task per (field component, tile row): halo pair, 8 + 8 interior cells, halo pair
+    // one task per (field component, tile row): the 20 values of the row (halo pair, 8 + 8
+    // interior cells, halo pair) as five 16-byte stores; each quarter-warp takes 4 rows of 2
+    // consecutive planes, whose 16-byte bank groups are distinct (plane stride = 4 mod 32)
     for (int task = threadIdx.x; task < 4 * 144; task += blockDim.x) {
-        const int c = task / 144, rr = task - c * 144;
-        const int tj = rr % 12, tk = rr / 12;
+        const int c = task / 144, u = task - c * 144;
+        const int q = u >> 3, w = u & 7;
+        const int tk = 2 * (q / 3) + (w >> 2), tj = 4 * (q % 3) + (w & 3);
         const int lj = tj - 2, lk = tk - 2;
         const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
         const int rowoff = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8;
         const int *nb = snb + (dk + 1) * 12 + (dj + 1) * 4;
         const float *F = c < 3 ? e_in : eta;
         const int nc = c < 3 ? 3 : 1, cc = c < 3 ? c : 0;
-        float *dst = (c < 3 ? tB + c * G::CS : tE) + tk * G::PS + tj * G::RRS + G::OFF;
+        float4 *dst = reinterpret_cast<float4 *>((c < 3 ? tB + c * G::CS : tE) + tk * G::PS + tj * G::RRS + G::OFF);
         const float2 lo = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)nb[0] * nc + cc) * B3 + rowoff + 6));
         const float4 *pa = reinterpret_cast<const float4 *>(F + ((size_t)nb[1] * nc + cc) * B3 + rowoff);
         const float4 *pb = reinterpret_cast<const float4 *>(F + ((size_t)nb[2] * nc + cc) * B3 + rowoff);
         const float2 hi = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)nb[3] * nc + cc) * B3 + rowoff));
         const float4 a0 = __ldg(pa), a1 = __ldg(pa + 1), b0 = __ldg(pb), b1 = __ldg(pb + 1);
-        *reinterpret_cast<float2 *>(dst) = lo;
-        reinterpret_cast<float4 *>(dst + 2)[0] = a0;
-        reinterpret_cast<float4 *>(dst + 2)[1] = a1;
-        reinterpret_cast<float4 *>(dst + 10)[0] = b0;
-        reinterpret_cast<float4 *>(dst + 10)[1] = b1;
-        *reinterpret_cast<float2 *>(dst + 18) = hi;
+        dst[0] = make_float4(lo.x, lo.y, a0.x, a0.y);
+        dst[1] = make_float4(a0.z, a0.w, a1.x, a1.y);
+        dst[2] = make_float4(a1.z, a1.w, b0.x, b0.y);
+        dst[3] = make_float4(b0.z, b0.w, b1.x, b1.y);
+        dst[4] = make_float4(b1.z, b1.w, hi.x, hi.y);
     }
     const int t = threadIdx.x;
     const int k = t >> 6, j = (t >> 3) & 7, i2 = t & 7;
