@@ -719,6 +719,26 @@ def serving_requests(count, rate, seed=5):
     return reqs
 
 
+def serving_cpu_baseline(reqs, inputs):
+    """The oracle on the host cores for one request of the stream's smallest uniform class (one
+    step to 1e-9): a bounded sample, in served cell-steps/s."""
+    try:
+        from oracle import build as obuild
+        from oracle.oracle import Oracle
+        obuild.build()
+        k = min((q for q, r in enumerate(reqs) if r["key"] != "amr"), key=lambda q: reqs[q]["hier"].leaf_cells())
+        r = reqs[k]
+        o = Oracle(r["hier"], 0.5, inputs[k][1])
+        t = time.perf_counter()
+        o.cn_step(inputs[k][0], r["dt"], 1e-9, 2, 2, 16, 400)
+        sec = time.perf_counter() - t
+        return {"value": r["hier"].leaf_cells() / sec, "unit": UNIT,
+                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                "sample": f"request {k} of the stream ({r['key']}^3, one step to 1e-9, {sec:.1f} s)"}
+    except Exception as ex:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
+
+
 def run_serving(args):
     """Poisson stream of CN-solve requests through the continuous-batching service: requests
     are submitted at their arrival times (host clock) with host arrays; latency = completion
@@ -803,7 +823,9 @@ def run_serving(args):
                     "h2d_bytes_per_step": int(np.mean([a.nbytes + b.nbytes for a, b in inputs])),
                     "d2h_bytes_per_step": int(np.mean([a.nbytes for a, _ in inputs])),
                     "timing": "host clock, submit to result in host memory"},
-            "clocks": clk.summary(), "gpu_launches": None, "roofline": None, "cpu_baseline": None}
+            "clocks": clk.summary(), "gpu_launches": stats.get("kernel_launches"),
+            "roofline": None, "roofline_note": "the service runs the kernels of the batched and headline lines",
+            "cpu_baseline": serving_cpu_baseline(reqs, inputs) if not args.no_cpu_baseline else None}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -77,6 +77,7 @@ typedef struct {
     int64_t bytes_resident, bytes_resident_max;
     int64_t steps_run;          /* batched steps issued                                        */
     double mean_active_slots;   /* active slots per batched step                               */
+    int64_t kernel_launches;    /* kernel launches issued by all batches so far                */
 } ohm_server_stats;
 
 /* Starts the worker threads on the calling thread's current CUDA device. */

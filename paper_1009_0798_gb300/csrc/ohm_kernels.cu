@@ -43,13 +43,17 @@ template <>
 struct G10<double> {
     static constexpr int RS = 10, PX = 9, OFF = 0;
 };
+// z-face planes are PZ apart: 72 for float32 (= 8 mod 32 banks, like the x- and y-face arrays
+// and the tile planes, so a warp of 4 planes x 8 cells reads 32 distinct banks), 64 for float64
 template <typename T>
 struct Geo {
     static constexpr int RS = G10<T>::RS, PS = TS * RS, CS = TS * PS, PX = G10<T>::PX, OFF = G10<T>::OFF;
+    static constexpr int PZ = sizeof(T) == 4 ? 72 : 64;
     static constexpr int PHI_X = 64 * PX;  // x faces per component
-    static constexpr int PHI = 2 * PHI_X + 4 * 576;
+    static constexpr int PHI = 2 * PHI_X + 2 * 576 + 2 * 9 * PZ;
     __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RS + i + OFF; }
     __device__ static __forceinline__ int xf(int fi, int j, int k) { return (k * 8 + j) * PX + fi; }
+    __device__ static __forceinline__ int zf(int i, int j, int fk) { return fk * PZ + j * 8 + i; }
 };
 
 // 8 consecutive values of a block row (16-byte aligned in global memory) as vector loads
@@ -205,11 +209,27 @@ __device__ __forceinline__ void face10(const T *__restrict__ tB, const T *__rest
 }
 
 // Offsets of the six flux arrays: x faces [2 comps][64 rows][PX] (index xf), y faces
-// [2][8][9][8] ((k*9+fj)*8+i), z faces [2][9][8][8] ((fk*8+j)*8+i).
+// [2][8][9][8] ((k*9+fj)*8+i), z faces [2][9][PZ] (index zf).
 template <typename T>
 __device__ __forceinline__ int phi_base(int ax, int comp) {
     using G = Geo<T>;
-    return ax == 0 ? comp * G::PHI_X : 2 * G::PHI_X + ((ax - 1) * 2 + comp) * 576;
+    return ax == 0 ? comp * G::PHI_X : (ax == 1 ? 2 * G::PHI_X + comp * 576 : 2 * G::PHI_X + 2 * 576 + comp * 9 * G::PZ);
+}
+
+// Cell of thread t in the 512-thread stencil kernels.  float32: a warp takes one row index j of
+// 4 consecutive planes (i fastest), whose tile and face-array offsets fall on 32 distinct banks
+// for the compact strides above; float64 keeps i + 8 j + 64 k.
+template <typename T>
+__device__ __forceinline__ void cell_of_thread(int t, int &i, int &j, int &k) {
+    if (sizeof(T) == 4) {
+        i = t & 7;
+        k = ((t >> 3) & 3) + 4 * (t >> 8);
+        j = (t >> 5) & 7;
+    } else {
+        i = t & 7;
+        j = (t >> 3) & 7;
+        k = t >> 6;
+    }
 }
 
 // All 1728 face fluxes of a staged block (512 threads): thread (i,j,k) computes the low x, y
@@ -217,7 +237,9 @@ __device__ __forceinline__ int phi_base(int ax, int comp) {
 template <typename T>
 __device__ __forceinline__ void all_faces_512(const T *__restrict__ tB, const T *__restrict__ tE, T *__restrict__ phi) {
     using G = Geo<T>;
-    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    const int t = threadIdx.x;
+    int i, j, k;
+    cell_of_thread<T>(t, i, j, k);
     const int p = G::at(i + 1, j + 1, k + 1);
     T p1, p2;
     face10(tB, tE, p - 1, 0, p1, p2);
@@ -227,8 +249,8 @@ __device__ __forceinline__ void all_faces_512(const T *__restrict__ tB, const T 
     phi[phi_base<T>(1, 0) + (k * 9 + j) * 8 + i] = p1;
     phi[phi_base<T>(1, 1) + (k * 9 + j) * 8 + i] = p2;
     face10(tB, tE, p - G::PS, 2, p1, p2);
-    phi[phi_base<T>(2, 0) + (k * 8 + j) * 8 + i] = p1;
-    phi[phi_base<T>(2, 1) + (k * 8 + j) * 8 + i] = p2;
+    phi[phi_base<T>(2, 0) + G::zf(i, j, k)] = p1;
+    phi[phi_base<T>(2, 1) + G::zf(i, j, k)] = p2;
     if (t < 192) {
         const int ax = t >> 6, u = t & 7, v = (t >> 3) & 7;
         if (ax == 0) {  // x = 8 plane: (j, k) = (u, v)
@@ -241,8 +263,8 @@ __device__ __forceinline__ void all_faces_512(const T *__restrict__ tB, const T 
             phi[phi_base<T>(1, 1) + (v * 9 + 8) * 8 + u] = p2;
         } else {  // z = 8 plane: (i, j) = (u, v)
             face10(tB, tE, G::at(u + 1, v + 1, 8), 2, p1, p2);
-            phi[phi_base<T>(2, 0) + (8 * 8 + v) * 8 + u] = p1;
-            phi[phi_base<T>(2, 1) + (8 * 8 + v) * 8 + u] = p2;
+            phi[phi_base<T>(2, 0) + G::zf(u, v, 8)] = p1;
+            phi[phi_base<T>(2, 1) + G::zf(u, v, 8)] = p2;
         }
     }
 }
@@ -254,9 +276,9 @@ __device__ __forceinline__ void cell_div(const T *__restrict__ phi, int i, int j
     const T *px0 = phi, *px1 = phi + G::PHI_X;                                // x faces: comps y, z
     const T *py0 = phi + phi_base<T>(1, 0), *py1 = phi + phi_base<T>(1, 1);  // y faces: comps x, z
     const T *pz0 = phi + phi_base<T>(2, 0), *pz1 = phi + phi_base<T>(2, 1);  // z faces: comps x, y
-    const int xl = G::xf(i, j, k), yl = (k * 9 + j) * 8 + i, zl = (k * 8 + j) * 8 + i;
-    dx = (py0[yl + 8] - py0[yl]) + (pz0[zl + 64] - pz0[zl]);
-    dy = (px0[xl + 1] - px0[xl]) + (pz1[zl + 64] - pz1[zl]);
+    const int xl = G::xf(i, j, k), yl = (k * 9 + j) * 8 + i, zl = G::zf(i, j, k);
+    dx = (py0[yl + 8] - py0[yl]) + (pz0[zl + G::PZ] - pz0[zl]);
+    dy = (px0[xl + 1] - px0[xl]) + (pz1[zl + G::PZ] - pz1[zl]);
     dz = (px1[xl + 1] - px1[xl]) + (py1[yl + 8] - py1[yl]);
 }
 
@@ -267,7 +289,7 @@ __device__ __forceinline__ int plane_face(int a, int hi, int comp, int u, int v)
     using G = Geo<T>;
     if (a == 0) return phi_base<T>(0, comp) + G::xf(hi ? 8 : 0, u, v);
     if (a == 1) return phi_base<T>(1, comp) + (v * 9 + (hi ? 8 : 0)) * 8 + u;
-    return phi_base<T>(2, comp) + ((hi ? 8 : 0) * 8 + v) * 8 + u;
+    return phi_base<T>(2, comp) + G::zf(u, v, hi ? 8 : 0);
 }
 
 // Block-wide sum / max in a fixed order (deterministic); the result is valid in thread 0.
@@ -363,14 +385,16 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
         }
     }
     __syncthreads();
-    const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    int i, j, k;
+    cell_of_thread<TC>(threadIdx.x, i, j, k);
+    const int cell = (k * 8 + j) * 8 + i;
     TC dv[3];
     cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
     TC sr = 0, ss = 0, mx = 0;
     const int p = G::at(i + 1, j + 1, k + 1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        size_t id = ((size_t)b * 3 + c) * B3 + t;
+        size_t id = ((size_t)b * 3 + c) * B3 + cell;
         TC y = Y ? Y[id] : TC(0);
         TC o = a * tB[c * G::CS + p] + coef * dv[c] + d * y;
         if (outS) {  // o is the source; the residual of X against it is coef2 divF(X)
@@ -860,15 +884,17 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 1) k_resid_restrict(
     all_faces_512(tB, tE, phi);
     __syncthreads();
     {
-        const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+        int i, j, k;
+        cell_of_thread<T>(threadIdx.x, i, j, k);
+        const int cell = (k * 8 + j) * 8 + i;
         T dv[3];
         cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
         const int p = G::at(i + 1, j + 1, k + 1);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            size_t id = ((size_t)b * 3 + c) * B3 + t;
+            size_t id = ((size_t)b * 3 + c) * B3 + cell;
             T v = r[id] - tB[c * G::CS + p] - coef * dv[c];
-            tt[c * B3 + t] = v;
+            tt[c * B3 + cell] = v;
             if (t_out) t_out[id] = v;
         }
     }

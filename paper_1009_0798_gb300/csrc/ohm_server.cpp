@@ -80,6 +80,7 @@ struct ohm_server {
     std::vector<std::thread> workers;
     ohm_server_stats st{};
     double active_sum = 0;
+    int64_t launches_freed = 0;  // launches of batches already destroyed
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -121,7 +122,8 @@ int64_t batch_bytes(ohm_server *S, const Req *r, int K) {
     return b;
 }
 
-void free_batch(Batch *b) {
+void free_batch(Batch *b, int64_t *launches = nullptr) {
+    if (b->h && launches) *launches += ohm_launch_count(b->h);
     if (b->h) ohm_destroy(b->h);
     if (b->Bd) cudaFree(b->Bd);
     if (b->etad) cudaFree(b->etad);
@@ -301,8 +303,10 @@ void worker(ohm_server *S) {
                         break;
                     }
                 lk.unlock();
-                free_batch(owned.get());
+                int64_t n = 0;
+                free_batch(owned.get(), &n);
                 lk.lock();
+                S->launches_freed += n;
             }
             if (S->resident + need > S->d.hbm_budget_bytes) {
                 // the running batches hold the memory: wait for one to go idle
@@ -446,6 +450,9 @@ int ohm_server_get_stats(ohm_server *S, ohm_server_stats *st) {
     *st = S->st;
     st->bytes_resident = S->resident;
     st->mean_active_slots = S->st.steps_run ? S->active_sum / (double)S->st.steps_run : 0.0;
+    st->kernel_launches = S->launches_freed;
+    for (auto &b : S->batches)
+        if (b->h) st->kernel_launches += ohm_launch_count(b->h);
     return OHM_OK;
 }
 

@@ -35,7 +35,7 @@ class RequestResult(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("requests_done", C.c_int64), ("batches_created", C.c_int64), ("batches_evicted", C.c_int64),
                 ("bytes_resident", C.c_int64), ("bytes_resident_max", C.c_int64), ("steps_run", C.c_int64),
-                ("mean_active_slots", C.c_double)]
+                ("mean_active_slots", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 _bound = False
