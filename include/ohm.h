@@ -212,6 +212,7 @@ int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double
 #define OHM_K_UPDATE         6  /* B += e                                                     */
 #define OHM_K_BOTTOM         7  /* coarsest-grid V-cycle (one thread block)                   */
 #define OHM_K_NORM           8  /* norm reduction                                             */
+#define OHM_K_KRYLOV         9  /* FGMRES vector kernels (multi-dot, multi-axpy)              */
 
 /* From now on, bracket every launch of `kernel` that covers at least min_blocks blocks with
  * a pair of CUDA events on the hierarchy's stream, up to max_launches launches (events are

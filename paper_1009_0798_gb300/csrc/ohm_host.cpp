@@ -51,6 +51,7 @@ struct HGrid {
     int slot0 = 0, nslot = 0;
     int inst_nblk = 0;          // batches: blocks per instance
     bool brick = false;         // blocks pair up as x-neighbours (2q, 2q+1), every neighbour present
+    bool octet = false;         // the children of coarser-grid block c are blocks 8c .. 8c+7
     GridDev dev;
     int find(int i, int j, int k) const {
         auto it = index.find(key3(wrapi(i, nb[0]), wrapi(j, nb[1]), wrapi(k, nb[2])));
@@ -601,6 +602,14 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
         k += 10;
     }
     H->d_rsrc = (int *)(H->rsrc_tab.empty() ? nullptr : base + offs[k]);
+    // grids whose coarser multigrid grid holds their octets in order (Morton-ordered complete grids)
+    auto set_octet = [](HGrid &f, const HGrid &c) {
+        f.octet = f.n() == 8 * c.n() && c.nslot == 0 && !c.nbr.empty() &&
+                  std::none_of(c.nbr.begin(), c.nbr.end(), [](int v) { return v < 0; });
+        for (int b = 0; f.octet && b < f.n(); b++) f.octet = f.parent[b] == (b >> 3) && f.octant[b] == (b & 7);
+    };
+    if (!H->mg.empty()) set_octet(H->amr[0], H->mg[0]);
+    for (size_t m = 0; m + 1 < H->mg.size(); m++) set_octet(H->mg[m], H->mg[m + 1]);
     return OHM_OK;
 }
 
@@ -774,7 +783,10 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
                                     nullptr, (T *)C.r, nullptr, nullptr, H->s));
         CK(cudaMemsetAsync(C.e, 0, (size_t)C.g->n() * 3 * B3 * sizeof(T), H->s));
         if ((st = base_vcycle<T>(H, m + 1, lamdt))) return st;
-        LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
+        if (G.g->octet)
+            LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add8<T>(gdev(H, *C.g), (const T *)C.e, (T *)G.e, H->s));
+        else
+            LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), &C.g->dev, (const T *)C.e, nullptr, nullptr, (T *)G.e, H->d_err, H->s));
     } else {
         LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, nullptr, (T *)H->smallbuf[0].r, H->small[0].data(), H->s));
@@ -966,7 +978,7 @@ double inner_floor(const ohm_hier *H) { return H->d.inner_tol > 0 ? H->d.inner_t
 
 // Weighted inner products <w, v_i> (i < S.k) and <w, w>, read back to the host.
 int mdot(ohm_hier *H, const float *w, const VecSet &S, double *out) {
-    LAUNCH(H, OHM_K_NORM, 0, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s));
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s));
     CK(cudaMemcpyAsync(H->hdots, H->kdots, (S.k + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
     CK(cudaStreamSynchronize(H->s));
     memcpy(out, H->hdots, (S.k + 1) * sizeof(double));
@@ -1001,7 +1013,7 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
     const double beta0 = std::sqrt(nn[0]);
     if (!(beta0 > 0) || !std::isfinite(beta0)) return OHM_OK;
     double beta = beta0, beta_restart = beta0;
-    CK(launch_maxpy(H->kv[0], rhs, none, (float)(1.0 / beta), nel, H->s));
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[0], rhs, none, (float)(1.0 / beta), nel, H->s));
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     auto h = [&](int i, int j) -> double & { return Hm[(size_t)i * m + j]; };
     for (;;) {
@@ -1039,12 +1051,12 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             double hn;
             if (ww - proj > 0.01 * ww) {
                 hn = std::sqrt(ww - proj);
-                CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, (float)(1.0 / hn), nel, H->s));
+                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, (float)(1.0 / hn), nel, H->s));
             } else {
-                CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, 1.0f, nel, H->s));
+                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, 1.0f, nel, H->s));
                 if ((st = mdot(H, H->kv[j + 1], none, nn))) return st;
                 hn = std::sqrt(std::max(nn[0], 0.0));
-                if (hn > 0) CK(launch_maxpy(H->kv[j + 1], H->kv[j + 1], none, (float)(1.0 / hn), nel, H->s));
+                if (hn > 0) LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[j + 1], H->kv[j + 1], none, (float)(1.0 / hn), nel, H->s));
             }
             h(j + 1, j) = hn;
             // Givens rotations
@@ -1079,7 +1091,7 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
                 Z.v[i] = H->kz[i];
                 Z.c[i] = (float)(-y[i]);
             }
-            CK(launch_maxpy(x, x, Z, 1.0f, nel, H->s));
+            LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(x, x, Z, 1.0f, nel, H->s));
         }
         if (done || *cycles >= H->d.max_outer || jend == 0) break;
         // restart from the true residual rhs - L x
@@ -1088,7 +1100,7 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
         beta = std::sqrt(std::max(nn[0], 0.0));
         if (beta <= target * beta0 || !(beta > 0) || beta > 0.5 * beta_restart) break;
         beta_restart = beta;
-        CK(launch_maxpy(H->kv[0], H->kv[0], none, (float)(1.0 / beta), nel, H->s));
+        LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[0], H->kv[0], none, (float)(1.0 / beta), nel, H->s));
     }
     return OHM_OK;
 }
@@ -1243,7 +1255,7 @@ int batch_scale(ohm_hier *H, const double *dt) {
 // ---- batched FGMRES: one Arnoldi recurrence per instance, every launch covering the batch
 // Per-instance products <w, v_i> (i < S.k) and <w, w>, read back to the host: out[q][0..k].
 int mdot_inst(ohm_hier *H, const float *w, const VecSet &S, std::vector<double> &out) {
-    LAUNCH(H, OHM_K_NORM, 0,
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks,
            launch_mdot_inst(w, S, H->wblk, (int)H->nblocks, H->ranges, H->K, H->kpart, H->kdots, H->s));
     CK(cudaMemcpyAsync(H->hdotsK, H->kdots, (size_t)H->K * (KMAX + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
     CK(cudaStreamSynchronize(H->s));
@@ -1261,7 +1273,7 @@ int maxpy_inst(ohm_hier *H, float *dst, const float *src, const VecSet &S, const
         H->hcoef[(size_t)q * (KMAX + 1) + KMAX] = sc[q];
     }
     CK(cudaMemcpyAsync(H->kcoef, H->hcoef, (size_t)K * (KMAX + 1) * sizeof(float), cudaMemcpyHostToDevice, H->s));
-    LAUNCH(H, OHM_K_UPDATE, 0, launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s));
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s));
     // the pinned coefficients are rewritten by the next call: wait for this copy
     CK(cudaStreamSynchronize(H->s));
     return OHM_OK;

@@ -94,6 +94,11 @@ template <typename T>
 cudaError_t launch_prolong_add(const GridDev &g, const GridDev *gc, const T *coarse,
                                const T *lex, const int *ldims, T *fine, int *err, cudaStream_t s);
 
+// the same for a coarse grid gc whose blocks' children are the fine blocks 8c .. 8c+7 in
+// octant order (one thread block per coarse block)
+template <typename T>
+cudaError_t launch_prolong_add8(const GridDev &gc, const T *coarse, T *fine, cudaStream_t s);
+
 // plain restriction of ncomp components (eta chain): blocked fine -> blocked or lex coarse
 template <typename T>
 cudaError_t launch_restrict(const GridDev &g, const T *fine, int ncomp, T *coarse, T *lex,

@@ -1042,6 +1042,53 @@ template cudaError_t launch_prolong_add<double>(const GridDev &, const GridDev *
 template cudaError_t launch_prolong_add<float>(const GridDev &, const GridDev *, const float *, const float *,
                                                const int *, float *, int *, cudaStream_t);
 
+// Prolongation for a coarse grid whose blocks' 8 children are the fine blocks 8c .. 8c+7 in
+// octant order (Morton-ordered complete grids): one thread block per coarse block stages the
+// coarse block and its 1-cell halo once (10^3, as the stencil kernels do) and adds the
+// trilinear interpolant (3/4, 1/4 per axis, the weights of k_prolong_add) to all 4096 cells of
+// the 8 children, one child block per pass of its 512 threads.
+template <typename T>
+__global__ void __launch_bounds__(512) k_prolong_add8(GridDev gc, const T *__restrict__ coarse, T *__restrict__ fine) {
+    using G = Geo<T>;
+    __shared__ __align__(16) T tC[3 * G::CS];
+    __shared__ int snb[27];
+    const int c = blockIdx.x;
+    if (skip_block(gc, c)) return;
+    stage_nbr(snb, gc.nbr, c);
+    __syncthreads();
+    stage_rows<T, 3, 1, G::RS, G::OFF>(tC, coarse, snb, nullptr);
+    __syncthreads();
+    const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+    for (int o = 0; o < 8; o++) {
+        const int fx = lx + 8 * (o & 1), fy = ly + 8 * ((o >> 1) & 1), fz = lz + 8 * (o >> 2);
+        const int cx = fx >> 1, cy = fy >> 1, cz = fz >> 1;
+        const int sx = (fx & 1) ? 1 : -1, sy = (fy & 1) ? 1 : -1, sz = (fz & 1) ? 1 : -1;
+        const int p = G::at(cx + 1, cy + 1, cz + 1);
+        const size_t fb = ((size_t)(8 * c + o) * 3) * B3 + t;
+#pragma unroll
+        for (int comp = 0; comp < 3; comp++) {
+            const T *w = tC + comp * G::CS;
+            T v = 0;
+            for (int ak = 0; ak < 2; ak++)
+                for (int aj = 0; aj < 2; aj++)
+                    for (int ai = 0; ai < 2; ai++) {
+                        const T wt = (ai ? T(0.25) : T(0.75)) * (aj ? T(0.25) : T(0.75)) * (ak ? T(0.25) : T(0.75));
+                        v += wt * w[p + ak * sz * G::PS + aj * sy * G::RS + ai * sx];
+                    }
+            fine[fb + (size_t)comp * B3] += v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_prolong_add8(const GridDev &gc, const T *coarse, T *fine, cudaStream_t s) {
+    if (gc.nblk == 0) return cudaSuccess;
+    k_prolong_add8<T><<<gc.nblk, 512, 0, s>>>(gc, coarse, fine);
+    return cudaGetLastError();
+}
+template cudaError_t launch_prolong_add8<double>(const GridDev &, const double *, double *, cudaStream_t);
+template cudaError_t launch_prolong_add8<float>(const GridDev &, const float *, float *, cudaStream_t);
+
 // ------------------------------------------------------------------ coarse-fine ghosts
 // Ghost slot of a level-l block: every halo cell gets the tri-quadratic interpolant of the
 // parent's 3x3x3 coarse neighbourhood at the child's centre (offset s h_c/4 per axis):
@@ -1314,45 +1361,54 @@ template cudaError_t launch_convert<double, double>(const double *, double *, si
 // ------------------------------------------------------------------ Krylov vector kernels
 // Vectors are block fields [nblk][3][512]; inner products are volume weighted over leaf
 // blocks (weight w_b = h^3, 0 for covered blocks), the norm of the convergence tests.
+// The number of vectors NV is a template parameter (one instantiation per count, chosen at
+// launch), so a thread holds exactly NV + 1 partial sums: with a run-time count the compiler
+// kept the 13 sums of the largest case, which cost occupancy (76 registers).
 // One warp per 8^3 block: each lane forms 12 float4 products per column in float32, the warp
-// reduces them by shuffles, the sum is weighted in float64; the 8 warps of a thread block are
-// folded in warp order into part[blockIdx][col] (fixed order: deterministic).
-__global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
-                                              int nblk, double *__restrict__ part) {
-    __shared__ double sred[8][KMAX + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x * 8 + warp;
-    const int ncol = V.k + 1;
-    float f[KMAX + 1];
+// reduces them by shuffles and lane 0 weights the sum in float64.
+template <int NV>
+__device__ __forceinline__ void warp_block_dots(const float *__restrict__ w, const VecSet &V, int b, int lane,
+                                                double wt, double out[NV + 1]) {
+    float f[NV + 1];
 #pragma unroll
-    for (int i = 0; i <= KMAX; i++) f[i] = 0.f;
-    const double wt = b < nblk ? wb[b] : 0.0;
+    for (int i = 0; i <= NV; i++) f[i] = 0.f;
     if (wt != 0.0) {
         const float4 *w4 = reinterpret_cast<const float4 *>(w + (size_t)b * 1536);
-#pragma unroll 4
+#pragma unroll 1
         for (int s = 0; s < 12; s++) {
             const float4 x = w4[lane + 32 * s];
-            f[KMAX] += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+            f[NV] += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
 #pragma unroll
-            for (int i = 0; i < KMAX; i++)
-                if (i < V.k) {
-                    const float4 v = reinterpret_cast<const float4 *>(V.v[i] + (size_t)b * 1536)[lane + 32 * s];
-                    f[i] += x.x * v.x + x.y * v.y + x.z * v.z + x.w * v.w;
-                }
+            for (int i = 0; i < NV; i++) {
+                const float4 v = reinterpret_cast<const float4 *>(V.v[i] + (size_t)b * 1536)[lane + 32 * s];
+                f[i] += x.x * v.x + x.y * v.y + x.z * v.z + x.w * v.w;
+            }
         }
     }
 #pragma unroll
-    for (int i = 0; i <= KMAX; i++) {
-        if (i > V.k) break;
-        float s = i == V.k ? f[KMAX] : f[i < KMAX ? i : KMAX];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sred[warp][i] = (double)s * wt;
+    for (int i = 0; i <= NV; i++) {
+        float v = f[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        out[i] = (double)v * wt;
     }
+}
+
+// the 8 warps of a thread block are folded in warp order into part[blockIdx][col]
+template <int NV>
+__global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
+                                              int nblk, double *__restrict__ part) {
+    __shared__ double sred[8][NV + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
+    double d[NV + 1];
+    warp_block_dots<NV>(w, V, b < nblk ? b : 0, lane, b < nblk ? wb[b] : 0.0, d);
+    if (lane == 0)
+        for (int i = 0; i <= NV; i++) sred[warp][i] = d[i];
     __syncthreads();
-    if (threadIdx.x < ncol) {
+    if (threadIdx.x <= NV) {
         double a = 0.0;
         for (int q = 0; q < 8; q++) a += sred[q][threadIdx.x];
-        part[(size_t)blockIdx.x * ncol + threadIdx.x] = a;
+        part[(size_t)blockIdx.x * (NV + 1) + threadIdx.x] = a;
     }
 }
 
@@ -1366,28 +1422,20 @@ __global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part,
     if (threadIdx.x == 0) out[c] = s;
 }
 
-cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
-                        cudaStream_t s) {
-    const int grid = (nblk + 7) / 8;
-    k_mdot<<<grid, 256, 0, s>>>(w, V, wb, nblk, part);
-    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out);
-    return cudaGetLastError();
-}
-
 // dst = (src - sum_i c_i v_i) * scale (dst may equal src); float4 over n/4 groups
+template <int NV>
 __global__ void __launch_bounds__(256) k_maxpy(float4 *dst, const float4 *src, VecSet V, float scale, size_t n4) {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
         float4 x = src[q];
 #pragma unroll
-        for (int i = 0; i < KMAX; i++)
-            if (i < V.k) {
-                const float4 v = reinterpret_cast<const float4 *>(V.v[i])[q];
-                const float c = V.c[i];
-                x.x -= c * v.x;
-                x.y -= c * v.y;
-                x.z -= c * v.z;
-                x.w -= c * v.w;
-            }
+        for (int i = 0; i < NV; i++) {
+            const float4 v = reinterpret_cast<const float4 *>(V.v[i])[q];
+            const float c = V.c[i];
+            x.x -= c * v.x;
+            x.y -= c * v.y;
+            x.z -= c * v.z;
+            x.w -= c * v.w;
+        }
         x.x *= scale;
         x.y *= scale;
         x.z *= scale;
@@ -1396,46 +1444,57 @@ __global__ void __launch_bounds__(256) k_maxpy(float4 *dst, const float4 *src, V
     }
 }
 
+// one instantiation per vector count 0 .. KMAX
+#define OHM_NV_SWITCH(k, CALL)   \
+    switch (k) {                 \
+        case 0: CALL(0); break;  \
+        case 1: CALL(1); break;  \
+        case 2: CALL(2); break;  \
+        case 3: CALL(3); break;  \
+        case 4: CALL(4); break;  \
+        case 5: CALL(5); break;  \
+        case 6: CALL(6); break;  \
+        case 7: CALL(7); break;  \
+        case 8: CALL(8); break;  \
+        case 9: CALL(9); break;  \
+        case 10: CALL(10); break; \
+        case 11: CALL(11); break; \
+        default: CALL(12); break; \
+    }
+
+cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
+                        cudaStream_t s) {
+    const int grid = (nblk + 7) / 8;
+#define OHM_MDOT(N) k_mdot<N><<<grid, 256, 0, s>>>(w, V, wb, nblk, part)
+    OHM_NV_SWITCH(V.k, OHM_MDOT)
+#undef OHM_MDOT
+    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s) {
     const size_t n4 = n / 4;  // fields are whole 8^3 blocks: n is a multiple of 1536
-    int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
-    k_maxpy<<<grid, 256, 0, s>>>(reinterpret_cast<float4 *>(dst), reinterpret_cast<const float4 *>(src), V, scale, n4);
+    const int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#define OHM_MAXPY(N) k_maxpy<N><<<grid, 256, 0, s>>>(d4, s4, V, scale, n4)
+    OHM_NV_SWITCH(V.k, OHM_MAXPY)
+#undef OHM_MAXPY
     return cudaGetLastError();
 }
 
 // Per-instance Krylov vector kernels of batched hierarchies.  Block partials: one warp per
 // block writes its weighted products (no folding across blocks, so no sum mixes instances).
+template <int NV>
 __global__ void __launch_bounds__(256) k_mdot_blocks(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
                                                      int nblk, double *__restrict__ part) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + warp;
     if (b >= nblk) return;
-    const int ncol = V.k + 1;
-    float f[KMAX + 1];
-#pragma unroll
-    for (int i = 0; i <= KMAX; i++) f[i] = 0.f;
-    const double wt = wb[b];
-    if (wt != 0.0) {
-        const float4 *w4 = reinterpret_cast<const float4 *>(w + (size_t)b * 1536);
-#pragma unroll 4
-        for (int s = 0; s < 12; s++) {
-            const float4 x = w4[lane + 32 * s];
-            f[KMAX] += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
-#pragma unroll
-            for (int i = 0; i < KMAX; i++)
-                if (i < V.k) {
-                    const float4 v = reinterpret_cast<const float4 *>(V.v[i] + (size_t)b * 1536)[lane + 32 * s];
-                    f[i] += x.x * v.x + x.y * v.y + x.z * v.z + x.w * v.w;
-                }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i <= KMAX; i++) {
-        if (i > V.k) break;
-        float v = i == V.k ? f[KMAX] : f[i < KMAX ? i : KMAX];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) part[(size_t)b * ncol + i] = (double)v * wt;
-    }
+    double d[NV + 1];
+    warp_block_dots<NV>(w, V, b, lane, wb[b], d);
+    if (lane == 0)
+        for (int i = 0; i <= NV; i++) part[(size_t)b * (NV + 1) + i] = d[i];
 }
 
 // out[q][c] = sum of part[b][c] over instance q's blocks of every level, in a fixed order
@@ -1456,13 +1515,16 @@ __global__ void __launch_bounds__(256) k_colsum_inst(const double *__restrict__ 
 
 cudaError_t launch_mdot_inst(const float *w, const VecSet &V, const double *wb, int nblk, const InstRanges &R, int ninst,
                              double *part, double *out, cudaStream_t s) {
-    k_mdot_blocks<<<(nblk + 7) / 8, 256, 0, s>>>(w, V, wb, nblk, part);
+#define OHM_MDOTB(N) k_mdot_blocks<N><<<(nblk + 7) / 8, 256, 0, s>>>(w, V, wb, nblk, part)
+    OHM_NV_SWITCH(V.k, OHM_MDOTB)
+#undef OHM_MDOTB
     k_colsum_inst<<<ninst, 256, 0, s>>>(part, R, V.k + 1, out);
     return cudaGetLastError();
 }
 
 // dst = (src - sum_i c[q][i] v_i) * c[q][KMAX] with q the instance of the element's block;
 // terms whose coefficient is 0 are skipped (their vectors may hold anything for that instance)
+template <int NV>
 __global__ void __launch_bounds__(256) k_maxpy_inst(float4 *dst, const float4 *src, VecSet V,
                                                     const float *__restrict__ coef, const int *__restrict__ binst,
                                                     size_t n4) {
@@ -1470,17 +1532,16 @@ __global__ void __launch_bounds__(256) k_maxpy_inst(float4 *dst, const float4 *s
         const float *cq = coef + (size_t)binst[e / 384] * (KMAX + 1);
         float4 x = src[e];
 #pragma unroll
-        for (int i = 0; i < KMAX; i++)
-            if (i < V.k) {
-                const float c = cq[i];
-                if (c != 0.f) {
-                    const float4 v = reinterpret_cast<const float4 *>(V.v[i])[e];
-                    x.x -= c * v.x;
-                    x.y -= c * v.y;
-                    x.z -= c * v.z;
-                    x.w -= c * v.w;
-                }
+        for (int i = 0; i < NV; i++) {
+            const float c = cq[i];
+            if (c != 0.f) {
+                const float4 v = reinterpret_cast<const float4 *>(V.v[i])[e];
+                x.x -= c * v.x;
+                x.y -= c * v.y;
+                x.z -= c * v.z;
+                x.w -= c * v.w;
             }
+        }
         const float sc = cq[KMAX];
         x.x *= sc;
         x.y *= sc;
@@ -1493,9 +1554,12 @@ __global__ void __launch_bounds__(256) k_maxpy_inst(float4 *dst, const float4 *s
 cudaError_t launch_maxpy_inst(float *dst, const float *src, const VecSet &V, const float *coef, const int *binst,
                               size_t n, cudaStream_t s) {
     const size_t n4 = n / 4;
-    int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
-    k_maxpy_inst<<<grid, 256, 0, s>>>(reinterpret_cast<float4 *>(dst), reinterpret_cast<const float4 *>(src), V, coef,
-                                      binst, n4);
+    const int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#define OHM_MAXPYI(N) k_maxpy_inst<N><<<grid, 256, 0, s>>>(d4, s4, V, coef, binst, n4)
+    OHM_NV_SWITCH(V.k, OHM_MAXPYI)
+#undef OHM_MAXPYI
     return cudaGetLastError();
 }
 

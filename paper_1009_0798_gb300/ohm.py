@@ -20,7 +20,7 @@ OHM_ERR_CUDA = -5
 OHM_FP64 = 0
 OHM_MIXED = 1
 OHM_K_COMPOSITE, OHM_K_SMOOTH, OHM_K_RESID_RESTRICT, OHM_K_PROLONG, OHM_K_GHOST = 0, 1, 2, 3, 4
-OHM_K_SYNC_DOWN, OHM_K_UPDATE, OHM_K_BOTTOM, OHM_K_NORM = 5, 6, 7, 8
+OHM_K_SYNC_DOWN, OHM_K_UPDATE, OHM_K_BOTTOM, OHM_K_NORM, OHM_K_KRYLOV = 5, 6, 7, 8, 9
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libohm.so")
 
