@@ -115,3 +115,22 @@ def test_batched_fp64_fixed_schedule_elementwise_sampled(ohm, batch512, oracle_m
     for q in (0, len(lst) // 2, len(lst) - 1):
         want, _ = oracle_mod.Oracle(h, 0.5, lst[q].eta).cn_step(lst[q].B, lst[q].dt, -1.0, 2, 2, 16, 3)
         assert rel_err(got[q], want) < 1e-12, q
+
+
+def test_largest_grid_512(ohm, oracle_mod):
+    """The largest uniform grid this suite runs (512^3 = 134 M cells, 262,144 blocks; about 20 GB
+    of device memory in mixed precision): one step of the resistive bump converges, and the
+    oracle re-evaluates the residual of the GPU's answer."""
+    wl = W.resistive_bump_256(n=512)
+    g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam, precision=ohm.OHM_MIXED,
+                                 nu_pre=2, nu_post=2, n_coarse=16, max_outer=300, krylov=6)
+    B = dev(wl.B)
+    st = ohm.ohm_cn_step(g, B, dev(wl.eta), wl.dt, wl.tol)
+    assert st["converged"] and st["rel_l2"] <= wl.tol
+    got = B.cpu().numpy().reshape(wl.B.shape)
+    del B
+    g.close()
+    o = oracle_mod.Oracle(wl.hier, wl.lam, wl.eta)
+    S = o.source(wl.B, wl.dt)
+    _, norms = o.residual(got, S, wl.dt)
+    assert norms["rel_l2"] <= 1.05 * wl.tol
