@@ -326,7 +326,7 @@ __device__ __forceinline__ T block_max(T v, T *red) {
 // ------------------------------------------------------------------ composite operator
 // Computed in TC (float64 for the outer residual and the source, float32 for the inner
 // residual of mixed precision); refluxed fluxes travel through float64 registers.
-template <typename TC, typename TO>
+template <typename TC, typename TO, bool NORMS>
 __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(GridDev g, const TC *__restrict__ X, const TC *__restrict__ Y,
                                                    const TC *__restrict__ eta, const TC *__restrict__ Gx,
                                                    const TC *__restrict__ Geta, TC a, TC coef, TC d,
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
     const int b = blockIdx.x;
     if (skip_block(g, b)) return;
     if (g.covered && g.covered[b]) {
-        if (partials && threadIdx.x < 3) partials[b * 3 + threadIdx.x] = 0.0;
+        if (NORMS && threadIdx.x < 3) partials[b * 3 + threadIdx.x] = 0.0;
         return;
     }
     const int slot = g.gslot ? g.gslot[b] : -1;
@@ -397,20 +397,20 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
         size_t id = ((size_t)b * 3 + c) * B3 + cell;
         TC y = Y ? Y[id] : TC(0);
         TC o = a * tB[c * G::CS + p] + coef * dv[c] + d * y;
-        if (outS) {  // o is the source; the residual of X against it is coef2 divF(X)
+        if (sizeof(TC) == 8 && outS) {  // o is the source; the residual of X against it is coef2 divF(X)
             outS[id] = (double)o;
             y = o;
             o = coef2 * dv[c];
         }
         out[id] = (TO)o;
         if (out2) out2[id] = (TO)o;
-        if (partials) {
+        if constexpr (NORMS) {
             sr += o * o;
             ss += y * y;
             mx = fmax(mx, fabs(o));
         }
     }
-    if (partials) {
+    if constexpr (NORMS) {
         TC s1 = block_sum(sr, red);
         TC s2 = block_sum(ss, red);
         TC s3 = block_max(mx, red);
@@ -429,11 +429,18 @@ cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const T
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = (4 * Geo<TC>::CS + Geo<TC>::PHI) * sizeof(TC);
     // set once per process (thread-safe static initialisation)
-    static const bool attr = (cudaFuncSetAttribute(k_composite<TC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
+    static const bool attr = (cudaFuncSetAttribute(k_composite<TC, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              cudaFuncSetAttribute(k_composite<TC, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              true);
     (void)attr;
     double coef = c / (2.0 * g.h * g.h);
-    k_composite<TC, TO><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg, rsrc_tab,
-                                                partials, vol, outS, (TC)(c2 / (2.0 * g.h * g.h)));
+    const TC coef2 = (TC)(c2 / (2.0 * g.h * g.h));
+    if (partials)  // with norm partials (the block reductions are compiled out otherwise)
+        k_composite<TC, TO, true><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg,
+                                                          rsrc_tab, partials, vol, outS, coef2);
+    else
+        k_composite<TC, TO, false><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg,
+                                                           rsrc_tab, partials, vol, outS, coef2);
     return cudaGetLastError();
 }
 #define INST_COMPOSITE(TC, TO)                                                                                        \
