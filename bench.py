@@ -45,7 +45,7 @@ def args_parse():
     p.add_argument("--only", choices=["fgmres", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
     p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
-    p.add_argument("--n-coarse", type=int, default=16, help="sweeps on the coarsest grid")
+    p.add_argument("--n-coarse", type=int, default=4, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
     p.add_argument("--workload", choices=["resistive_bump", "batched512", "serving"], default="resistive_bump",
                    help="resistive_bump: the headline 256^3 line; batched512: 512 independent instances "

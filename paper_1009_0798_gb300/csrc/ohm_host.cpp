@@ -851,11 +851,22 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
         const HGrid &g = H->amr[l];
         double vol = g.h * g.h * g.h;
         const size_t o3 = (size_t)g.off * 3 * B3;
-        LAUNCH(H, OHM_K_COMPOSITE, g.n(),
-               (launch_composite<TC, TO>(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta, a, c,
-                                         dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
-                                         norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s,
-                                         outS ? outS + o3 : nullptr, c2)));
+        if constexpr (std::is_same<TC, double>::value && std::is_same<TO, float>::value) {
+            // outer residual of the mixed path: float-float arithmetic, Y and outS hold the
+            // source in float-float form
+            LAUNCH(H, OHM_K_COMPOSITE, g.n(),
+                   (launch_composite_df(gdev(H, g), X + o3, Y ? reinterpret_cast<const dfloat *>(Y) + o3 : nullptr,
+                                        eta + (size_t)g.off * B3, Gx, Geta, a, c, dcoef, out + o3,
+                                        out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
+                                        norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s,
+                                        outS ? reinterpret_cast<dfloat *>(outS) + o3 : nullptr, c2)));
+        } else {
+            LAUNCH(H, OHM_K_COMPOSITE, g.n(),
+                   (launch_composite<TC, TO>(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta,
+                                             a, c, dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
+                                             norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s,
+                                             outS ? outS + o3 : nullptr, c2)));
+        }
     }
     if (norms) {
         if (H->batched)

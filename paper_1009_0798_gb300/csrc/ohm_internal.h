@@ -67,6 +67,27 @@ cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const T
                              double *reg, const int *rsrc_tab, double *partials, double vol,
                              cudaStream_t s, double *outS = nullptr, double c2 = 0.0);
 
+// Float-float number: the unevaluated sum hi + lo of two float32 values (about 48 significant
+// bits).  The mixed-precision path evaluates its outer residual in this arithmetic on the
+// float32 pipe and keeps the source S of a step in this form (8 bytes per value, like float64).
+struct alignas(8) dfloat {
+    float hi, lo;
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    constexpr explicit dfloat(float h = 0.f, float l = 0.f) : hi(h), lo(l) {}
+};
+
+// launch_composite for the outer residual of the mixed path: X, eta and the ghosts are float64
+// fields, split into float-float values when staged; Y and outS are the source in float-float
+// form; out / out2 are float32 (the inner solve's right-hand side).  Float-float arithmetic
+// keeps the error of R = S - L X near 2^-48 (1 + lambda dt |divF| / |X|) |X|, which bounds the
+// relative residual the mixed path can certify; norm partials are accumulated in float32.
+cudaError_t launch_composite_df(const GridDev &g, const double *X, const dfloat *Y, const double *eta,
+                                const double *Gx, const double *Geta, double a, double c, double d, float *out,
+                                float *out2, double *reg, const int *rsrc_tab, double *partials, double vol,
+                                cudaStream_t s, dfloat *outS, double c2);
+
 template <typename T>
 cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta,
                           const T *inv, const T *Ge, const T *Geta, double lamdt, int colour,

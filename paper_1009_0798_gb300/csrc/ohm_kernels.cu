@@ -25,6 +25,94 @@ __device__ __forceinline__ bool skip_block(const GridDev &g, int b) {
     return g.imask && !g.imask[g.inst_nblk ? b / g.inst_nblk : 0];
 }
 
+// ------------------------------------------------------------------ float-float arithmetic
+// GB300 issues float64 at 1/58 of the float32 rate, so the outer residual of the mixed path
+// runs on pairs of float32 values instead (Dekker 1971).  Every operation uses the explicitly
+// rounded intrinsics, which the compiler never fuses into FMAs, so the error-free
+// transformations stay exact:
+//   two_sum (Knuth): s = fl(a + b) and the exact error of that addition;
+//   fast_two_sum (Dekker): the same when |a| >= |b| (or a = 0), in three operations;
+//   products: fl(a.hi b.hi) and its exact error from an FMA, plus the cross terms.
+// Sums fold the trailing parts in before one renormalisation.  Their error is at most about
+// 2^-47 (|a| + |b|): bounded against the operands, not the result, which is the measure the
+// residual needs (its cancellation error is measured against |X|).
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dfloat(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+    const dfloat s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+// float64 -> float-float by bit manipulation (no float64 instruction): hi carries the sign,
+// the exponent and the leading 24 significand bits (truncated), lo the remaining 29 bits
+// rounded to 24, so hi + lo keeps about 48 of the 53 bits.  Magnitudes outside the normal
+// float32 range are converted to float32 with lo = 0 (NaN and infinity keep their class,
+// finite values beyond 2^128 become infinite, values below 2^-126 lose precision).
+__device__ __forceinline__ dfloat split_double(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
+    const int e = (int)((uh >> 20) & 0x7ffu);  // biased float64 exponent
+    const int fe = e - (1023 - 127);           // the same exponent biased for float32
+    if ((unsigned)(fe - 1) >= 254u) return dfloat(__double2float_rn(x));
+    const unsigned int sgn = uh & 0x80000000u;
+    const float hi = __uint_as_float(sgn | ((unsigned)fe << 23) | ((uh & 0xfffffu) << 3) | (ul >> 29));
+    // lo = r 2^(e - 1075) for the 29 low significand bits r; below 2^-126 the power of two is
+    // applied in two exact steps, 2^(e - 1075 + 64) 2^-64, each in the normal float32 range
+    const int k = e < 1075 - 126 ? 64 : 0;
+    const float s1 = __uint_as_float((unsigned)(e - 1075 + k + 127) << 23);
+    const float s2 = __uint_as_float((unsigned)(127 - k) << 23);
+    const float lo = __fmul_rn(__fmul_rn(__uint2float_rn(ul & 0x1fffffffu), s1), s2);
+    return dfloat(hi, sgn ? -lo : lo);
+}
+
+// Conversions used outside the float-float hot loop (flux registers, refluxing)
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(dfloat v) { return (double)v.hi + (double)v.lo; }
+template <typename T>
+__device__ __forceinline__ T from_double(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ dfloat from_double<dfloat>(double v) {
+    const float h = __double2float_rn(v);
+    return dfloat(h, __double2float_rn(v - (double)h));
+}
+// staged tile value from a field value (float64 fields split for float-float tiles)
+template <typename T, typename TS>
+__device__ __forceinline__ T tile_val(TS v) {
+    static_assert(sizeof(T) == sizeof(TS), "tile and field types differ in size");
+    return v;
+}
+template <>
+__device__ __forceinline__ dfloat tile_val<dfloat, double>(double v) { return split_double(v); }
+// x / 4 (exact for every type)
+__device__ __forceinline__ float quarter(float v) { return 0.25f * v; }
+__device__ __forceinline__ double quarter(double v) { return 0.25 * v; }
+__device__ __forceinline__ dfloat quarter(dfloat v) { return dfloat(0.25f * v.hi, 0.25f * v.lo); }
+// leading value (the float32 or float64 approximation used for outputs and norms)
+__device__ __forceinline__ float lead(float v) { return v; }
+__device__ __forceinline__ double lead(double v) { return v; }
+__device__ __forceinline__ float lead(dfloat v) { return v.hi; }
+template <typename X>
+struct Ident {
+    using type = X;
+};
+
 // Shared-memory geometry of a staged 10^3 tile (block + 1-cell halo).  Rows along x are RS
 // elements apart; PX is the row stride of the x-face flux array; tile x index ti sits at row
 // offset OFF + ti.  float32 rows of 12 with OFF = 1 put the 8 interior cells of a row on an
@@ -41,6 +129,10 @@ struct G10<float> {
 };
 template <>
 struct G10<double> {
+    static constexpr int RS = 10, PX = 9, OFF = 0;
+};
+template <>
+struct G10<dfloat> {
     static constexpr int RS = 10, PX = 9, OFF = 0;
 };
 // z-face planes are PZ apart: 72 for float32 (= 8 mod 32 banks, like the x- and y-face arrays
@@ -87,25 +179,30 @@ __device__ __forceinline__ Row8<double> load_row8(const double *__restrict__ p) 
 // each end from the x-neighbours of that block.  Rows or cells of an absent neighbour come
 // from `ghost` ([NC][10^3] compact, HW = 1 only) or are zero.  Values at the corners of the
 // box are never read by the stencil and may be left stale.
-template <typename T>
-__device__ __forceinline__ void store_row8(T *dst, const Row8<T> &row, bool aligned16, bool aligned8 = false) {
-    if (sizeof(T) == 4 && aligned16) {
-        float4 *d4 = reinterpret_cast<float4 *>(dst);
-        d4[0] = make_float4((float)row.v[0], (float)row.v[1], (float)row.v[2], (float)row.v[3]);
-        d4[1] = make_float4((float)row.v[4], (float)row.v[5], (float)row.v[6], (float)row.v[7]);
-    } else if (sizeof(T) == 4 && aligned8) {
-        float2 *d2 = reinterpret_cast<float2 *>(dst);
+template <typename T, typename TS>
+__device__ __forceinline__ void store_row8(T *dst, const Row8<TS> &row, bool aligned16, bool aligned8 = false) {
+    if constexpr (sizeof(T) == 4) {
+        if (aligned16) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+            d4[0] = make_float4((float)row.v[0], (float)row.v[1], (float)row.v[2], (float)row.v[3]);
+            d4[1] = make_float4((float)row.v[4], (float)row.v[5], (float)row.v[6], (float)row.v[7]);
+            return;
+        }
+        if (aligned8) {
+            float2 *d2 = reinterpret_cast<float2 *>(dst);
 #pragma unroll
-        for (int q = 0; q < 4; q++) d2[q] = make_float2((float)row.v[2 * q], (float)row.v[2 * q + 1]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 8; q++) dst[q] = row.v[q];
+            for (int q = 0; q < 4; q++) d2[q] = make_float2((float)row.v[2 * q], (float)row.v[2 * q + 1]);
+            return;
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 8; q++) dst[q] = tile_val<T, TS>(row.v[q]);
 }
 
-template <typename T, int NC, int HW, int RS, int OFF = 0>
-__device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__restrict__ F, const int *__restrict__ snb,
-                                           const T *__restrict__ ghost) {
+// TS is the field's element type (T, or float64 for float-float tiles)
+template <typename T, int NC, int HW, int RS, int OFF = 0, typename TS = T>
+__device__ __forceinline__ void stage_rows(T *__restrict__ tile, const TS *__restrict__ F, const int *__restrict__ snb,
+                                           const typename Ident<TS>::type *__restrict__ ghost) {
     constexpr int S = 8 + 2 * HW, S2 = S * S;
     constexpr bool A16 = sizeof(T) == 4 && (OFF + HW) % 4 == 0 && RS % 4 == 0;
     constexpr bool A8 = sizeof(T) == 4 && (OFF + HW) % 2 == 0 && RS % 2 == 0;
@@ -116,15 +213,15 @@ __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__rest
         const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
         const int sj = lj - 8 * dj, sk = lk - 8 * dk;
         T *dst = tile + c * (S2 * RS) + rr * RS + OFF;
-        const T *gh = ghost ? ghost + c * T3 + rr * S : nullptr;
+        const TS *gh = ghost ? ghost + c * T3 + rr * S : nullptr;
         const int dcent = (dk + 1) * 9 + (dj + 1) * 3;
         const int src = snb[dcent + 1];
         if (src >= 0) {
-            const Row8<T> row = load_row8(F + ((size_t)src * NC + c) * B3 + (sk * 8 + sj) * 8);
+            const Row8<TS> row = load_row8(F + ((size_t)src * NC + c) * B3 + (sk * 8 + sj) * 8);
             store_row8(dst + HW, row, A16, A8);
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; q++) dst[HW + q] = gh ? gh[HW + q] : T(0);
+            for (int q = 0; q < 8; q++) dst[HW + q] = gh ? tile_val<T, TS>(gh[HW + q]) : T(0);
         }
         const int slo = snb[dcent], shi = snb[dcent + 2];
         if constexpr (sizeof(T) == 4 && HW == 2 && OFF % 2 == 0 && RS % 2 == 0) {
@@ -140,9 +237,10 @@ __device__ __forceinline__ void stage_rows(T *__restrict__ tile, const T *__rest
 #pragma unroll
         for (int h = 0; h < HW; h++) {
             // low end: cells 8-HW+h of the x- neighbour; high end: cells h of the x+ neighbour
-            dst[h] = slo >= 0 ? F[((size_t)slo * NC + c) * B3 + (sk * 8 + sj) * 8 + 8 - HW + h] : (gh ? gh[h] : T(0));
-            dst[HW + 8 + h] = shi >= 0 ? F[((size_t)shi * NC + c) * B3 + (sk * 8 + sj) * 8 + h]
-                                       : (gh ? gh[HW + 8 + h] : T(0));
+            dst[h] = slo >= 0 ? tile_val<T, TS>(F[((size_t)slo * NC + c) * B3 + (sk * 8 + sj) * 8 + 8 - HW + h])
+                              : (gh ? tile_val<T, TS>(gh[h]) : T(0));
+            dst[HW + 8 + h] = shi >= 0 ? tile_val<T, TS>(F[((size_t)shi * NC + c) * B3 + (sk * 8 + sj) * 8 + h])
+                                       : (gh ? tile_val<T, TS>(gh[HW + 8 + h]) : T(0));
         }
     }
 }
@@ -190,10 +288,10 @@ __device__ __forceinline__ void face_phi_s(const T *__restrict__ tB, const T *__
     const T *B2 = tB + b2 * cs;
     T n1 = B1[p + sa] - B1[p];
     T t1 = (Ba[p + sa + s1] + Ba[p + s1]) - (Ba[p + sa - s1] + Ba[p - s1]);
-    phi1 = es * (T(0.25) * t1 - n1);
+    phi1 = es * (quarter(t1) - n1);
     T n2 = B2[p + sa] - B2[p];
     T t2 = (Ba[p + sa + s2] + Ba[p + s2]) - (Ba[p + sa - s2] + Ba[p - s2]);
-    phi2 = es * (T(0.25) * t2 - n2);
+    phi2 = es * (quarter(t2) - n2);
 }
 
 // Faces of a 10^3 tile along axis a from the low tile cell p, in the geometry of T
@@ -324,22 +422,36 @@ __device__ __forceinline__ T block_max(T v, T *red) {
 }
 
 // ------------------------------------------------------------------ composite operator
-// Computed in TC (float64 for the outer residual and the source, float32 for the inner
-// residual of mixed precision); refluxed fluxes travel through float64 registers.
+// Computed in TC: float64 for the outer residual and the source of the float64 path, float-float
+// (dfloat, from float64 fields) for those of the mixed path, float32 for the inner residual of
+// mixed precision; refluxed fluxes travel through float64 registers.
+template <typename TC>
+struct CompTypes {
+    using In = TC;   // element type of X, eta and the ghosts
+    using Acc = TC;  // norm accumulation
+    static constexpr int minb = sizeof(TC) == 4 ? 4 : 1;
+};
+template <>
+struct CompTypes<dfloat> {
+    using In = double;
+    using Acc = float;
+    static constexpr int minb = 2;
+};
+
 template <typename TC, typename TO, bool NORMS>
-__global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(GridDev g, const TC *__restrict__ X, const TC *__restrict__ Y,
-                                                   const TC *__restrict__ eta, const TC *__restrict__ Gx,
-                                                   const TC *__restrict__ Geta, TC a, TC coef, TC d,
-                                                   TO *__restrict__ out, TO *__restrict__ out2,
-                                                   double *__restrict__ reg, const int *__restrict__ rsrc_tab,
-                                                   double *__restrict__ partials, double vol,
-                                                   double *__restrict__ outS, TC coef2) {
+__global__ void __launch_bounds__(512, CompTypes<TC>::minb)
+    k_composite(GridDev g, const typename CompTypes<TC>::In *__restrict__ X, const TC *__restrict__ Y,
+                const typename CompTypes<TC>::In *__restrict__ eta, const typename CompTypes<TC>::In *__restrict__ Gx,
+                const typename CompTypes<TC>::In *__restrict__ Geta, TC a, TC coef, TC d, TO *__restrict__ out,
+                TO *__restrict__ out2, double *__restrict__ reg, const int *__restrict__ rsrc_tab,
+                double *__restrict__ partials, double vol, TC *__restrict__ outS, TC coef2) {
     using G = Geo<TC>;
+    using TA = typename CompTypes<TC>::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC *tB = reinterpret_cast<TC *>(smem_raw);
     TC *tE = tB + 3 * G::CS;
     TC *phi = tE + G::CS;
-    __shared__ TC red[32];
+    __shared__ TA red[32];
     __shared__ int snb[27];
     const int b = blockIdx.x;
     if (skip_block(g, b)) return;
@@ -364,7 +476,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
             int ax = s >> 1, hi = s & 1;
             for (int q = threadIdx.x; q < 128; q += blockDim.x) {
                 int comp = q >> 6, uv = q & 63;
-                reg[(size_t)slotr * 128 + q] = (double)phi[plane_face<TC>(ax, hi, comp, uv & 7, uv >> 3)] * inv2h;
+                reg[(size_t)slotr * 128 + q] = to_double(phi[plane_face<TC>(ax, hi, comp, uv & 7, uv >> 3)]) * inv2h;
             }
         }
     }
@@ -380,7 +492,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
                 const double *R = reg + (size_t)fslot * 128 + comp * 64;
                 int fu = 2 * (u & 3), fv = 2 * (v & 3);
                 double m = 0.25 * ((R[fv * 8 + fu] + R[fv * 8 + fu + 1]) + (R[(fv + 1) * 8 + fu] + R[(fv + 1) * 8 + fu + 1]));
-                phi[plane_face<TC>(ax, hi, comp, u, v)] = (TC)(m * (2.0 * g.h));
+                phi[plane_face<TC>(ax, hi, comp, u, v)] = from_double<TC>(m * (2.0 * g.h));
             }
         }
     }
@@ -390,7 +502,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
     const int cell = (k * 8 + j) * 8 + i;
     TC dv[3];
     cell_div(phi, i, j, k, dv[0], dv[1], dv[2]);
-    TC sr = 0, ss = 0, mx = 0;
+    TA sr = 0, ss = 0, mx = 0;
     const int p = G::at(i + 1, j + 1, k + 1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -398,22 +510,24 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
         TC y = Y ? Y[id] : TC(0);
         TC o = a * tB[c * G::CS + p] + coef * dv[c] + d * y;
         if (sizeof(TC) == 8 && outS) {  // o is the source; the residual of X against it is coef2 divF(X)
-            outS[id] = (double)o;
+            outS[id] = o;
             y = o;
             o = coef2 * dv[c];
         }
-        out[id] = (TO)o;
-        if (out2) out2[id] = (TO)o;
+        const TA ol = lead(o);
+        out[id] = (TO)ol;
+        if (out2) out2[id] = (TO)ol;
         if constexpr (NORMS) {
-            sr += o * o;
-            ss += y * y;
-            mx = fmax(mx, fabs(o));
+            const TA yl = lead(y);
+            sr += ol * ol;
+            ss += yl * yl;
+            mx = fmax(mx, fabs(ol));
         }
     }
     if constexpr (NORMS) {
-        TC s1 = block_sum(sr, red);
-        TC s2 = block_sum(ss, red);
-        TC s3 = block_max(mx, red);
+        TA s1 = block_sum(sr, red);
+        TA s2 = block_sum(ss, red);
+        TA s3 = block_max(mx, red);
         if (threadIdx.x == 0) {
             partials[b * 3 + 0] = (double)s1 * vol;
             partials[b * 3 + 1] = (double)s2 * vol;
@@ -423,9 +537,11 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 4 : 1) k_composite(Grid
 }
 
 template <typename TC, typename TO>
-cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta,
-                             double a, double c, double d, TO *out, TO *out2, double *reg, const int *rsrc_tab,
-                             double *partials, double vol, cudaStream_t s, double *outS, double c2) {
+static cudaError_t launch_composite_t(const GridDev &g, const typename CompTypes<TC>::In *X, const TC *Y,
+                                     const typename CompTypes<TC>::In *eta, const typename CompTypes<TC>::In *Gx,
+                                     const typename CompTypes<TC>::In *Geta, TC a, TC coef, TC d, TO *out, TO *out2,
+                                     double *reg, const int *rsrc_tab, double *partials, double vol, cudaStream_t s,
+                                     TC *outS, TC coef2) {
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = (4 * Geo<TC>::CS + Geo<TC>::PHI) * sizeof(TC);
     // set once per process (thread-safe static initialisation)
@@ -433,22 +549,46 @@ cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const T
                               cudaFuncSetAttribute(k_composite<TC, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                               true);
     (void)attr;
-    double coef = c / (2.0 * g.h * g.h);
-    const TC coef2 = (TC)(c2 / (2.0 * g.h * g.h));
     if (partials)  // with norm partials (the block reductions are compiled out otherwise)
-        k_composite<TC, TO, true><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg,
-                                                          rsrc_tab, partials, vol, outS, coef2);
+        k_composite<TC, TO, true><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
+                                                          partials, vol, outS, coef2);
     else
-        k_composite<TC, TO, false><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg,
-                                                           rsrc_tab, partials, vol, outS, coef2);
+        k_composite<TC, TO, false><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
+                                                           partials, vol, outS, coef2);
     return cudaGetLastError();
+}
+
+template <typename TC, typename TO>
+cudaError_t launch_composite(const GridDev &g, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta,
+                             double a, double c, double d, TO *out, TO *out2, double *reg, const int *rsrc_tab,
+                             double *partials, double vol, cudaStream_t s, double *outS, double c2) {
+    const double coef = c / (2.0 * g.h * g.h), coef2 = c2 / (2.0 * g.h * g.h);
+    // outS is set only for TC = float64 (the source of a step)
+    return launch_composite_t<TC, TO>(g, X, Y, eta, Gx, Geta, (TC)a, (TC)coef, (TC)d, out, out2, reg, rsrc_tab,
+                                      partials, vol, s, reinterpret_cast<TC *>(outS), (TC)coef2);
+}
+
+// float64 coefficient as float-float (hi = nearest float32, lo = nearest float32 to the rest)
+static dfloat df_from_host(double v) {
+    const float h = (float)v;
+    return dfloat(h, (float)(v - (double)h));
+}
+
+cudaError_t launch_composite_df(const GridDev &g, const double *X, const dfloat *Y, const double *eta,
+                                const double *Gx, const double *Geta, double a, double c, double d, float *out,
+                                float *out2, double *reg, const int *rsrc_tab, double *partials, double vol,
+                                cudaStream_t s, dfloat *outS, double c2) {
+    const double coef = c / (2.0 * g.h * g.h), coef2 = c2 / (2.0 * g.h * g.h);
+    return launch_composite_t<dfloat, float>(g, X, Y, eta, Gx, Geta, df_from_host(a), df_from_host(coef),
+                                             df_from_host(d), out, out2, reg, rsrc_tab, partials, vol, s, outS,
+                                             df_from_host(coef2));
 }
 #define INST_COMPOSITE(TC, TO)                                                                                        \
     template cudaError_t launch_composite<TC, TO>(const GridDev &, const TC *, const TC *, const TC *, const TC *,     \
                                                   const TC *, double, double, double, TO *, TO *, double *, const int *, \
                                                   double *, double, cudaStream_t, double *, double);
 INST_COMPOSITE(double, double)
-INST_COMPOSITE(double, float)
+
 INST_COMPOSITE(float, float)
 
 // ------------------------------------------------------------------ red-black smoothing
@@ -833,18 +973,18 @@ __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict_
     __syncthreads();
     stage_rows<T, 1, 1, G::RS, G::OFF>(tE, eta, snb, slot >= 0 && Geta ? Geta + (size_t)slot * T3 : nullptr);
     __syncthreads();
+    // computed in T: the inverse diagonal only scales smoother updates
     const int t = threadIdx.x, i = t & 7, j = (t >> 3) & 7, k = t >> 6;
     const int p = G::at(i + 1, j + 1, k + 1);
-    const double e0 = (double)tE[p];
-    const double sa[3] = {0.5 * (e0 + (double)tE[p + 1]) + 0.5 * (e0 + (double)tE[p - 1]),
-                          0.5 * (e0 + (double)tE[p + G::RS]) + 0.5 * (e0 + (double)tE[p - G::RS]),
-                          0.5 * (e0 + (double)tE[p + G::PS]) + 0.5 * (e0 + (double)tE[p - G::PS])};
+    const T e0 = tE[p], h = T(0.5), l = (T)lh2;
+    const T sa[3] = {h * (e0 + tE[p + 1]) + h * (e0 + tE[p - 1]), h * (e0 + tE[p + G::RS]) + h * (e0 + tE[p - G::RS]),
+                     h * (e0 + tE[p + G::PS]) + h * (e0 + tE[p - G::PS])};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        double al = 0.0;
+        T al = T(0);
         for (int ax = 0; ax < 3; ax++)
-            if (ax != c) al += lh2 * sa[ax];
-        inv[((size_t)b * 3 + c) * B3 + t] = (T)(1.0 / (1.0 + al));
+            if (ax != c) al += l * sa[ax];
+        inv[((size_t)b * 3 + c) * B3 + t] = T(1) / (T(1) + al);
     }
 }
 

@@ -242,6 +242,52 @@ def test_mixed_precision_matches_fp64_oracle(ohm, orc, name, krylov):
     assert rel <= 1e-11
 
 
+@pytest.mark.parametrize("name", ["uniform_32", "amr_3level"])
+def test_mixed_outer_residual_is_float_float_accurate(ohm, orc, name):
+    """The mixed path evaluates its outer residual in float-float arithmetic (about 48 bits).
+    At the oracle's converged float64 solution it reports a relative residual near 2^-48
+    times the operator's scale (a float32 evaluation reports about 1e-6 here, a dropped
+    trailing part of a coefficient or field the same); on an unconverged field its norms
+    agree with the oracle's to float32 accuracy (they are accumulated in float32)."""
+    h = HIERS[name]()
+    b, eta = rand_fields(h, 13, 1.0)
+    o = orc.Oracle(h, 0.5, eta)
+    b = o.sync_down(b)
+    dt = 4.0 * h.dx(h.nlevels - 1) ** 2
+    want, info = o.cn_step(b, dt, 1e-14, 2, 2, 8, 80)
+    assert info["converged"]
+    g = make(ohm, h, precision=1)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e30)  # stores the source S of b, B unchanged
+    assert st["cycles"] == 0 and rel_err(host(B), b.ravel()) == 0.0
+    rel, _ = ohm.ohm_residual_norm(g, dev(want))
+    _, n_want = o.residual(want, o.source(b, dt), dt)
+    assert n_want["rel_l2"] < 1e-14
+    assert rel < 1e-12, rel
+    rel0, mx0 = ohm.ohm_residual_norm(g, dev(b))
+    _, n0 = o.residual(b, o.source(b, dt), dt)
+    assert rel0 == pytest.approx(n0["rel_l2"], rel=1e-5)
+    assert mx0 == pytest.approx(n0["max_abs"], rel=1e-6)
+
+
+@pytest.mark.parametrize("bad", ["nan_eta", "inf_B", "huge_B"])
+def test_mixed_nonfinite_inputs_report_nonfinite(ohm, bad):
+    """NaN, infinity and float64 values beyond the float32 range reach the mixed path's
+    float-float residual as non-finite values and end the step with OHM_ERR_NONFINITE."""
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    g = make(ohm, h, precision=1, max_outer=3)
+    b, eta = rand_fields(h, 12)
+    if bad == "nan_eta":
+        eta[3, 0, 1, 2, 3] = float("nan")
+    elif bad == "inf_B":
+        b[5, 1, 2, 3, 4] = float("inf")
+    else:
+        b[5, 1, 2, 3, 4] = 1e300
+    with pytest.raises(ohm.OhmError) as ei:
+        ohm.ohm_cn_step(g, dev(b), dev(eta), 0.01, 1e-9)
+    assert ei.value.status == ohm.OHM_ERR_NONFINITE
+
+
 def test_fgmres_takes_fewer_cycles_than_defect_correction(ohm):
     """Same converged tolerance, fewer V-cycles with the Krylov-accelerated inner solve on a
     stiff case (3-decade eta, dt = 100x the explicit limit)."""
