@@ -35,8 +35,15 @@ extern "C" {
 #define OHM_ERR_CUDA          -5  /* a CUDA call or kernel launch failed                    */
 
 #define OHM_FP64  0  /* every kernel in float64                                             */
-#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the residual
-                        R = S - L B, the update B += e, refluxed fluxes and norms stay float64 */
+#define OHM_MIXED 1  /* multigrid in float32 inside defect correction on the float64 state:
+                        B and the update B += e stay float64; the residual R = S - L B is
+                        evaluated in float-float arithmetic (pairs of float32, about 48
+                        significant bits, on the float32 pipe), so the relative residual it
+                        can certify is about 2^-48 (1 + 12 lambda dt eta_max / dx^2); its
+                        norms are accumulated in float32.  B, eta and R must lie within the
+                        float32 range (|values| < 2^64 keeps the squared norms finite);
+                        values below 2^-126 count as zero, NaN and values beyond 2^128 end
+                        the step with OHM_ERR_NONFINITE.  Refluxed fluxes stay float64.    */
 
 typedef struct ohm_hier ohm_hier;
 

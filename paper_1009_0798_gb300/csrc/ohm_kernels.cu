@@ -62,18 +62,21 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
 // float64 -> float-float by bit manipulation (no float64 instruction): hi carries the sign,
 // the exponent and the leading 24 significand bits (truncated), lo the remaining 29 bits
 // rounded to 24, so hi + lo keeps about 48 of the 53 bits.  Magnitudes outside the normal
-// float32 range are converted to float32 with lo = 0 (NaN and infinity keep their class,
-// finite values beyond 2^128 become infinite, values below 2^-126 lose precision).
+// float32 range give lo = 0 and a signed hi: NaN stays NaN, infinities and finite values of
+// 2^128 and above become infinite, values below 2^-126 become zero.
 __device__ __forceinline__ dfloat split_double(double x) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
     const int e = (int)((uh >> 20) & 0x7ffu);  // biased float64 exponent
     const int fe = e - (1023 - 127);           // the same exponent biased for float32
-    if ((unsigned)(fe - 1) >= 254u) return dfloat(__double2float_rn(x));
     const unsigned int sgn = uh & 0x80000000u;
+    if ((unsigned)(fe - 1) >= 254u) {
+        const unsigned int nan = e == 0x7ff && ((uh & 0xfffffu) | ul) ? 0x400000u : 0u;
+        return dfloat(__uint_as_float(fe >= 255 ? sgn | 0x7f800000u | nan : sgn));
+    }
     const float hi = __uint_as_float(sgn | ((unsigned)fe << 23) | ((uh & 0xfffffu) << 3) | (ul >> 29));
-    // lo = r 2^(e - 1075) for the 29 low significand bits r; below 2^-126 the power of two is
-    // applied in two exact steps, 2^(e - 1075 + 64) 2^-64, each in the normal float32 range
+    // lo = r 2^(e - 1075) for the 29 low significand bits r; where 2^(e - 1075) is below the
+    // normal float32 range it is applied in two exact steps, 2^(e - 1075 + 64) and 2^-64
     const int k = e < 1075 - 126 ? 64 : 0;
     const float s1 = __uint_as_float((unsigned)(e - 1075 + k + 127) << 23);
     const float s2 = __uint_as_float((unsigned)(127 - k) << 23);
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
                 const typename CompTypes<TC>::In *__restrict__ eta, const typename CompTypes<TC>::In *__restrict__ Gx,
                 const typename CompTypes<TC>::In *__restrict__ Geta, TC a, TC coef, TC d, TO *__restrict__ out,
                 TO *__restrict__ out2, double *__restrict__ reg, const int *__restrict__ rsrc_tab,
-                double *__restrict__ partials, double vol, TC *__restrict__ outS, TC coef2) {
+                double *__restrict__ partials, double vol, TC *__restrict__ outS, TC coef2, double inv2h, double twoh) {
     using G = Geo<TC>;
     using TA = typename CompTypes<TC>::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -467,8 +470,9 @@ __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
     __syncthreads();
     all_faces_512(tB, tE, phi);
     __syncthreads();
-    const double inv2h = 0.5 / g.h;
-    // flux registers: faces with no same-level neighbour publish F = Phi / (2h)
+    // flux registers: faces with no same-level neighbour publish F = Phi / (2h) (inv2h = 1 / (2h)
+    // and twoh = 2h come from the host: a float64 division here would cost the float32 kernels
+    // dearly on a GPU with few float64 units)
     if (g.freg) {
         for (int s = 0; s < 6; s++) {
             int slotr = g.freg[b * 6 + s];
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
                 const double *R = reg + (size_t)fslot * 128 + comp * 64;
                 int fu = 2 * (u & 3), fv = 2 * (v & 3);
                 double m = 0.25 * ((R[fv * 8 + fu] + R[fv * 8 + fu + 1]) + (R[(fv + 1) * 8 + fu] + R[(fv + 1) * 8 + fu + 1]));
-                phi[plane_face<TC>(ax, hi, comp, u, v)] = from_double<TC>(m * (2.0 * g.h));
+                phi[plane_face<TC>(ax, hi, comp, u, v)] = from_double<TC>(m * twoh);
             }
         }
     }
@@ -551,10 +555,10 @@ static cudaError_t launch_composite_t(const GridDev &g, const typename CompTypes
     (void)attr;
     if (partials)  // with norm partials (the block reductions are compiled out otherwise)
         k_composite<TC, TO, true><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
-                                                          partials, vol, outS, coef2);
+                                                          partials, vol, outS, coef2, 0.5 / g.h, 2.0 * g.h);
     else
         k_composite<TC, TO, false><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
-                                                           partials, vol, outS, coef2);
+                                                           partials, vol, outS, coef2, 0.5 / g.h, 2.0 * g.h);
     return cudaGetLastError();
 }
 
