@@ -438,7 +438,7 @@ template <>
 struct CompTypes<dfloat> {
     using In = double;
     using Acc = float;
-    static constexpr int minb = 2;
+    static constexpr int minb = 3;
 };
 
 template <typename TC, typename TO, bool NORMS>
@@ -499,8 +499,8 @@ __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
                 phi[plane_face<TC>(ax, hi, comp, u, v)] = from_double<TC>(m * twoh);
             }
         }
+        __syncthreads();  // refluxed faces before the divergence (g.rsrc is uniform: legal)
     }
-    __syncthreads();
     int i, j, k;
     cell_of_thread<TC>(threadIdx.x, i, j, k);
     const int cell = (k * 8 + j) * 8 + i;
