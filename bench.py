@@ -42,7 +42,7 @@ def args_parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--only", choices=["fgmres", "mixed", "fp64"], default=None,
+    p.add_argument("--only", choices=["fgmres", "fgmres_ff", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
     p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
     p.add_argument("--n-coarse", type=int, default=4, help="sweeps on the coarsest grid")
@@ -298,12 +298,12 @@ def run_ours(args):
         g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam,
                                      precision=precision, nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse,
                                      max_outer=400, stream=stream, krylov=krylov,
-                                     inner_tol=args.inner_tol if precision == ohm.OHM_MIXED else 0.0)
+                                     inner_tol=args.inner_tol if precision != ohm.OHM_FP64 else 0.0)
         ohm.ohm_set_eta(g, eta)
         return g
 
     def timed(g, precision, profile=True):
-        tsize = 4 if precision == ohm.OHM_MIXED else 8
+        tsize = 4 if precision != ohm.OHM_FP64 else 8
         # warm-up; the first two also pick the dominant kernel (composite vs smooth)
         totals = {}
         for k in range(args.warmup):
@@ -336,8 +336,8 @@ def run_ours(args):
                 "ms_per_step": r["total_ms"] / args.steps, "cycles_per_step": [s["cycles"] for s in r["infos"]]}
 
     if args.only:
-        prec = ohm.OHM_FP64 if args.only == "fp64" else ohm.OHM_MIXED
-        g1 = make(prec, KRYLOV if args.only == "fgmres" else 0)
+        prec = {"fp64": ohm.OHM_FP64, "fgmres_ff": ohm.OHM_MIXED_FF}.get(args.only, ohm.OHM_MIXED)
+        g1 = make(prec, KRYLOV if args.only.startswith("fgmres") else 0)
         for _ in range(args.warmup):
             run_steps(ohm, g1, B, B0, eta, wl, 1, stream)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -345,7 +345,7 @@ def run_ours(args):
         ms = evs[0].elapsed_time(evs[args.steps])
         if rank == 0:
             print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "nu": nu,
-                              "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only == "fgmres" else 0,
+                              "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only.startswith("fgmres") else 0,
                               "inner_tol": args.inner_tol,
                               "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos]}),
                   flush=True)
@@ -360,9 +360,13 @@ def run_ours(args):
     # paper's scheme: float64 V-cycles in float64 defect correction)
     others = {}
     if not args.no_fp64:
-        for name, prec, kr in (("mixed_defect_correction", ohm.OHM_MIXED, 0), ("fp64_plain", ohm.OHM_FP64, 0)):
+        for name, prec, kr in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV),
+                               ("mixed_defect_correction", ohm.OHM_MIXED, 0), ("fp64_plain", ohm.OHM_FP64, 0)):
             g2 = make(prec, kr)
             others[name] = summary(timed(g2, prec, profile=False))
+            if prec == ohm.OHM_MIXED_FF:
+                others[name]["precision"] = ("OHM_MIXED_FF: as the headline, but the outer residual in float-float "
+                                             "(float32 pairs, ~48 bits) with float32-accumulated norms")
             g2.close()
             del g2
     fp64 = others.get("fp64_plain")
@@ -438,6 +442,7 @@ def run_ours(args):
             "final_rel_l2": [s["rel_l2"] for s in mixed["infos"]],
             "fp64_plain": fp64,
             "mixed_defect_correction": others.get("mixed_defect_correction"),
+            "mixed_float_float_residual": others.get("mixed_float_float_residual"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": mixed["clocks"],
             "gpu_launches": mixed["launches"]}
     print(json.dumps(line), flush=True)

@@ -35,15 +35,18 @@ extern "C" {
 #define OHM_ERR_CUDA          -5  /* a CUDA call or kernel launch failed                    */
 
 #define OHM_FP64  0  /* every kernel in float64                                             */
-#define OHM_MIXED 1  /* multigrid in float32 inside defect correction on the float64 state:
-                        B and the update B += e stay float64; the residual R = S - L B is
-                        evaluated in float-float arithmetic (pairs of float32, about 48
-                        significant bits, on the float32 pipe), so the relative residual it
-                        can certify is about 2^-48 (1 + 12 lambda dt eta_max / dx^2); its
-                        norms are accumulated in float32.  B, eta and R must lie within the
-                        float32 range (|values| < 2^64 keeps the squared norms finite);
-                        values below 2^-126 count as zero, NaN and values beyond 2^128 end
-                        the step with OHM_ERR_NONFINITE.  Refluxed fluxes stay float64.    */
+#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the residual
+                        R = S - L B, the update B += e, refluxed fluxes and norms stay float64 */
+#define OHM_MIXED_FF 2 /* as OHM_MIXED, but the outer residual R = S - L B is evaluated in
+                        float-float arithmetic (pairs of float32, about 48 significant bits,
+                        on the float32 pipe, which GB300 issues 58x faster than float64) and
+                        its norms are accumulated in float32.  B and the update stay float64.
+                        The relative residual it can certify is about
+                        2^-48 (1 + 12 lambda dt eta_max / dx^2) (2e-13 for dt = 100x the
+                        explicit limit).  B, eta and R must lie within the float32 range (|values| <
+                        2^64 keeps the squared norms finite); values below 2^-126 count as
+                        zero, NaN and values beyond 2^128 end the step with
+                        OHM_ERR_NONFINITE.  Refluxed fluxes stay float64.                    */
 
 typedef struct ohm_hier ohm_hier;
 
@@ -60,16 +63,16 @@ typedef struct {
                                    refined block's parent exist (proper nesting).  Copied.     */
     double lambda;              /* theta parameter of Eq. 7: 0.5 Crank-Nicolson, 1 backward
                                    Euler; any value in (0, 1]                                  */
-    int32_t precision;          /* OHM_FP64 or OHM_MIXED                                       */
+    int32_t precision;          /* OHM_FP64, OHM_MIXED or OHM_MIXED_FF                         */
     int32_t nu_pre, nu_post;    /* red-black sweeps before / after coarse correction (>= 0)   */
     int32_t n_coarse;           /* red-black sweeps on the coarsest grid (>= 1)               */
     int32_t max_outer;          /* V-cycles allowed per step (>= 1)                           */
-    int32_t krylov;             /* OHM_MIXED only: 0 = the float32 inner solve is defect
+    int32_t krylov;             /* OHM_MIXED(_FF) only: 0 = the float32 inner solve is defect
                                    correction with the V-cycle (Eqs. 16-18); m in 1..11 = it is
                                    FGMRES(m) right-preconditioned by the same V-cycle (not in
                                    the paper; same converged solution, fewer cycles).  Must be
                                    0 for OHM_FP64.                                              */
-    double inner_tol;           /* OHM_MIXED: each float32 inner solve reduces its residual by
+    double inner_tol;           /* OHM_MIXED(_FF): each float32 inner solve reduces its residual by
                                    max(inner_tol, 0.3 tol / current ||R||/||S||); 0 selects
                                    1e-5.  Values below ~1e-6 ask more than float32 can give: the
                                    inner solve then stops when it stagnates.                   */

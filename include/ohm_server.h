@@ -38,12 +38,12 @@ typedef struct {
     int64_t hbm_budget_bytes;   /* device bytes the resident batches may hold (> 0)            */
     int32_t max_batch;          /* slots (instances) per batch, 1 .. 4096                      */
     int32_t n_workers;          /* batches in flight at once (host threads, streams), 1 .. 64  */
-    int32_t precision;          /* OHM_FP64 or OHM_MIXED                                       */
+    int32_t precision;          /* OHM_FP64, OHM_MIXED or OHM_MIXED_FF                         */
     int32_t nu_pre, nu_post, n_coarse, max_outer;  /* multigrid schedule, as ohm_hier_desc   */
     double lambda;              /* theta parameter (0, 1]                                      */
     double tol;                 /* relative residual of every step (>= 0)                      */
     int32_t use_graphs;         /* 1: batches replay their inner iteration as a CUDA graph     */
-    int32_t krylov;             /* OHM_MIXED: 0 = defect-correction inner solves, m in 1..11 =
+    int32_t krylov;             /* OHM_MIXED(_FF): 0 = defect-correction inner solves, m in 1..11 =
                                    per-instance FGMRES(m) (see ohm_hier_desc)                  */
 } ohm_server_desc;
 

@@ -70,6 +70,7 @@ struct ohm_hier {
     ohm_hier_desc d{};
     cudaStream_t s = nullptr;
     bool mixed = false;
+    bool ff = false;     // OHM_MIXED_FF: float-float outer residual, S in float-float form
     int nlev = 0;
     int64_t nblocks = 0;
     std::vector<int32_t> lijk;
@@ -852,15 +853,19 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
         double vol = g.h * g.h * g.h;
         const size_t o3 = (size_t)g.off * 3 * B3;
         if constexpr (std::is_same<TC, double>::value && std::is_same<TO, float>::value) {
-            // outer residual of the mixed path: float-float arithmetic, Y and outS hold the
-            // source in float-float form
+          if (H->ff) {
+            // outer residual of OHM_MIXED_FF: float-float arithmetic, Y and outS hold the source
+            // in float-float form
             LAUNCH(H, OHM_K_COMPOSITE, g.n(),
                    (launch_composite_df(gdev(H, g), X + o3, Y ? reinterpret_cast<const dfloat *>(Y) + o3 : nullptr,
                                         eta + (size_t)g.off * B3, Gx, Geta, a, c, dcoef, out + o3,
                                         out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
                                         norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s,
                                         outS ? reinterpret_cast<dfloat *>(outS) + o3 : nullptr, c2)));
-        } else {
+            continue;
+          }
+        }
+        {
             LAUNCH(H, OHM_K_COMPOSITE, g.n(),
                    (launch_composite<TC, TO>(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta,
                                              a, c, dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
@@ -1606,10 +1611,13 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     if (d->nlevels < 1 || d->nlevels > MAX_LEVELS) { err = "nlevels out of range"; return false; }
     if (d->nblocks <= 0 || !d->block_lijk) { err = "empty block list"; return false; }
     if (!(d->lambda > 0 && d->lambda <= 1)) { err = "lambda must be in (0, 1]"; return false; }
-    if (d->precision != OHM_FP64 && d->precision != OHM_MIXED) { err = "unknown precision"; return false; }
+    if (d->precision != OHM_FP64 && d->precision != OHM_MIXED && d->precision != OHM_MIXED_FF) {
+        err = "unknown precision";
+        return false;
+    }
     if (d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1) { err = "bad cycle counts"; return false; }
-    if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision != OHM_MIXED)) {
-        err = "krylov must be 0, or 1..11 with OHM_MIXED";
+    if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision == OHM_FP64)) {
+        err = "krylov must be 0, or 1..11 with OHM_MIXED or OHM_MIXED_FF";
         return false;
     }
     if (!(d->inner_tol >= 0 && d->inner_tol < 1)) { err = "inner_tol must be in [0, 1)"; return false; }
@@ -1652,7 +1660,8 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
     H->d = *d;
     H->d.block_lijk = nullptr;
     H->s = (cudaStream_t)d->stream;
-    H->mixed = d->precision == OHM_MIXED;
+    H->mixed = d->precision != OHM_FP64;
+    H->ff = d->precision == OHM_MIXED_FF;
     H->nlev = d->nlevels;
     H->nblocks = d->nblocks;
     H->lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);
@@ -1680,7 +1689,8 @@ int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes) {
     ohm_hier H;
     H.d = *d;
     H.d.block_lijk = nullptr;
-    H.mixed = d->precision == OHM_MIXED;
+    H.mixed = d->precision != OHM_FP64;
+    H.ff = d->precision == OHM_MIXED_FF;
     H.nlev = d->nlevels;
     H.nblocks = d->nblocks;
     H.lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);

@@ -374,9 +374,9 @@ int ohm_server_create(const ohm_server_desc *d, ohm_server **out) {
     if (!d || !out) return OHM_ERR_INVALID;
     *out = nullptr;
     if (d->hbm_budget_bytes <= 0 || d->max_batch < 1 || d->max_batch > 4096 || d->n_workers < 1 || d->n_workers > 64 ||
-        (d->precision != OHM_FP64 && d->precision != OHM_MIXED) || !(d->lambda > 0 && d->lambda <= 1) || !(d->tol >= 0) ||
+        (d->precision != OHM_FP64 && d->precision != OHM_MIXED && d->precision != OHM_MIXED_FF) || !(d->lambda > 0 && d->lambda <= 1) || !(d->tol >= 0) ||
         d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1 || d->krylov < 0 || d->krylov > 11 ||
-        (d->krylov > 0 && d->precision != OHM_MIXED))
+        (d->krylov > 0 && d->precision == OHM_FP64))
         return OHM_ERR_INVALID;
     ohm_server *S = new ohm_server();
     S->d = *d;

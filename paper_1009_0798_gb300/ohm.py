@@ -19,6 +19,7 @@ OHM_ERR_OOM = -4
 OHM_ERR_CUDA = -5
 OHM_FP64 = 0
 OHM_MIXED = 1
+OHM_MIXED_FF = 2
 OHM_K_COMPOSITE, OHM_K_SMOOTH, OHM_K_RESID_RESTRICT, OHM_K_PROLONG, OHM_K_GHOST = 0, 1, 2, 3, 4
 OHM_K_SYNC_DOWN, OHM_K_UPDATE, OHM_K_BOTTOM, OHM_K_NORM, OHM_K_KRYLOV = 5, 6, 7, 8, 9
 
@@ -172,7 +173,7 @@ def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, preci
                    inner_tol, n_instances, use_graphs)
     h = C.c_void_p()
     _check(lib().ohm_create_hierarchy(C.byref(d), C.byref(h)), "ohm_create_hierarchy")
-    return Hierarchy(h, len(blocks) * max(1, int(n_instances)), lam, precision == OHM_MIXED, int(n_instances))
+    return Hierarchy(h, len(blocks) * max(1, int(n_instances)), lam, precision != OHM_FP64, int(n_instances))
 
 
 def ohm_hierarchy_bytes(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,

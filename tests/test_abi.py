@@ -52,7 +52,7 @@ def _desc(libohm, base=(16, 16, 16), blocks=None, **kw):
 
 
 @pytest.mark.parametrize("case", ["bad_base", "unsorted", "duplicate", "incomplete_base", "bad_lambda",
-                                  "bad_counts", "not_nested", "incomplete_octet", "krylov_fp64",
+                                  "bad_counts", "not_nested", "incomplete_octet", "krylov_fp64", "bad_precision",
                                   "bad_inner_tol"])
 def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
     from paper_1009_0798_gb300 import workloads as W
@@ -76,6 +76,8 @@ def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
         kw["krylov"] = 4
     elif case == "bad_inner_tol":
         kw.update(precision=libohm.OHM_MIXED, inner_tol=1.5)
+    elif case == "bad_precision":
+        kw["precision"] = libohm.OHM_MIXED_FF + 1
     elif case == "not_nested":
         # a level-2 octet whose parent's neighbourhood is missing at level 1
         h = W.refined(32, 32, 32, 1.0 / 32, [lambda lo, hi: lo[0] < 0.2 and lo[1] < 0.2 and lo[2] < 0.2])

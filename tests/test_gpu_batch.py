@@ -101,13 +101,14 @@ def test_fp64_batch_fixed_schedule_matches_oracle(ohm, orc, name):
 
 
 @pytest.mark.parametrize("name", ["uniform_16", "amr_2level"])
-def test_mixed_batch_converges_to_oracle(ohm, orc, name):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_batch_converges_to_oracle(ohm, orc, name, precision):
     h = W.uniform(16, 16, 16, 1.0 / 16) if name == "uniform_16" else amr_two_level(16)
     K = 4
     bs, etas = instances(h, K, 50)
     bs = [orc.Oracle(h, 0.5, etas[q]).sync_down(bs[q]) for q in range(K)]
     dts = [(3.0 + q) * h.dx(h.nlevels - 1) ** 2 for q in range(K)]
-    g = make(ohm, h, K, precision=1, max_outer=120)
+    g = make(ohm, h, K, precision=precision, max_outer=120)
     ohm.ohm_set_eta(g, dev(stack(h, etas)))
     B = dev(stack(h, bs))
     status, st = ohm.ohm_cn_step_batch(g, B, dts, 1e-11)
@@ -120,7 +121,8 @@ def test_mixed_batch_converges_to_oracle(ohm, orc, name):
 
 
 @pytest.mark.parametrize("graphs", [False, True])
-def test_instance_same_bits_alone_and_in_batch(ohm, graphs):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_instance_same_bits_alone_and_in_batch(ohm, graphs, precision):
     """An instance stepped alone (K = 1) and inside a batch of 5 with other eta, dt and data,
     some of them inactive, gives identical bits; inactive instances are left untouched."""
     h = amr_two_level(16)
@@ -129,12 +131,12 @@ def test_instance_same_bits_alone_and_in_batch(ohm, graphs):
     dts = [(2.0 + q) * h.dx(1) ** 2 for q in range(K)]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        g1 = make(ohm, h, 1, precision=1, stream=stream, use_graphs=graphs)
+        g1 = make(ohm, h, 1, precision=precision, stream=stream, use_graphs=graphs)
         ohm.ohm_set_eta(g1, dev(etas[2]))
         B1 = dev(bs[2])
         s1, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[2]], 1e-9)
         s1b, st1b = ohm.ohm_cn_step_batch(g1, B1, [dts[2]], 1e-9)  # second step: graph replay
-        gK = make(ohm, h, K, precision=1, stream=stream, use_graphs=graphs)
+        gK = make(ohm, h, K, precision=precision, stream=stream, use_graphs=graphs)
         ohm.ohm_set_eta(gK, dev(stack(h, etas)))
         BK = dev(stack(h, bs))
         active = [1, 0, 1, 1, 0]
@@ -237,16 +239,17 @@ def test_fgmres_batch_converges_to_oracle(ohm, orc, name):
         assert rel_err(got[q], want.reshape(-1, 1536)) < 1e-9, q
 
 
-def test_fgmres_batch_same_bits_alone_and_in_batch(ohm):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fgmres_batch_same_bits_alone_and_in_batch(ohm, precision):
     h = amr_two_level(16)
     K = 4
     bs, etas = instances(h, K, 95)
     dts = [(2.0 + q) * h.dx(1) ** 2 for q in range(K)]
-    g1 = make(ohm, h, 1, precision=1, krylov=4)
+    g1 = make(ohm, h, 1, precision=precision, krylov=4)
     ohm.ohm_set_eta(g1, dev(etas[1]))
     B1 = dev(bs[1])
     _, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[1]], 1e-9)
-    gK = make(ohm, h, K, precision=1, krylov=4)
+    gK = make(ohm, h, K, precision=precision, krylov=4)
     ohm.ohm_set_eta(gK, dev(stack(h, etas)))
     BK = dev(stack(h, bs))
     _, stK = ohm.ohm_cn_step_batch(gK, BK, dts, 1e-9, active=[1, 1, 0, 1])
