@@ -47,6 +47,9 @@ def args_parse():
     p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
     p.add_argument("--n-coarse", type=int, default=4, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
+    p.add_argument("--omega", type=float, default=1.2,
+                   help="relaxation factor of the red-black sweeps on the headline and serving paths (1 = the paper's "
+                        "Gauss-Seidel, kept by the FP64 and defect-correction comparisons)")
     p.add_argument("--workload", choices=["resistive_bump", "batched512", "serving"], default="resistive_bump",
                    help="resistive_bump: the headline 256^3 line; batched512: 512 independent instances "
                         "(edges 16..64) in batched hierarchies; serving: Poisson request stream through "
@@ -294,11 +297,11 @@ def run_ours(args):
     nu = tuple(int(v) for v in args.nu.split(","))
     KRYLOV = args.krylov
 
-    def make(precision, krylov=0):
+    def make(precision, krylov=0, omega=1.0):
         g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam,
                                      precision=precision, nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse,
                                      max_outer=400, stream=stream, krylov=krylov,
-                                     inner_tol=args.inner_tol if precision != ohm.OHM_FP64 else 0.0)
+                                     inner_tol=args.inner_tol if precision != ohm.OHM_FP64 else 0.0, omega=omega)
         ohm.ohm_set_eta(g, eta)
         return g
 
@@ -337,7 +340,8 @@ def run_ours(args):
 
     if args.only:
         prec = {"fp64": ohm.OHM_FP64, "fgmres_ff": ohm.OHM_MIXED_FF}.get(args.only, ohm.OHM_MIXED)
-        g1 = make(prec, KRYLOV if args.only.startswith("fgmres") else 0)
+        g1 = make(prec, KRYLOV if args.only.startswith("fgmres") else 0,
+                  args.omega if args.only.startswith("fgmres") else 1.0)
         for _ in range(args.warmup):
             run_steps(ohm, g1, B, B0, eta, wl, 1, stream)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -346,13 +350,13 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "nu": nu,
                               "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only.startswith("fgmres") else 0,
-                              "inner_tol": args.inner_tol,
+                              "inner_tol": args.inner_tol, "omega": args.omega if args.only.startswith("fgmres") else 1.0,
                               "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos]}),
                   flush=True)
         return
 
     # headline: float32 multigrid, FGMRES-accelerated, inside float64 iterative refinement
-    gm = make(ohm.OHM_MIXED, KRYLOV)
+    gm = make(ohm.OHM_MIXED, KRYLOV, args.omega)
     mixed = timed(gm, ohm.OHM_MIXED)
     t_max = barrier_max(ws, mixed["total_ms"])
     value = job_throughput(ws, cells, args.steps, mixed["total_ms"])
@@ -360,9 +364,9 @@ def run_ours(args):
     # paper's scheme: float64 V-cycles in float64 defect correction)
     others = {}
     if not args.no_fp64:
-        for name, prec, kr in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV),
-                               ("mixed_defect_correction", ohm.OHM_MIXED, 0), ("fp64_plain", ohm.OHM_FP64, 0)):
-            g2 = make(prec, kr)
+        for name, prec, kr, om in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV, args.omega),
+                                   ("mixed_defect_correction", ohm.OHM_MIXED, 0, 1.0), ("fp64_plain", ohm.OHM_FP64, 0, 1.0)):
+            g2 = make(prec, kr, om)
             others[name] = summary(timed(g2, prec, profile=False))
             if prec == ohm.OHM_MIXED_FF:
                 others[name]["precision"] = ("OHM_MIXED_FF: as the headline, but the outer residual in float-float "
@@ -433,8 +437,9 @@ def run_ours(args):
             "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
             "config": {"workload": f"resistive_bump_{args.size}^3", "cells": cells, "tol": wl.tol,
                        "dt_over_explicit_limit": 100, "cn_steps_per_run": args.steps, "precision": "mixed",
-                       "multigrid": f"V({nu[0]},{nu[1]}), {args.n_coarse} coarsest sweeps; float32 inner solve FGMRES({KRYLOV}) "
-                                    "right-preconditioned by the V-cycle; float64 iterative refinement",
+                       "multigrid": f"V({nu[0]},{nu[1]}) of red-black SOR sweeps (omega {args.omega}), {args.n_coarse} "
+                                    f"coarsest sweeps; float32 inner solve FGMRES({KRYLOV}) right-preconditioned by "
+                                    "the V-cycle; float64 iterative refinement",
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (402 MB per float64 field vs 129 MB L2), no flush"},
             "latency_ms": {"p50": statistics.median(lat), "p99": p99},
@@ -766,7 +771,7 @@ def run_serving(args):
     # V(4,4) with 4 coarsest sweeps: the schedule the autotuner picks for every class of the
     # batched workload (defect-correction inner solves)
     cfg = dict(hbm_budget_bytes=budget, max_batch=8, n_workers=6, precision=1, tol=1e-9, use_graphs=True,
-               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400, krylov=args.batch_krylov)
+               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400, krylov=args.batch_krylov, omega=args.omega)
     # warm-up service: one request per class (kernels loaded, batches of each class built once)
     with server.Server(**cfg) as s:
         seen = {}

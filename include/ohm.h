@@ -88,6 +88,12 @@ typedef struct {
                                    residual) is captured once into a CUDA graph and replayed.
                                    Needs a non-NULL stream; ignored otherwise.                  */
     void *stream;               /* cudaStream_t used for all work, NULL = legacy default      */
+    double omega;               /* relaxation factor of the red-black sweeps: each colour update
+                                   becomes e + omega (e_GS - e) (red-black SOR).  0 selects 1,
+                                   the paper's Gauss-Seidel (Eq. 19); allowed in (0, 2).  Not in
+                                   the paper: it changes the iterates, not the converged
+                                   solution (1.2 saves 2 of 15 V-cycles per step of the 256^3
+                                   resistive bump; 1.5 and above slow convergence down).       */
 } ohm_hier_desc;
 
 typedef struct {
@@ -149,14 +155,16 @@ int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes);
  * in {fused red+black sweep, two colour passes} (the fused sweep stages a 12^3 tile, the
  * two-pass smoother a 10^3 tile).  Each candidate runs one step of ohm_cn_step (batches:
  * ohm_cn_step_batch with dt) from B_dev on a private copy (B_dev is not modified), timed
- * with CUDA events; candidates that do not converge are discarded.  The fastest is kept in
- * the hierarchy and reported.  Allocates one copy of B for the duration of the call.
+ * with CUDA events; candidates that do not converge are discarded.  The best schedule is
+ * then timed with the relaxation factors omega in {1, 1.15, 1.3} besides the hierarchy's own.
+ * The fastest is kept in the hierarchy and reported.  Allocates one copy of B for the duration of the call.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     int32_t nu_pre, nu_post, n_coarse;
     int32_t smoother;           /* 0 = fused red+black sweep, 1 = two colour passes            */
     double ms;                  /* time of the chosen candidate's step                         */
     int32_t candidates;         /* candidates timed                                            */
+    double omega;               /* chosen relaxation factor                                    */
 } ohm_tune_result;
 int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol, ohm_tune_result *res);
 
@@ -198,7 +206,8 @@ int ohm_mg_grid_info(ohm_hier *h, int m, int32_t dims[3], int64_t *nblocks, int3
 
 /* Single-grid steps on blocked base multigrid grid m (OHM_FP64; arrays in that grid's
  * block layout; eta_dev [nblocks][8][8][8]):
- *   smooth:  one red-black colour pass (Eq. 19 with alpha from Eqs. 21-23) in place on e;
+ *   smooth:  one red-black colour pass (Eq. 19 with alpha from Eqs. 21-23) in place on e,
+ *            relaxed by the hierarchy's omega: e + omega (e_GS - e);
  *   residual: t = r - (e + lambda dt div F(e));
  *   restrict: coarse grid m+1 (blocked) = mean of 8 children of fine grid m, ncomp comps;
  *   prolong_add: fine grid m += trilinear interpolation of coarse grid m+1 (blocked). */

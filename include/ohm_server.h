@@ -45,6 +45,7 @@ typedef struct {
     int32_t use_graphs;         /* 1: batches replay their inner iteration as a CUDA graph     */
     int32_t krylov;             /* OHM_MIXED(_FF): 0 = defect-correction inner solves, m in 1..11 =
                                    per-instance FGMRES(m) (see ohm_hier_desc)                  */
+    double omega;               /* relaxation factor of the sweeps (see ohm_hier_desc); 0 = 1  */
 } ohm_server_desc;
 
 typedef struct {

@@ -655,6 +655,7 @@ SmallDev<T> small_dev(ohm_hier *H) {
     sm.n = (int)H->small.size();
     sm.ninst = H->K;
     sm.imask = H->cmask;
+    sm.omega = H->d.omega;
     double h = H->d.dx0 * std::pow(2.0, (double)(H->mg.size() + 1));
     for (int q = 0; q < sm.n; q++) {
         for (int a = 0; a < 3; a++) sm.dims[q][a] = H->small[q][a];
@@ -700,11 +701,18 @@ int prepare_dt(ohm_hier *H, double dt) {
     if (H->inv_dt == dt) return OHM_OK;
     const double lamdt = H->d.lambda * dt;
     cudaStream_t s = H->s;
-    for (auto &g : H->amr)
-        CK(launch_invdiag<T>(g.dev, amr_ptr<T>(H->amrbuf.eta, g, 1), (const T *)H->ghostEtaT, lamdt,
+    // the relaxation factor is folded into the inverse diagonal (omega / (1 + alpha))
+    for (auto &g : H->amr) {
+        GridDev d = g.dev;
+        d.omega = H->d.omega;
+        CK(launch_invdiag<T>(d, amr_ptr<T>(H->amrbuf.eta, g, 1), (const T *)H->ghostEtaT, lamdt,
                              amr_ptr<T>(H->amrbuf.inv, g, 3), s));
-    for (size_t m = 0; m < H->mg.size(); m++)
-        CK(launch_invdiag<T>(H->mg[m].dev, (const T *)H->mgbuf[m].eta, nullptr, lamdt, (T *)H->mgbuf[m].inv, s));
+    }
+    for (size_t m = 0; m < H->mg.size(); m++) {
+        GridDev d = H->mg[m].dev;
+        d.omega = H->d.omega;
+        CK(launch_invdiag<T>(d, (const T *)H->mgbuf[m].eta, nullptr, lamdt, (T *)H->mgbuf[m].inv, s));
+    }
     SmallDev<T> sm = small_dev<T>(H);
     CK(launch_small_setup<T>(sm, lamdt, false, s));
     H->inv_dt = dt;
@@ -715,6 +723,7 @@ int prepare_dt(ohm_hier *H, double dt) {
 GridDev gdev(const ohm_hier *H, const HGrid &g) {
     GridDev d = g.dev;
     d.imask = H->cmask;
+    d.omega = H->d.omega;
     return d;
 }
 
@@ -1616,6 +1625,7 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
         return false;
     }
     if (d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1) { err = "bad cycle counts"; return false; }
+    if (!(d->omega == 0 || (d->omega > 0 && d->omega < 2))) { err = "omega must be 0 (= 1) or in (0, 2)"; return false; }
     if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision == OHM_FP64)) {
         err = "krylov must be 0, or 1..11 with OHM_MIXED or OHM_MIXED_FF";
         return false;
@@ -1658,6 +1668,7 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
     }
     ohm_hier *H = new ohm_hier();
     H->d = *d;
+    if (H->d.omega == 0) H->d.omega = 1.0;
     H->d.block_lijk = nullptr;
     H->s = (cudaStream_t)d->stream;
     H->mixed = d->precision != OHM_FP64;
@@ -1798,24 +1809,56 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
                     br = ohm_tune_result{h->d.nu_pre, h->d.nu_post, h->d.n_coarse, h->smoother, ms, 0};
                 }
             }
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    cudaFree(Bw);
-    reset_graph(h);
-    if (st != OHM_OK && st != OHM_ERR_NOT_CONVERGED) {
-        h->d = saved;
+    if ((st != OHM_OK && st != OHM_ERR_NOT_CONVERGED) || !(best < INFINITY)) {
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        cudaFree(Bw);
+        h->d = saved;  // a failure, or nothing converged: keep the schedule the hierarchy had
         h->smoother = saved_sm;
-        return st;
-    }
-    if (!(best < INFINITY)) {  // nothing converged: keep the schedule the hierarchy had
-        h->d = saved;
-        h->smoother = saved_sm;
-        return OHM_ERR_NOT_CONVERGED;
+        h->inv_dt = NAN;
+        reset_graph(h);
+        return st != OHM_OK && st != OHM_ERR_NOT_CONVERGED ? st : OHM_ERR_NOT_CONVERGED;
     }
     h->d.nu_pre = br.nu_pre;
     h->d.nu_post = br.nu_post;
     h->d.n_coarse = br.n_coarse;
     h->smoother = br.smoother;
+    // relaxation factor of the sweeps on the chosen schedule (folded into the inverse diagonals,
+    // so they are recomputed for each candidate)
+    br.omega = saved.omega;
+    const double oms[3] = {1.0, 1.15, 1.3};
+    for (int q = 0; q < 3 && st != OHM_ERR_CUDA; q++) {
+        if (oms[q] == saved.omega) continue;
+        h->d.omega = oms[q];
+        h->inv_dt = NAN;
+        reset_graph(h);
+        cudaEventRecord(ev[0], h->s);
+        const int r = step();
+        cudaEventRecord(ev[1], h->s);
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+            st = OHM_ERR_CUDA;
+            break;
+        }
+        ncand++;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (r == OHM_OK && ms < best) {
+            best = ms;
+            br.ms = ms;
+            br.omega = oms[q];
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaFree(Bw);
+    h->d.omega = br.omega;
+    h->inv_dt = NAN;
+    reset_graph(h);
+    if (st == OHM_ERR_CUDA) {
+        h->d = saved;
+        h->smoother = saved_sm;
+        return st;
+    }
     br.candidates = ncand;
     if (res) *res = br;
     return OHM_OK;
@@ -1964,7 +2007,8 @@ static int grid_setup(ohm_hier *h, int m, const double *eta_dev, double dt, Grid
     G = base_ref<double>(h, m);
     const size_t nb = (size_t)G.g->n();
     CK(cudaMemcpyAsync(G.eta, eta_dev, nb * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-    CK(launch_invdiag<double>(G.g->dev, (const double *)G.eta, nullptr, h->d.lambda * dt, (double *)G.inv, h->s));
+    // omega / (1 + alpha): the colour pass applies the hierarchy's relaxation factor
+    CK(launch_invdiag<double>(gdev(h, *G.g), (const double *)G.eta, nullptr, h->d.lambda * dt, (double *)G.inv, h->s));
     h->eta_set = false;
     h->inv_dt = NAN;
     return OHM_OK;

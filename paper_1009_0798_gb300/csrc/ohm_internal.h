@@ -36,6 +36,7 @@ struct GridDev {
                                     // = b / inst_nblk); 0 = one instance
     const uint8_t *imask = nullptr; // batched inner iterations: thread blocks of instances whose
                                     // flag is 0 return at once (their results are not used)
+    double omega = 1.0;             // relaxation factor of the red-black sweeps (1 = Gauss-Seidel)
 };
 
 // Lexicographic coarse grids below the last blocked grid (solved in one thread block).
@@ -46,6 +47,7 @@ struct SmallDev {
     int ninst = 1;                  // instances; the arrays of grid s hold them one after another
                                     // (instance q at q * ncomp * cells(s)), one thread block each
     const uint8_t *imask = nullptr; // k_bottom skips instances whose flag is 0
+    double omega = 1.0;             // relaxation factor folded into inv (1 = Gauss-Seidel)
     int dims[MAX_SMALL][3];
     double h[MAX_SMALL];
     T *e[MAX_SMALL], *r[MAX_SMALL], *t[MAX_SMALL], *eta[MAX_SMALL], *inv[MAX_SMALL];

@@ -704,7 +704,7 @@ __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 template <typename T, typename G = G12<T>>
 __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
-                                          const T rr[3], T out[3]) {
+                                          const T rr[3], T out[3], T omega) {
     T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
     face_phi_s(tB, tE, p - 1, 0, 1, G::RRS, G::PS, G::CS, xl1, xl2);
     face_phi_s(tB, tE, p, 0, 1, G::RRS, G::PS, G::CS, xh1, xh2);
@@ -722,7 +722,7 @@ __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__r
     for (int c = 0; c < 3; c++) {
         T ev = tB[c * G::CS + p];
         T res = rr[c] - ev - coef * dv[c];
-        out[c] = ev + fast_div(res, T(1) + al[c]);
+        out[c] = ev + fast_div(omega * res, T(1) + al[c]);
     }
 }
 
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
         const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
         const T rr[3] = {r[(size_t)src * 3 * B3 + off], r[(size_t)src * 3 * B3 + B3 + off], r[(size_t)src * 3 * B3 + 2 * B3 + off]};
         np[s4] = G::at(li + 2, lj + 2, lk + 2);
-        rb_update(tB, tE, np[s4], coef, lh2, rr, nv[s4]);
+        rb_update(tB, tE, np[s4], coef, lh2, rr, nv[s4], (T)g.omega);
     }
     __syncthreads();
 #pragma unroll
@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     const T rr[3] = {r[(size_t)b * 3 * B3 + cb], r[(size_t)b * 3 * B3 + B3 + cb], r[(size_t)b * 3 * B3 + 2 * B3 + cb]};
     T out[3];
     const int pb = G::at(ib + 2, j + 2, k + 2), pr = G::at(ir + 2, j + 2, k + 2);
-    rb_update(tB, tE, pb, coef, lh2, rr, out);
+    rb_update(tB, tE, pb, coef, lh2, rr, out, (T)g.omega);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         e_out[((size_t)b * 3 + c) * B3 + cb] = out[c];
@@ -952,8 +952,9 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     // red: the brick's 512 (one per thread), then the 384 of its ring, from the pre-sweep state
     float nv0[3], nv1[3];
     const int p0 = G::at(ir + 2, j + 2, k + 2);
-    rb_update<float, G>(tB, tE, p0, coef, lh2, rr0, nv0);
-    if (p1 >= 0) rb_update<float, G>(tB, tE, p1, coef, lh2, rr1, nv1);
+    const float om = (float)g.omega;
+    rb_update<float, G>(tB, tE, p0, coef, lh2, rr0, nv0, om);
+    if (p1 >= 0) rb_update<float, G>(tB, tE, p1, coef, lh2, rr1, nv1, om);
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -963,7 +964,7 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     __syncthreads();
     // black cells of the brick from the post-red state, then both blocks are written out
     float out[3];
-    rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out);
+    rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out, om);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         e_out[((size_t)own * 3 + c) * B3 + cb] = out[c];
@@ -983,7 +984,7 @@ cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out,
 }
 
 // ------------------------------------------------------------------ inverse diagonal
-// inv_c = 1 / (1 + alpha_c), alpha_c = lamdt/h^2 sum_{a != c} (eta_{-1/2} + eta_{+1/2})
+// inv_c = omega / (1 + alpha_c), alpha_c = lamdt/h^2 sum_{a != c} (eta_{-1/2} + eta_{+1/2})
 // with face eta the mean of the two cells (Eqs. 11, 21-23).
 template <typename T>
 __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict__ eta, const T *__restrict__ Geta,
@@ -1009,7 +1010,7 @@ __global__ void __launch_bounds__(512) k_invdiag(GridDev g, const T *__restrict_
         T al = T(0);
         for (int ax = 0; ax < 3; ax++)
             if (ax != c) al += l * sa[ax];
-        inv[((size_t)b * 3 + c) * B3 + t] = T(1) / (T(1) + al);
+        inv[((size_t)b * 3 + c) * B3 + t] = (T)g.omega / (T(1) + al);
     }
 }
 
@@ -1935,7 +1936,7 @@ __global__ void __launch_bounds__(1024) k_small_setup(SmallDev<T> sm_all, double
                 double al = 0.0;
                 for (int ax = 0; ax < 3; ax++)
                     if (ax != c) al += lh2 * sa[ax];
-                sm.inv[s][(size_t)c * n + q] = (T)(1.0 / (1.0 + al));
+                sm.inv[s][(size_t)c * n + q] = (T)(sm.omega / (1.0 + al));
             }
         }
         __syncthreads();

@@ -52,7 +52,7 @@ def _desc(libohm, base=(16, 16, 16), blocks=None, **kw):
 
 
 @pytest.mark.parametrize("case", ["bad_base", "unsorted", "duplicate", "incomplete_base", "bad_lambda",
-                                  "bad_counts", "not_nested", "incomplete_octet", "krylov_fp64", "bad_precision",
+                                  "bad_counts", "not_nested", "incomplete_octet", "krylov_fp64", "bad_precision", "omega_2", "omega_negative",
                                   "bad_inner_tol"])
 def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
     from paper_1009_0798_gb300 import workloads as W
@@ -78,6 +78,10 @@ def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
         kw.update(precision=libohm.OHM_MIXED, inner_tol=1.5)
     elif case == "bad_precision":
         kw["precision"] = libohm.OHM_MIXED_FF + 1
+    elif case == "omega_2":
+        kw["omega"] = 2.0
+    elif case == "omega_negative":
+        kw["omega"] = -0.5
     elif case == "not_nested":
         # a level-2 octet whose parent's neighbourhood is missing at level 1
         h = W.refined(32, 32, 32, 1.0 / 32, [lambda lo, hi: lo[0] < 0.2 and lo[1] < 0.2 and lo[2] < 0.2])
@@ -111,3 +115,35 @@ def test_server_rejects_bad_descriptor_without_gpu(libohm):
         server.Server(hbm_budget_bytes=0)
     with pytest.raises(libohm.OhmError):
         server.Server(hbm_budget_bytes=1 << 30, max_batch=0)
+
+
+def test_ctypes_mirrors_match_the_c_layouts(tmp_path):
+    """The Python structures that mirror ohm_hier_desc, ohm_tune_result, ohm_step_stats,
+    ohm_server_desc and ohm_request have the sizes and field offsets the C compiler gives the
+    header's structs."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_1009_0798_gb300 import ohm, server
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    mirrors = {"ohm_hier_desc": ohm.HierDesc, "ohm_tune_result": ohm.TuneResult, "ohm_step_stats": ohm.StepStats,
+               "ohm_server_desc": server.ServerDesc, "ohm_request": server.Request}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ohm_server.h"', "int main(void) {"]
+    cnames = {"lam": "lambda"}
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {cnames.get(f, f)}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.split("\n") if l)
+    for cname, py in mirrors.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)

@@ -122,6 +122,28 @@ def test_grid_smooth(ohm, orc, m, colour):
     assert rel_err(got, want) < TOL64
 
 
+@pytest.mark.parametrize("colour", [0, 1])
+def test_grid_smooth_relaxed(ohm, orc, colour):
+    """A colour pass of a hierarchy with omega = 1.3 (red-black SOR) moves every cell of the
+    colour 1.3 times as far as the oracle's Gauss-Seidel pass and leaves the other colour."""
+    h = W.uniform(32, 32, 32, 1.0 / 32)
+    o = orc.Oracle(h, 0.5)
+    g = make(ohm, h, omega=1.3)
+    dims, nb, ijk = ohm.ohm_mg_grid_info(g, 0)
+    rng = np.random.default_rng(17)
+    e = rng.standard_normal((3,) + dims[::-1])
+    r = rng.standard_normal((3,) + dims[::-1])
+    eta = 10 ** rng.uniform(-1, 1, (1,) + dims[::-1])
+    dt = 5.0 * h.dx0 ** 2
+    et = dev(grid_of_dense(e, ijk))
+    ohm.ohm_op_grid_smooth(g, 0, et, dev(grid_of_dense(r, ijk)), dev(grid_of_dense(eta, ijk)), dt, colour)
+    got = dense_of_grid(host(et).reshape(nb, 3, 8, 8, 8), ijk, dims, 3)
+    gs = o.grid_smooth(0, e, r, eta, dt, colour)
+    moved = np.abs(gs - e).max(axis=0) > 0
+    assert rel_err(got, e + 1.3 * (gs - e)) < TOL64
+    assert np.array_equal(got[:, ~moved], e[:, ~moved])
+
+
 @pytest.mark.parametrize("m", [0, 1])
 def test_grid_residual_restrict_prolong(ohm, orc, m):
     """a4 (level residual), a6 restriction, a7 prolongation on base multigrid grid m."""
@@ -295,6 +317,24 @@ def test_mixed_nonfinite_inputs_report_nonfinite(ohm, bad, precision):
     with pytest.raises(ohm.OhmError) as ei:
         ohm.ohm_cn_step(g, dev(b), dev(eta), 0.01, 1e-9)
     assert ei.value.status == ohm.OHM_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision,krylov", [(0, 0), (1, 0), (1, 4)])
+def test_relaxed_sweeps_reach_the_same_solution(ohm, orc, precision, krylov):
+    """omega = 1.25 changes the multigrid iterates, not the converged solution: the step
+    reaches the oracle's converged Gauss-Seidel solution (float64: 1e-11, both sides at 1e-13;
+    mixed: 1e-9)."""
+    h = HIERS["amr_3level"]()
+    b, eta = rand_fields(h, 21, 1.0)
+    o = orc.Oracle(h, 0.5, eta)
+    b = o.sync_down(b)
+    dt = 4.0 * h.dx(h.nlevels - 1) ** 2
+    want, _ = o.cn_step(b, dt, 1e-14, 2, 2, 8, 80)
+    g = make(ohm, h, precision=precision, max_outer=80, krylov=krylov, omega=1.25)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-13 if precision == 0 else 1e-11)
+    assert st["converged"]
+    assert rel_err(host(B), want.ravel()) < (1e-11 if precision == 0 else 1e-9)
 
 
 def test_fgmres_takes_fewer_cycles_than_defect_correction(ohm):
