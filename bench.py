@@ -44,7 +44,7 @@ def args_parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--only", choices=["fgmres", "fgmres_ff", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
-    p.add_argument("--nu", default="2,2", help="pre,post red-black sweeps per level")
+    p.add_argument("--nu", default="3,2", help="pre,post red-black sweeps per level")
     p.add_argument("--n-coarse", type=int, default=4, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
     p.add_argument("--omega", type=float, default=1.2,

@@ -150,13 +150,13 @@ int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes);
 
 /* ---------------------------------------------------------------------------------------
  * Autotuner (not in the paper): picks the multigrid schedule of a hierarchy by timing real
- * steps.  Candidates: (nu_pre, nu_post) in {(1,1), (2,1), (2,2), (3,3), (4,4)} (the paper's
+ * steps.  Candidates: (nu_pre, nu_post) in {(1,1), (2,1), (2,2), (3,2), (3,3), (4,4)} (the paper's
  * Table 1 uses 2/2 on the base grid and 4/4 on AMR levels) x n_coarse in {4, 16} x smoother
  * in {fused red+black sweep, two colour passes} (the fused sweep stages a 12^3 tile, the
  * two-pass smoother a 10^3 tile).  Each candidate runs one step of ohm_cn_step (batches:
  * ohm_cn_step_batch with dt) from B_dev on a private copy (B_dev is not modified), timed
  * with CUDA events; candidates that do not converge are discarded.  The best schedule is
- * then timed with the relaxation factors omega in {1, 1.15, 1.3} besides the hierarchy's own.
+ * then timed with the relaxation factors omega in {1, 1.15, 1.3, 1.45} besides the hierarchy's own.
  * The fastest is kept in the hierarchy and reported.  Allocates one copy of B for the duration of the call.
  * ------------------------------------------------------------------------------------- */
 typedef struct {

@@ -1781,12 +1781,12 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
         return h->mixed ? cn_step_mixed(h, Bw, dt[0], tol, nullptr) : cn_step_impl<double>(h, Bw, dt[0], tol, nullptr);
     };
     int st = step();  // warm-up: first-use setup outside the timings
-    const int nus[5][2] = {{1, 1}, {2, 1}, {2, 2}, {3, 3}, {4, 4}};
+    const int nus[6][2] = {{1, 1}, {2, 1}, {2, 2}, {3, 2}, {3, 3}, {4, 4}};
     const int ncs[2] = {4, 16};
     double best = INFINITY;
     ohm_tune_result br{};
     int ncand = 0;
-    for (int a = 0; a < 5 && (st == OHM_OK || st == OHM_ERR_NOT_CONVERGED); a++)
+    for (int a = 0; a < 6 && (st == OHM_OK || st == OHM_ERR_NOT_CONVERGED); a++)
         for (int c = 0; c < 2; c++)
             for (int sm = 0; sm < (h->mixed ? 2 : 1); sm++) {
                 h->d.nu_pre = nus[a][0];
@@ -1826,8 +1826,8 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
     // relaxation factor of the sweeps on the chosen schedule (folded into the inverse diagonals,
     // so they are recomputed for each candidate)
     br.omega = saved.omega;
-    const double oms[3] = {1.0, 1.15, 1.3};
-    for (int q = 0; q < 3 && st != OHM_ERR_CUDA; q++) {
+    const double oms[4] = {1.0, 1.15, 1.3, 1.45};
+    for (int q = 0; q < 4 && st != OHM_ERR_CUDA; q++) {
         if (oms[q] == saved.omega) continue;
         h->d.omega = oms[q];
         h->inv_dt = NAN;
