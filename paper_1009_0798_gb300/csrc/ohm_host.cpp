@@ -754,22 +754,31 @@ GridRef base_ref(ohm_hier *H, int m) {  // m = 0: AMR level 0
 }
 
 template <typename T>
-int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
+int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt, bool zero = false) {
+    // zero: G.e holds no valid values yet and stands for e = 0 (the pre-smoothing of a level)
+    const size_t bytes = (size_t)G.g->n() * 3 * B3 * sizeof(T);
     if (std::is_same<T, float>::value && G.g->nslot == 0 && H->smoother == 0) {
         // float32 grids with every neighbour: one fused red+black launch per sweep, on block
-        // pairs where the grid's blocks pair up along x
+        // pairs where the grid's blocks pair up along x.  The buffers alternate so that the
+        // last sweep writes G.e; a pair sweep from zero reads nothing for e, so neither a
+        // memset nor a final copy is needed then.
+        const bool zs = zero && G.g->brick;
+        if (zero && (!zs || n == 0)) CK(cudaMemsetAsync(G.e, 0, bytes, H->s));
         for (int i = 0; i < n; i++) {
-            const T *src = (const T *)((i & 1) ? G.e2 : G.e);
-            T *dst = (T *)((i & 1) ? G.e : G.e2);
+            const bool to_e = zs ? ((n - 1 - i) % 2 == 0) : (i & 1);
+            const T *src = (const T *)(to_e ? G.e2 : G.e);
+            T *dst = (T *)(to_e ? G.e : G.e2);
             if (G.g->brick)
-                LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb2(gdev(H, *G.g), (const float *)src, (float *)dst,
-                                                                    (const float *)G.r, (const float *)G.eta, lamdt, H->s));
+                LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb2(gdev(H, *G.g), i == 0 && zs ? nullptr : (const float *)src,
+                                                                    (float *)dst, (const float *)G.r, (const float *)G.eta,
+                                                                    lamdt, H->s));
             else
                 LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth_rb<T>(gdev(H, *G.g), src, dst, (const T *)G.r, (const T *)G.eta, lamdt, H->s));
         }
-        if (n & 1) CK(cudaMemcpyAsync(G.e, G.e2, (size_t)G.g->n() * 3 * B3 * sizeof(T), cudaMemcpyDeviceToDevice, H->s));
+        if (!zs && (n & 1)) CK(cudaMemcpyAsync(G.e, G.e2, bytes, cudaMemcpyDeviceToDevice, H->s));
         return OHM_OK;
     }
+    if (zero) CK(cudaMemsetAsync(G.e, 0, bytes, H->s));
     for (int i = 0; i < n; i++) {
         LAUNCH(H, OHM_K_SMOOTH, G.g->n(), launch_smooth<T>(gdev(H, *G.g), (const T *)G.e, (T *)G.e2, (const T *)G.r, (const T *)G.eta, (const T *)G.inv,
                             (const T *)G.Ge, (const T *)G.Geta, lamdt, 0, H->s));
@@ -778,20 +787,17 @@ int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt) {
     }
     return OHM_OK;
 }
-
-// V-cycle on base grid m (e_m zeroed by the caller); m = 0 is AMR level 0
 template <typename T>
 int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const ohm_hier_desc &d = H->d;
     GridRef G = base_ref<T>(H, m);
     int st;
-    if ((st = sweeps<T>(H, G, d.nu_pre, lamdt))) return st;
+    if ((st = sweeps<T>(H, G, d.nu_pre, lamdt, true))) return st;  // the level's correction starts at 0
     const bool next_blocked = m < (int)H->mg.size();
     if (next_blocked) {
         GridRef C = base_ref<T>(H, m + 1);
         LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, (T *)C.r, nullptr, nullptr, H->s));
-        CK(cudaMemsetAsync(C.e, 0, (size_t)C.g->n() * 3 * B3 * sizeof(T), H->s));
         if ((st = base_vcycle<T>(H, m + 1, lamdt))) return st;
         if (G.g->octet)
             LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add8<T>(gdev(H, *C.g), (const T *)C.e, (T *)G.e, H->s));
@@ -817,18 +823,13 @@ int vcycle(ohm_hier *H, double lamdt) {
     for (int l = H->nlev - 1; l >= 1; l--) {
         GridRef G = amr_ref<T>(H, l, true);
         const HGrid &g = *G.g;
-        CK(cudaMemsetAsync(G.e, 0, (size_t)g.n() * 3 * B3 * sizeof(T), H->s));
         if (g.nslot) CK(cudaMemsetAsync((T *)H->ghostE + (size_t)g.slot0 * 3 * T3, 0, (size_t)g.nslot * 3 * T3 * sizeof(T), H->s));
-        if ((st = sweeps<T>(H, G, d.nu_pre, lamdt))) return st;
+        if ((st = sweeps<T>(H, G, d.nu_pre, lamdt, true))) return st;  // from e = 0
         GridRef C = amr_ref<T>(H, l - 1, true);
         LAUNCH(H, OHM_K_RESID_RESTRICT, g.n(), launch_resid_restrict<T>(gdev(H, g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, (const T *)G.Ge,
                                     (const T *)G.Geta, lamdt, nullptr, (T *)C.r, nullptr, nullptr, H->s));
     }
-    {
-        GridRef G0 = amr_ref<T>(H, 0, false);
-        CK(cudaMemsetAsync(G0.e, 0, (size_t)G0.g->n() * 3 * B3 * sizeof(T), H->s));
-    }
-    if ((st = base_vcycle<T>(H, 0, lamdt))) return st;
+    if ((st = base_vcycle<T>(H, 0, lamdt))) return st;  // level 0 starts from e = 0 inside
     for (int l = 1; l < H->nlev; l++) {
         GridRef G = amr_ref<T>(H, l, true);
         GridRef C = amr_ref<T>(H, l - 1, true);

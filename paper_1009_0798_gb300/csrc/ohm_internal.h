@@ -102,7 +102,8 @@ cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T 
                              cudaStream_t s);
 
 // The same sweep for pairs of x-adjacent blocks (2q, 2q+1): grids with an even block count whose
-// pairs are x-neighbours and whose blocks all have their 26 neighbours.
+// pairs are x-neighbours and whose blocks all have their 26 neighbours.  e_in = nullptr: the
+// sweep starts from e = 0 (nothing is read for e).
 cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out, const float *r, const float *eta,
                               double lamdt, cudaStream_t s);
 

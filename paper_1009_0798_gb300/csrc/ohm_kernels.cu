@@ -883,6 +883,9 @@ constexpr Ring2 make_ring2() {
 }
 __device__ const Ring2 g_ring2 = make_ring2();
 
+// ZERO: the sweep starts from e = 0 (the first pre-smoothing sweep of a level): the tile's e
+// values are set to zero instead of loaded, and e_in is not read.
+template <bool ZERO>
 __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *__restrict__ e_in, float *__restrict__ e_out,
                                                     const float *__restrict__ r, const float *__restrict__ eta, float coef,
                                                     float lh2) {
@@ -914,6 +917,11 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
         const float *F = c < 3 ? e_in : eta;
         const int nc = c < 3 ? 3 : 1, cc = c < 3 ? c : 0;
         float4 *dst = reinterpret_cast<float4 *>((c < 3 ? tB + c * G::CS : tE) + tk * G::PS + tj * G::RRS + G::OFF);
+        if (ZERO && c < 3) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            dst[0] = z; dst[1] = z; dst[2] = z; dst[3] = z; dst[4] = z;
+            continue;
+        }
         const float2 lo = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)nb[0] * nc + cc) * B3 + rowoff + 6));
         const float4 *pa = reinterpret_cast<const float4 *>(F + ((size_t)nb[1] * nc + cc) * B3 + rowoff);
         const float4 *pb = reinterpret_cast<const float4 *>(F + ((size_t)nb[2] * nc + cc) * B3 + rowoff);
@@ -976,10 +984,15 @@ cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out,
                               double lamdt, cudaStream_t s) {
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = 4 * G20::CS * sizeof(float);
-    static const bool attr = (cudaFuncSetAttribute(k_smooth_rb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
+    static const bool attr = (cudaFuncSetAttribute(k_smooth_rb2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              cudaFuncSetAttribute(k_smooth_rb2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              true);
     (void)attr;
-    k_smooth_rb2<<<g.nblk / 2, 512, sm, s>>>(g, e_in, e_out, r, eta, (float)(lamdt / (2.0 * g.h * g.h)),
-                                             (float)(lamdt / (g.h * g.h)));
+    const float coef = (float)(lamdt / (2.0 * g.h * g.h)), lh2 = (float)(lamdt / (g.h * g.h));
+    if (e_in)
+        k_smooth_rb2<false><<<g.nblk / 2, 512, sm, s>>>(g, e_in, e_out, r, eta, coef, lh2);
+    else  // from e = 0
+        k_smooth_rb2<true><<<g.nblk / 2, 512, sm, s>>>(g, nullptr, e_out, r, eta, coef, lh2);
     return cudaGetLastError();
 }
 
