@@ -94,6 +94,26 @@ ALGO = {
 KRYLOV = 6  # FGMRES restart length of the float32 inner solve in the headline path
 
 
+def smooth_zero_frac(nu_pre: int, nu_post: int) -> float:
+    """Share of a level's float32 sweeps per V-cycle that start from e = 0 (the first
+    pre-smoothing sweep: it reads r and eta and writes e, 28 instead of 40 bytes per cell)."""
+    return 1.0 / (nu_pre + nu_post) if nu_pre >= 1 else 0.0
+
+
+def smooth_bytes(nu_pre: int, nu_post: int) -> float:
+    """Algorithmic bytes per cell of the average float32 sweep launch of a V(nu_pre, nu_post)."""
+    return ALGO[("smooth", 4)]["bytes"] - 12.0 * smooth_zero_frac(nu_pre, nu_post)
+
+
+def smooth_traffic(nu_pre: int, nu_post: int):
+    """DRAM bytes per cell of the average float32 sweep launch, from the committed capture."""
+    t, tz = kernel_traffic("smooth_f32"), kernel_traffic("smooth_f32_zero")
+    if t is None or tz is None:
+        return None
+    f = smooth_zero_frac(nu_pre, nu_post)
+    return (1.0 - f) * t + f * tz
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -405,7 +425,9 @@ def run_ours(args):
         return
     # roofline of the dominant kernel, measured with events inside the timed region
     prof = mixed["prof"]
-    algo = ALGO[(mixed["dom"], mixed["tsize"])]
+    algo = dict(ALGO[(mixed["dom"], mixed["tsize"])])
+    if (mixed["dom"], mixed["tsize"]) == ("smooth", 4):
+        algo["bytes"] = smooth_bytes(*nu)
     per_launch_cells = prof["cells"] / max(prof["launches"], 1)
     sec = prof["ms"] * 1e-3
     if mixed["dom"] == "composite":
@@ -416,7 +438,8 @@ def run_ours(args):
         achieved = algo["bytes"] * prof["cells"] / sec * 1e-9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    tb = kernel_traffic(mixed["dom"] + ("_f32" if mixed["tsize"] == 4 else "_f64"))
+    tb = (smooth_traffic(*nu) if (mixed["dom"], mixed["tsize"]) == ("smooth", 4)
+          else kernel_traffic(mixed["dom"] + ("_f32" if mixed["tsize"] == 4 else "_f64")))
     roof.update({"kernel": mixed["dom"], "launches": prof["launches"], "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
                  "algorithmic_bytes_per_launch": algo["bytes"] * per_launch_cells,
                  "traffic": tb * per_launch_cells if tb is not None else None})
@@ -553,11 +576,13 @@ def run_batched(args):
     ohm.ohm_prof_enable(big["g"], -1)
     hbm_peak, peak_src = peaks()
     sec = prof["ms"] * 1e-3
-    ach = ALGO[("smooth", 4)]["bytes"] * prof["cells"] / max(sec, 1e-12) * 1e-9
+    tn = tuned.get(big["n"], {})
+    sb = smooth_bytes(tn.get("nu_pre", nu[0]), tn.get("nu_post", nu[1]))
+    ach = sb * prof["cells"] / max(sec, 1e-12) * 1e-9
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)", "kernel": f"smooth ({big['n']}^3 class)",
             "launches": prof["launches"], "ms_per_launch": prof["ms"] / max(prof["launches"], 1),
-            "algorithmic_bytes_per_launch": ALGO[("smooth", 4)]["bytes"] * prof["cells"] / max(prof["launches"], 1),
+            "algorithmic_bytes_per_launch": sb * prof["cells"] / max(prof["launches"], 1),
             "traffic": None}
 
     # comparisons: every instance alone through the single-problem API (FGMRES(6), the
