@@ -44,7 +44,9 @@ def args_parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--only", choices=["fgmres", "fgmres_ff", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
-    p.add_argument("--nu", default="3,2", help="pre,post red-black sweeps per level")
+    p.add_argument("--nu", default="3,2", help="pre,post red-black sweeps on level 0")
+    p.add_argument("--nu-coarse", default="1,1",
+                   help="pre,post sweeps on the grids coarser than level 0 on the headline path (0,0 = as --nu)")
     p.add_argument("--n-coarse", type=int, default=4, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
     p.add_argument("--omega", type=float, default=1.2,
@@ -316,13 +318,15 @@ def run_ours(args):
     B = torch.empty_like(B0)
     hbm_peak, peak_src = peaks()
     nu = tuple(int(v) for v in args.nu.split(","))
+    nuc = tuple(int(v) for v in args.nu_coarse.split(","))
     KRYLOV = args.krylov
 
-    def make(precision, krylov=0, omega=1.0):
+    def make(precision, krylov=0, omega=1.0, nu_coarse=(0, 0)):
         g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam,
                                      precision=precision, nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse,
                                      max_outer=400, stream=stream, krylov=krylov,
-                                     inner_tol=args.inner_tol if precision != ohm.OHM_FP64 else 0.0, omega=omega)
+                                     inner_tol=args.inner_tol if precision != ohm.OHM_FP64 else 0.0, omega=omega,
+                                     nu_coarse=nu_coarse)
         ohm.ohm_set_eta(g, eta)
         return g
 
@@ -361,8 +365,8 @@ def run_ours(args):
 
     if args.only:
         prec = {"fp64": ohm.OHM_FP64, "fgmres_ff": ohm.OHM_MIXED_FF}.get(args.only, ohm.OHM_MIXED)
-        g1 = make(prec, KRYLOV if args.only.startswith("fgmres") else 0,
-                  args.omega if args.only.startswith("fgmres") else 1.0)
+        fg = args.only.startswith("fgmres")
+        g1 = make(prec, KRYLOV if fg else 0, args.omega if fg else 1.0, nuc if fg else (0, 0))
         for _ in range(args.warmup):
             run_steps(ohm, g1, B, B0, eta, wl, 1, stream)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -371,13 +375,14 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"only": args.only, "size": args.size, "steps": args.steps, "nu": nu,
                               "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only.startswith("fgmres") else 0,
-                              "inner_tol": args.inner_tol, "omega": args.omega if args.only.startswith("fgmres") else 1.0,
+                              "inner_tol": args.inner_tol, "omega": args.omega if fg else 1.0,
+                              "nu_coarse": nuc if fg else (0, 0),
                               "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos]}),
                   flush=True)
         return
 
     # headline: float32 multigrid, FGMRES-accelerated, inside float64 iterative refinement
-    gm = make(ohm.OHM_MIXED, KRYLOV, args.omega)
+    gm = make(ohm.OHM_MIXED, KRYLOV, args.omega, nuc)
     mixed = timed(gm, ohm.OHM_MIXED)
     # per-solve latency over at least 50 steps: the timed steps plus further ones after the
     # timed region (not part of value)
@@ -393,9 +398,10 @@ def run_ours(args):
     # paper's scheme: float64 V-cycles in float64 defect correction)
     others = {}
     if not args.no_fp64:
-        for name, prec, kr, om in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV, args.omega),
-                                   ("mixed_defect_correction", ohm.OHM_MIXED, 0, 1.0), ("fp64_plain", ohm.OHM_FP64, 0, 1.0)):
-            g2 = make(prec, kr, om)
+        for name, prec, kr, om, nc in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV, args.omega, nuc),
+                                       ("mixed_defect_correction", ohm.OHM_MIXED, 0, 1.0, (0, 0)),
+                                       ("fp64_plain", ohm.OHM_FP64, 0, 1.0, (0, 0))):
+            g2 = make(prec, kr, om, nc)
             others[name] = summary(timed(g2, prec, profile=False))
             if prec == ohm.OHM_MIXED_FF:
                 others[name]["precision"] = ("OHM_MIXED_FF: as the headline, but the outer residual in float-float "
@@ -469,9 +475,9 @@ def run_ours(args):
             "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
             "config": {"workload": f"resistive_bump_{args.size}^3", "cells": cells, "tol": wl.tol,
                        "dt_over_explicit_limit": 100, "cn_steps_per_run": args.steps, "precision": "mixed",
-                       "multigrid": f"V({nu[0]},{nu[1]}) of red-black SOR sweeps (omega {args.omega}), {args.n_coarse} "
-                                    f"coarsest sweeps; float32 inner solve FGMRES({KRYLOV}) right-preconditioned by "
-                                    "the V-cycle; float64 iterative refinement",
+                       "multigrid": f"V({nu[0]},{nu[1]}) on level 0 and V({nuc[0]},{nuc[1]}) below, red-black SOR sweeps "
+                                    f"(omega {args.omega}), {args.n_coarse} coarsest sweeps; float32 inner solve "
+                                    f"FGMRES({KRYLOV}) right-preconditioned by the V-cycle; float64 iterative refinement",
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (402 MB per float64 field vs 129 MB L2), no flush"},
             "latency_ms": {"p50": statistics.median(lat), "p99": p99, "solves": len(lat)},

@@ -94,6 +94,12 @@ typedef struct {
                                    the paper: it changes the iterates, not the converged
                                    solution (1.2 saves 2 of 15 V-cycles per step of the 256^3
                                    resistive bump; 1.5 and above slow convergence down).       */
+    int32_t nu_coarse_pre, nu_coarse_post; /* red-black sweeps before / after the coarse
+                                   correction on the grids coarser than level 0 (the base grid's
+                                   coarsenings and the coarsest-grid solver's grids); both 0 =
+                                   nu_pre / nu_post on every grid, the paper's single schedule.
+                                   Not in the paper (V(3,2) on level 0 with V(1,1) below takes
+                                   the 256^3 step 5% faster with the same V-cycle count).       */
 } ohm_hier_desc;
 
 typedef struct {
@@ -156,7 +162,8 @@ int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes);
  * two-pass smoother a 10^3 tile).  Each candidate runs one step of ohm_cn_step (batches:
  * ohm_cn_step_batch with dt) from B_dev on a private copy (B_dev is not modified), timed
  * with CUDA events; candidates that do not converge are discarded.  The best schedule is
- * then timed with the relaxation factors omega in {1, 1.15, 1.3, 1.45} besides the hierarchy's own.
+ * then timed with V(1,1) on the grids coarser than level 0, and then with the relaxation
+ * factors omega in {1, 1.15, 1.3, 1.45} besides the hierarchy's own.
  * The fastest is kept in the hierarchy and reported.  Allocates one copy of B for the duration of the call.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
@@ -165,6 +172,7 @@ typedef struct {
     double ms;                  /* time of the chosen candidate's step                         */
     int32_t candidates;         /* candidates timed                                            */
     double omega;               /* chosen relaxation factor                                    */
+    int32_t nu_coarse_pre, nu_coarse_post; /* chosen coarse-grid sweeps (0, 0 = as nu_pre/post)  */
 } ohm_tune_result;
 int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol, ohm_tune_result *res);
 

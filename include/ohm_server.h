@@ -46,6 +46,7 @@ typedef struct {
     int32_t krylov;             /* OHM_MIXED(_FF): 0 = defect-correction inner solves, m in 1..11 =
                                    per-instance FGMRES(m) (see ohm_hier_desc)                  */
     double omega;               /* relaxation factor of the sweeps (see ohm_hier_desc); 0 = 1  */
+    int32_t nu_coarse_pre, nu_coarse_post; /* sweeps on the coarser grids (see ohm_hier_desc)   */
 } ohm_server_desc;
 
 typedef struct {

@@ -792,7 +792,10 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const ohm_hier_desc &d = H->d;
     GridRef G = base_ref<T>(H, m);
     int st;
-    if ((st = sweeps<T>(H, G, d.nu_pre, lamdt, true))) return st;  // the level's correction starts at 0
+    // level 0 takes nu_pre / nu_post, its coarsenings the coarse-grid counts when those are set
+    const bool cs = m >= 1 && (d.nu_coarse_pre || d.nu_coarse_post);
+    const int npre = cs ? d.nu_coarse_pre : d.nu_pre, npost = cs ? d.nu_coarse_post : d.nu_post;
+    if ((st = sweeps<T>(H, G, npre, lamdt, true))) return st;  // the level's correction starts at 0
     const bool next_blocked = m < (int)H->mg.size();
     if (next_blocked) {
         GridRef C = base_ref<T>(H, m + 1);
@@ -807,11 +810,13 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
         LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, nullptr, (T *)H->smallbuf[0].r, H->small[0].data(), H->s));
         SmallDev<T> sm = small_dev<T>(H);
-        LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(sm, lamdt, d.nu_pre, d.nu_post, d.n_coarse, H->s));
+        const bool csb = d.nu_coarse_pre || d.nu_coarse_post;  // the small grids are all coarser than level 0
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(sm, lamdt, csb ? d.nu_coarse_pre : d.nu_pre,
+                                                    csb ? d.nu_coarse_post : d.nu_post, d.n_coarse, H->s));
         LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
                                  H->d_err, H->s));
     }
-    return sweeps<T>(H, G, d.nu_post, lamdt);
+    return sweeps<T>(H, G, npost, lamdt);
 }
 
 // One correction-scheme V-cycle over the AMR levels and the base grid.  r on leaf blocks
@@ -1627,6 +1632,7 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     }
     if (d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1) { err = "bad cycle counts"; return false; }
     if (!(d->omega == 0 || (d->omega > 0 && d->omega < 2))) { err = "omega must be 0 (= 1) or in (0, 2)"; return false; }
+    if (d->nu_coarse_pre < 0 || d->nu_coarse_post < 0) { err = "bad coarse-grid sweep counts"; return false; }
     if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision == OHM_FP64)) {
         err = "krylov must be 0, or 1..11 with OHM_MIXED or OHM_MIXED_FF";
         return false;
@@ -1824,6 +1830,27 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
     h->d.nu_post = br.nu_post;
     h->d.n_coarse = br.n_coarse;
     h->smoother = br.smoother;
+    // V(1,1) on the grids coarser than level 0, on the chosen schedule
+    br.nu_coarse_pre = saved.nu_coarse_pre;
+    br.nu_coarse_post = saved.nu_coarse_post;
+    if (!(saved.nu_coarse_pre == 1 && saved.nu_coarse_post == 1)) {
+        h->d.nu_coarse_pre = h->d.nu_coarse_post = 1;
+        reset_graph(h);
+        cudaEventRecord(ev[0], h->s);
+        const int r = step();
+        cudaEventRecord(ev[1], h->s);
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess) st = OHM_ERR_CUDA;
+        ncand++;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (st != OHM_ERR_CUDA && r == OHM_OK && ms < best) {
+            best = ms;
+            br.ms = ms;
+            br.nu_coarse_pre = br.nu_coarse_post = 1;
+        }
+        h->d.nu_coarse_pre = br.nu_coarse_pre;
+        h->d.nu_coarse_post = br.nu_coarse_post;
+    }
     // relaxation factor of the sweeps on the chosen schedule (folded into the inverse diagonals,
     // so they are recomputed for each candidate)
     br.omega = saved.omega;

@@ -108,6 +108,8 @@ ohm_hier_desc structure_desc(const ohm_server *S, const Req *r, int K, void *str
     d.use_graphs = S->d.use_graphs;
     d.stream = stream;
     d.omega = S->d.omega;
+    d.nu_coarse_pre = S->d.nu_coarse_pre;
+    d.nu_coarse_post = S->d.nu_coarse_post;
     return d;
 }
 
@@ -377,7 +379,8 @@ int ohm_server_create(const ohm_server_desc *d, ohm_server **out) {
     if (d->hbm_budget_bytes <= 0 || d->max_batch < 1 || d->max_batch > 4096 || d->n_workers < 1 || d->n_workers > 64 ||
         (d->precision != OHM_FP64 && d->precision != OHM_MIXED && d->precision != OHM_MIXED_FF) || !(d->lambda > 0 && d->lambda <= 1) || !(d->tol >= 0) ||
         d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1 || d->krylov < 0 || d->krylov > 11 ||
-        (d->krylov > 0 && d->precision == OHM_FP64) || !(d->omega == 0 || (d->omega > 0 && d->omega < 2)))
+        (d->krylov > 0 && d->precision == OHM_FP64) || !(d->omega == 0 || (d->omega > 0 && d->omega < 2)) ||
+        d->nu_coarse_pre < 0 || d->nu_coarse_post < 0)
         return OHM_ERR_INVALID;
     ohm_server *S = new ohm_server();
     S->d = *d;

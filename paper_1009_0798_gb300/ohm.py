@@ -37,7 +37,8 @@ class HierDesc(C.Structure):
                 ("block_lijk", C.POINTER(C.c_int32)), ("lam", C.c_double), ("precision", C.c_int32),
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32), ("max_outer", C.c_int32),
                 ("krylov", C.c_int32), ("inner_tol", C.c_double), ("n_instances", C.c_int32),
-                ("use_graphs", C.c_int32), ("stream", C.c_void_p), ("omega", C.c_double)]
+                ("use_graphs", C.c_int32), ("stream", C.c_void_p), ("omega", C.c_double),
+                ("nu_coarse_pre", C.c_int32), ("nu_coarse_post", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -47,7 +48,8 @@ class StepStats(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32), ("smoother", C.c_int32),
-                ("ms", C.c_double), ("candidates", C.c_int32), ("omega", C.c_double)]
+                ("ms", C.c_double), ("candidates", C.c_int32), ("omega", C.c_double),
+                ("nu_coarse_pre", C.c_int32), ("nu_coarse_post", C.c_int32)]
 
 
 _lib = None
@@ -139,7 +141,7 @@ class Hierarchy:
 
 
 def _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coarse, max_outer, raw_stream, krylov,
-               inner_tol, n_instances, use_graphs, omega=0.0):
+               inner_tol, n_instances, use_graphs, omega=0.0, nu_coarse=(0, 0)):
     d = HierDesc()
     d.base_cells[:] = [int(v) for v in base_cells]
     d.dx0 = float(dx0)
@@ -155,24 +157,26 @@ def _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coars
     d.use_graphs = 1 if use_graphs else 0
     d.stream = C.c_void_p(raw_stream)
     d.omega = float(omega)
+    d.nu_coarse_pre, d.nu_coarse_post = int(nu_coarse[0]), int(nu_coarse[1])
     return d
 
 
 def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
                          nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50,
                          stream=None, krylov: int = 0, inner_tol: float = 0.0, n_instances: int = 0,
-                         use_graphs: bool = False, omega: float = 0.0) -> Hierarchy:
+                         use_graphs: bool = False, omega: float = 0.0, nu_coarse=(0, 0)) -> Hierarchy:
     """blocks: int32 [nblocks, 4] rows (level, bi, bj, bk) sorted by level (one instance).
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None for torch's current stream.
     n_instances >= 1 makes a batch of that many independent instances (ohm_cn_step_batch).
-    omega: relaxation factor of the red-black sweeps (0 = 1, the paper's Gauss-Seidel)."""
+    omega: relaxation factor of the red-black sweeps (0 = 1, the paper's Gauss-Seidel).
+    nu_coarse: (pre, post) sweeps on the grids coarser than level 0; (0, 0) = nu_pre, nu_post."""
     import torch
     blocks = np.ascontiguousarray(blocks, dtype=np.int32)
     if stream is None:
         stream = torch.cuda.current_stream()
     raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     d = _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coarse, max_outer, raw, krylov,
-                   inner_tol, n_instances, use_graphs, omega)
+                   inner_tol, n_instances, use_graphs, omega, nu_coarse)
     h = C.c_void_p()
     _check(lib().ohm_create_hierarchy(C.byref(d), C.byref(h)), "ohm_create_hierarchy")
     return Hierarchy(h, len(blocks) * max(1, int(n_instances)), lam, precision != OHM_FP64, int(n_instances))
@@ -180,11 +184,11 @@ def ohm_create_hierarchy(base_cells, dx0: float, blocks, lam: float = 0.5, preci
 
 def ohm_hierarchy_bytes(base_cells, dx0: float, blocks, lam: float = 0.5, precision: int = OHM_FP64,
                         nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 50, krylov: int = 0,
-                        inner_tol: float = 0.0, n_instances: int = 0, omega: float = 0.0) -> int:
+                        inner_tol: float = 0.0, n_instances: int = 0, omega: float = 0.0, nu_coarse=(0, 0)) -> int:
     """Device bytes ohm_create_hierarchy would allocate for this description (no allocation)."""
     blocks = np.ascontiguousarray(blocks, dtype=np.int32)
     d = _make_desc(base_cells, dx0, blocks, lam, precision, nu_pre, nu_post, n_coarse, max_outer, 0, krylov,
-                   inner_tol, n_instances, False, omega)
+                   inner_tol, n_instances, False, omega, nu_coarse)
     out = C.c_int64()
     _check(lib().ohm_hierarchy_bytes(C.byref(d), C.byref(out)), "ohm_hierarchy_bytes")
     return int(out.value)
@@ -213,7 +217,7 @@ def ohm_autotune(h: Hierarchy, B, dt, tol: float) -> dict:
     r = TuneResult()
     _check(lib().ohm_autotune(h.handle, _ptr(B, h.nblocks * 1536, "B"), arr, float(tol), C.byref(r)), "ohm_autotune")
     return {"nu_pre": r.nu_pre, "nu_post": r.nu_post, "n_coarse": r.n_coarse, "smoother": r.smoother, "ms": r.ms,
-            "candidates": r.candidates, "omega": r.omega}
+            "candidates": r.candidates, "omega": r.omega, "nu_coarse": (r.nu_coarse_pre, r.nu_coarse_post)}
 
 
 def ohm_set_eta(h: Hierarchy, eta) -> None:

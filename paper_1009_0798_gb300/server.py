@@ -18,7 +18,8 @@ class ServerDesc(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch", C.c_int32), ("n_workers", C.c_int32),
                 ("precision", C.c_int32), ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("n_coarse", C.c_int32),
                 ("max_outer", C.c_int32), ("lam", C.c_double), ("tol", C.c_double), ("use_graphs", C.c_int32),
-                ("krylov", C.c_int32), ("omega", C.c_double)]
+                ("krylov", C.c_int32), ("omega", C.c_double), ("nu_coarse_pre", C.c_int32),
+                ("nu_coarse_post", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -64,10 +65,11 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int, max_batch: int = 8, n_workers: int = 4, precision: int = 1,
                  nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 16, max_outer: int = 400, lam: float = 0.5,
-                 tol: float = 1e-9, use_graphs: bool = False, krylov: int = 0, omega: float = 0.0):
+                 tol: float = 1e-9, use_graphs: bool = False, krylov: int = 0, omega: float = 0.0,
+                 nu_coarse=(0, 0)):
         d = ServerDesc(int(hbm_budget_bytes), int(max_batch), int(n_workers), int(precision), int(nu_pre),
                        int(nu_post), int(n_coarse), int(max_outer), float(lam), float(tol), 1 if use_graphs else 0,
-                       int(krylov), float(omega))
+                       int(krylov), float(omega), int(nu_coarse[0]), int(nu_coarse[1]))
         h = C.c_void_p()
         _ohm._check(_lib().ohm_server_create(C.byref(d), C.byref(h)), "ohm_server_create")
         self._h = h

@@ -52,7 +52,7 @@ def _desc(libohm, base=(16, 16, 16), blocks=None, **kw):
 
 
 @pytest.mark.parametrize("case", ["bad_base", "unsorted", "duplicate", "incomplete_base", "bad_lambda",
-                                  "bad_counts", "not_nested", "incomplete_octet", "krylov_fp64", "bad_precision", "omega_2", "omega_negative",
+                                  "bad_counts", "not_nested", "incomplete_octet", "krylov_fp64", "bad_precision", "omega_2", "omega_negative", "coarse_nu_negative",
                                   "bad_inner_tol"])
 def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
     from paper_1009_0798_gb300 import workloads as W
@@ -82,6 +82,8 @@ def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
         kw["omega"] = 2.0
     elif case == "omega_negative":
         kw["omega"] = -0.5
+    elif case == "coarse_nu_negative":
+        kw["nu_coarse"] = (-1, 1)
     elif case == "not_nested":
         # a level-2 octet whose parent's neighbourhood is missing at level 1
         h = W.refined(32, 32, 32, 1.0 / 32, [lambda lo, hi: lo[0] < 0.2 and lo[1] < 0.2 and lo[2] < 0.2])

@@ -53,17 +53,19 @@ def test_fp64_fixed_schedule_elementwise(ohm, case):
     assert st["rel_l2"] == pytest.approx(info["history"][-1], rel=1e-8)
 
 
-# (precision, nu_pre, nu_post, n_coarse, omega): the bench's headline schedule, the same with the
-# float-float outer residual, and the paper's Gauss-Seidel V(2,2)
-MIXED_CONFIGS = {"headline": (1, 3, 2, 4, 1.2), "float_float": (2, 3, 2, 4, 1.2), "gauss_seidel_v22": (1, 2, 2, 16, 1.0)}
+# (precision, nu_pre, nu_post, n_coarse, omega, nu_coarse): the bench's headline schedule, the same
+# with the float-float outer residual, and the paper's Gauss-Seidel V(2,2)
+MIXED_CONFIGS = {"headline": (1, 3, 2, 4, 1.2, (1, 1)), "float_float": (2, 3, 2, 4, 1.2, (1, 1)),
+                 "gauss_seidel_v22": (1, 2, 2, 16, 1.0, (0, 0))}
 
 
 @pytest.mark.parametrize("cfg", list(MIXED_CONFIGS))
 def test_mixed_fgmres_converged_residual_checked_by_oracle(ohm, case, cfg):
     name, wl, o, b = case
-    prec, n1, n2, nc, om = MIXED_CONFIGS[cfg]
+    prec, n1, n2, nc, om, nuc = MIXED_CONFIGS[cfg]
     g = ohm.ohm_create_hierarchy(wl.hier.base_cells, wl.hier.dx0, wl.hier.blocks, lam=wl.lam, precision=prec,
-                                 nu_pre=n1, nu_post=n2, n_coarse=nc, max_outer=200, krylov=6, omega=om)
+                                 nu_pre=n1, nu_post=n2, n_coarse=nc, max_outer=200, krylov=6, omega=om,
+                                 nu_coarse=nuc)
     B = dev(b)
     st = ohm.ohm_cn_step(g, B, dev(wl.eta), wl.dt, wl.tol)
     assert st["converged"] and st["rel_l2"] <= wl.tol

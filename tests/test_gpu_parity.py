@@ -319,18 +319,19 @@ def test_mixed_nonfinite_inputs_report_nonfinite(ohm, bad, precision):
     assert ei.value.status == ohm.OHM_ERR_NONFINITE
 
 
-@pytest.mark.parametrize("precision,krylov", [(0, 0), (1, 0), (1, 4)])
-def test_relaxed_sweeps_reach_the_same_solution(ohm, orc, precision, krylov):
-    """omega = 1.25 changes the multigrid iterates, not the converged solution: the step
-    reaches the oracle's converged Gauss-Seidel solution (float64: 1e-11, both sides at 1e-13;
-    mixed: 1e-9)."""
+@pytest.mark.parametrize("precision,krylov,nu_coarse", [(0, 0, (0, 0)), (1, 0, (0, 0)), (1, 4, (0, 0)),
+                                                      (0, 0, (1, 1)), (1, 4, (1, 1)), (2, 4, (1, 0))])
+def test_relaxed_sweeps_reach_the_same_solution(ohm, orc, precision, krylov, nu_coarse):
+    """omega = 1.25 and other sweep counts on the coarser grids change the multigrid iterates,
+    not the converged solution: the step reaches the oracle's converged Gauss-Seidel V(2,2)
+    solution (float64: 1e-11, both sides at 1e-13; mixed: 1e-9)."""
     h = HIERS["amr_3level"]()
     b, eta = rand_fields(h, 21, 1.0)
     o = orc.Oracle(h, 0.5, eta)
     b = o.sync_down(b)
     dt = 4.0 * h.dx(h.nlevels - 1) ** 2
     want, _ = o.cn_step(b, dt, 1e-14, 2, 2, 8, 80)
-    g = make(ohm, h, precision=precision, max_outer=80, krylov=krylov, omega=1.25)
+    g = make(ohm, h, precision=precision, max_outer=80, krylov=krylov, omega=1.25, nu_coarse=nu_coarse)
     B = dev(b)
     st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-13 if precision == 0 else 1e-11)
     assert st["converged"]
