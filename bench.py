@@ -61,6 +61,7 @@ def args_parse():
     p.add_argument("--batch-krylov", type=int, default=6,
                    help="batched512 / serving: FGMRES restart length of each instance's inner solve (0: defect correction)")
     p.add_argument("--requests", type=int, default=600, help="serving: requests in the stream")
+    p.add_argument("--serve-nu-coarse", default="1,1", help="serving: pre,post sweeps on the grids coarser than level 0")
     p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     p.add_argument("--inner-tol", type=float, default=1e-5,
                    help="residual reduction asked of each float32 inner solve (mixed precision)")
@@ -808,10 +809,11 @@ def run_serving(args):
     torch.cuda.init()
     reqs = serving_requests(args.requests, args.rate)
     budget = 60 << 30
-    # V(4,4) with 4 coarsest sweeps and omega 1.3: the schedule the autotuner picks for every
-    # class of the batched workload
+    # V(4,4) with 4 coarsest sweeps, omega 1.3 and V(1,1) on the coarser grids: the schedule the
+    # autotuner picks for most classes of the batched workload
     cfg = dict(hbm_budget_bytes=budget, max_batch=8, n_workers=6, precision=1, tol=1e-9, use_graphs=True,
-               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400, krylov=args.batch_krylov, omega=1.3)
+               nu_pre=4, nu_post=4, n_coarse=4, max_outer=400, krylov=args.batch_krylov, omega=1.3,
+               nu_coarse=tuple(int(v) for v in args.serve_nu_coarse.split(",")))
     # warm-up service: one request per class (kernels loaded, batches of each class built once)
     with server.Server(**cfg) as s:
         seen = {}
@@ -865,8 +867,8 @@ def run_serving(args):
                        "mix": "70% uniform 32^3-128^3 (edges " + ",".join(map(str, SERVE_EDGES)) + "), 30% 2-level AMR",
                        "hbm_budget_gb": budget / 2 ** 30, "max_batch": cfg["max_batch"], "n_workers": cfg["n_workers"],
                        "graphs": True, "tol": 1e-9, "parallelism": f"replicas x{ws}",
-                       "multigrid": f"V({cfg['nu_pre']},{cfg['nu_post']}), omega {cfg['omega']}, {cfg['n_coarse']} coarsest "
-                                    f"sweeps, FGMRES({cfg['krylov']}) inner solves"},
+                       "multigrid": f"V({cfg['nu_pre']},{cfg['nu_post']}) on level 0, V{cfg['nu_coarse']} below, omega "
+                                    f"{cfg['omega']}, {cfg['n_coarse']} coarsest sweeps, FGMRES({cfg['krylov']}) inner solves"},
             "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
             "solves_per_s": len(reqs) / span, "offered_rate_per_s": args.rate,
             "span_s": span, "converged": ok, "alone_vs_mix_identical": same,
