@@ -45,9 +45,9 @@ def args_parse():
     p.add_argument("--only", choices=["fgmres", "fgmres_ff", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
     p.add_argument("--nu", default="3,2", help="pre,post red-black sweeps on level 0")
-    p.add_argument("--nu-coarse", default="1,1",
+    p.add_argument("--nu-coarse", default="1,0",
                    help="pre,post sweeps on the grids coarser than level 0 on the headline path (0,0 = as --nu)")
-    p.add_argument("--n-coarse", type=int, default=4, help="sweeps on the coarsest grid")
+    p.add_argument("--n-coarse", type=int, default=2, help="sweeps on the coarsest grid")
     p.add_argument("--krylov", type=int, default=6, help="FGMRES restart length of the headline path")
     p.add_argument("--omega", type=float, default=1.2,
                    help="relaxation factor of the red-black sweeps on the headline path (1 = the paper's "

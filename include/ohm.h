@@ -162,7 +162,7 @@ int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes);
  * two-pass smoother a 10^3 tile).  Each candidate runs one step of ohm_cn_step (batches:
  * ohm_cn_step_batch with dt) from B_dev on a private copy (B_dev is not modified), timed
  * with CUDA events; candidates that do not converge are discarded.  The best schedule is
- * then timed with V(1,1) on the grids coarser than level 0, and then with the relaxation
+ * then timed with V(1,1) and V(1,0) on the grids coarser than level 0, then with the relaxation
  * factors omega in {1, 1.15, 1.3, 1.45} besides the hierarchy's own.
  * The fastest is kept in the hierarchy and reported.  Allocates one copy of B for the duration of the call.
  * ------------------------------------------------------------------------------------- */

@@ -1830,27 +1830,34 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
     h->d.nu_post = br.nu_post;
     h->d.n_coarse = br.n_coarse;
     h->smoother = br.smoother;
-    // V(1,1) on the grids coarser than level 0, on the chosen schedule
+    // V(1,1) and V(1,0) on the grids coarser than level 0, on the chosen schedule
     br.nu_coarse_pre = saved.nu_coarse_pre;
     br.nu_coarse_post = saved.nu_coarse_post;
-    if (!(saved.nu_coarse_pre == 1 && saved.nu_coarse_post == 1)) {
-        h->d.nu_coarse_pre = h->d.nu_coarse_post = 1;
+    const int cnu[2][2] = {{1, 1}, {1, 0}};
+    for (int q = 0; q < 2 && st != OHM_ERR_CUDA; q++) {
+        if (saved.nu_coarse_pre == cnu[q][0] && saved.nu_coarse_post == cnu[q][1]) continue;
+        h->d.nu_coarse_pre = cnu[q][0];
+        h->d.nu_coarse_post = cnu[q][1];
         reset_graph(h);
         cudaEventRecord(ev[0], h->s);
         const int r = step();
         cudaEventRecord(ev[1], h->s);
-        if (cudaEventSynchronize(ev[1]) != cudaSuccess) st = OHM_ERR_CUDA;
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+            st = OHM_ERR_CUDA;
+            break;
+        }
         ncand++;
         float ms = 0;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (st != OHM_ERR_CUDA && r == OHM_OK && ms < best) {
+        if (r == OHM_OK && ms < best) {
             best = ms;
             br.ms = ms;
-            br.nu_coarse_pre = br.nu_coarse_post = 1;
+            br.nu_coarse_pre = cnu[q][0];
+            br.nu_coarse_post = cnu[q][1];
         }
-        h->d.nu_coarse_pre = br.nu_coarse_pre;
-        h->d.nu_coarse_post = br.nu_coarse_post;
     }
+    h->d.nu_coarse_pre = br.nu_coarse_pre;
+    h->d.nu_coarse_post = br.nu_coarse_post;
     // relaxation factor of the sweeps on the chosen schedule (folded into the inverse diagonals,
     // so they are recomputed for each candidate)
     br.omega = saved.omega;
