@@ -433,19 +433,21 @@ def run_ours(args):
             return ev
 
         def pipeline(n):
+            # ohm_cn_step returns when its step is done, so the next upload is enqueued first:
+            # its buffers were last read by step k-1 (finished) and its download (earlier on cs)
             up = upload(0)
             for k in range(n):
+                nxt = upload(k + 1) if k + 1 < n else None
                 stream.wait_event(up)
                 st = ohm.ohm_cn_step(gm, Bd[k % 2], Ed[k % 2], wl.dt, wl.tol)
                 if not st["converged"]:
                     raise RuntimeError(f"e2e step {k} did not converge: {st}")
                 done = torch.cuda.Event()
                 done.record(stream)
-                if k + 1 < n:
-                    up = upload(k + 1)
                 with torch.cuda.stream(cs):
                     cs.wait_event(done)
                     outs[k % 2].copy_(Bd[k % 2], non_blocking=True)
+                up = nxt
 
         pipeline(2)  # warm-up
         torch.cuda.synchronize()
