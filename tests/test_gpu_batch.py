@@ -122,21 +122,24 @@ def test_mixed_batch_converges_to_oracle(ohm, orc, name, precision):
 
 @pytest.mark.parametrize("graphs", [False, True])
 @pytest.mark.parametrize("precision", [1, 2])
-def test_instance_same_bits_alone_and_in_batch(ohm, graphs, precision):
+@pytest.mark.parametrize("sched", ["paper", "relaxed"])
+def test_instance_same_bits_alone_and_in_batch(ohm, graphs, precision, sched):
     """An instance stepped alone (K = 1) and inside a batch of 5 with other eta, dt and data,
-    some of them inactive, gives identical bits; inactive instances are left untouched."""
+    some of them inactive, gives identical bits; inactive instances are left untouched.  Also
+    with omega 1.3, V(3,2) on level 0 and V(1,0) on the coarser grids."""
     h = amr_two_level(16)
     K = 5
     bs, etas = instances(h, K, 60)
     dts = [(2.0 + q) * h.dx(1) ** 2 for q in range(K)]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        g1 = make(ohm, h, 1, precision=precision, stream=stream, use_graphs=graphs)
+        kw = {} if sched == "paper" else dict(omega=1.3, nu_pre=3, nu_post=2, nu_coarse=(1, 0))
+        g1 = make(ohm, h, 1, precision=precision, stream=stream, use_graphs=graphs, **kw)
         ohm.ohm_set_eta(g1, dev(etas[2]))
         B1 = dev(bs[2])
         s1, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[2]], 1e-9)
         s1b, st1b = ohm.ohm_cn_step_batch(g1, B1, [dts[2]], 1e-9)  # second step: graph replay
-        gK = make(ohm, h, K, precision=precision, stream=stream, use_graphs=graphs)
+        gK = make(ohm, h, K, precision=precision, stream=stream, use_graphs=graphs, **kw)
         ohm.ohm_set_eta(gK, dev(stack(h, etas)))
         BK = dev(stack(h, bs))
         active = [1, 0, 1, 1, 0]
