@@ -910,6 +910,61 @@ template cudaError_t launch_smooth_rb<float>(const GridDev &, const float *, flo
 template cudaError_t launch_smooth_rb<double>(const GridDev &, const double *, double *, const double *, const double *,
                                               double, cudaStream_t);
 
+// The first sweep from e = 0, where the red colour pass reduces to e = omega r / (1 + alpha)
+// (every flux of the pre-pass state vanishes) and the black pass sees red values at the face
+// neighbours of a black cell and zeros at its edge neighbours and at itself.  The two updates
+// below are rb_update with those zeros folded in: every dropped term is an exact +-0 in
+// rb_update, so the results are the same bits (up to the sign of a zero).  The tangential
+// difference of a black cell is the same for its two faces along an axis, so a black update
+// reads 31 tile values instead of about 52.
+template <typename T, typename G>
+__device__ __forceinline__ void alpha_of(const T *__restrict__ tE, int p, T lh2, T al[3]) {
+    const T e0 = tE[p];
+    const T sx = e0 + T(0.5) * (tE[p + 1] + tE[p - 1]);
+    const T sy = e0 + T(0.5) * (tE[p + G::RRS] + tE[p - G::RRS]);
+    const T sz = e0 + T(0.5) * (tE[p + G::PS] + tE[p - G::PS]);
+    al[0] = lh2 * (sy + sz);
+    al[1] = lh2 * (sz + sx);
+    al[2] = lh2 * (sx + sy);
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ void red_from_zero(const T *__restrict__ tE, int p, T lh2, const T rr[3], T out[3],
+                                              T omega) {
+    T al[3];
+    alpha_of<T, G>(tE, p, lh2, al);
+#pragma unroll
+    for (int c = 0; c < 3; c++) out[c] = fast_div(omega * rr[c], T(1) + al[c]);
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ void black_after_zero(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef,
+                                                 T lh2, const T rr[3], T out[3], T omega) {
+    const T *Bx = tB, *By = tB + G::CS, *Bz = tB + 2 * G::CS;
+    const int sx = 1, sy = G::RRS, sz = G::PS;
+    const T e0 = tE[p];
+    // x faces: flux components y (tangential difference along y) and z
+    const T txy = Bx[p + sy] - Bx[p - sy], txz = Bx[p + sz] - Bx[p - sz];
+    const T exl = tE[p - sx] + e0, exh = e0 + tE[p + sx];
+    const T xl1 = exl * (quarter(txy) - (-By[p - sx])), xl2 = exl * (quarter(txz) - (-Bz[p - sx]));
+    const T xh1 = exh * (quarter(txy) - By[p + sx]), xh2 = exh * (quarter(txz) - Bz[p + sx]);
+    // y faces: components x and z
+    const T tyx = By[p + sx] - By[p - sx], tyz = By[p + sz] - By[p - sz];
+    const T eyl = tE[p - sy] + e0, eyh = e0 + tE[p + sy];
+    const T yl1 = eyl * (quarter(tyx) - (-Bx[p - sy])), yl2 = eyl * (quarter(tyz) - (-Bz[p - sy]));
+    const T yh1 = eyh * (quarter(tyx) - Bx[p + sy]), yh2 = eyh * (quarter(tyz) - Bz[p + sy]);
+    // z faces: components x and y
+    const T tzx = Bz[p + sx] - Bz[p - sx], tzy = Bz[p + sy] - Bz[p - sy];
+    const T ezl = tE[p - sz] + e0, ezh = e0 + tE[p + sz];
+    const T zl1 = ezl * (quarter(tzx) - (-Bx[p - sz])), zl2 = ezl * (quarter(tzy) - (-By[p - sz]));
+    const T zh1 = ezh * (quarter(tzx) - Bx[p + sz]), zh2 = ezh * (quarter(tzy) - By[p + sz]);
+    const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
+    T al[3];
+    alpha_of<T, G>(tE, p, lh2, al);
+#pragma unroll
+    for (int c = 0; c < 3; c++) out[c] = fast_div(omega * (rr[c] - coef * dv[c]), T(1) + al[c]);
+}
+
 // ------------------------------------------------------------------ fused sweep on brick pairs
 // The fused sweep above for two x-adjacent blocks A = 2q and B = 2q + 1 per thread block (512
 // threads): a 20 x 12 x 12 tile (two-cell halo) shares its halo and ring between the two
@@ -968,8 +1023,8 @@ constexpr Ring2 make_ring2() {
 }
 __device__ const Ring2 g_ring2 = make_ring2();
 
-// ZERO: the sweep starts from e = 0 (the first pre-smoothing sweep of a level): the tile's e
-// values are set to zero instead of loaded, and e_in is not read.
+// ZERO: the sweep starts from e = 0 (the first pre-smoothing sweep of a level): e_in is not read,
+// only eta is staged, the red pass is pointwise and the black pass reads only red values.
 template <bool ZERO>
 __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *__restrict__ e_in, float *__restrict__ e_out,
                                                     const float *__restrict__ r, const float *__restrict__ eta, float coef,
@@ -991,7 +1046,8 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     // one task per (field component, tile row): the 20 values of the row (halo pair, 8 + 8
     // interior cells, halo pair) as five 16-byte stores; each quarter-warp takes 4 rows of 2
     // consecutive planes, whose 16-byte bank groups are distinct (plane stride = 4 mod 32)
-    for (int task = threadIdx.x; task < 4 * 144; task += blockDim.x) {
+    // from e = 0 only eta is staged (e is never read before the red values are written)
+    for (int task = ZERO ? 3 * 144 + threadIdx.x : threadIdx.x; task < 4 * 144; task += blockDim.x) {
         const int c = task / 144, u = task - c * 144;
         const int q = u >> 3, w = u & 7;
         const int tk = 2 * (q / 3) + (w >> 2), tj = 4 * (q % 3) + (w & 3);
@@ -1002,11 +1058,6 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
         const float *F = c < 3 ? e_in : eta;
         const int nc = c < 3 ? 3 : 1, cc = c < 3 ? c : 0;
         float4 *dst = reinterpret_cast<float4 *>((c < 3 ? tB + c * G::CS : tE) + tk * G::PS + tj * G::RRS + G::OFF);
-        if (ZERO && c < 3) {
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            dst[0] = z; dst[1] = z; dst[2] = z; dst[3] = z; dst[4] = z;
-            continue;
-        }
         const float2 lo = __ldg(reinterpret_cast<const float2 *>(F + ((size_t)nb[0] * nc + cc) * B3 + rowoff + 6));
         const float4 *pa = reinterpret_cast<const float4 *>(F + ((size_t)nb[1] * nc + cc) * B3 + rowoff);
         const float4 *pb = reinterpret_cast<const float4 *>(F + ((size_t)nb[2] * nc + cc) * B3 + rowoff);
@@ -1046,9 +1097,14 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     float nv0[3], nv1[3];
     const int p0 = G::at(ir + 2, j + 2, k + 2);
     const float om = (float)g.omega;
-    rb_update<float, G>(tB, tE, p0, coef, lh2, rr0, nv0, om);
-    if (p1 >= 0) rb_update<float, G>(tB, tE, p1, coef, lh2, rr1, nv1, om);
-    __syncthreads();
+    if constexpr (ZERO) {  // nothing of e is read: no barrier before the red values are stored
+        red_from_zero<float, G>(tE, p0, lh2, rr0, nv0, om);
+        if (p1 >= 0) red_from_zero<float, G>(tE, p1, lh2, rr1, nv1, om);
+    } else {
+        rb_update<float, G>(tB, tE, p0, coef, lh2, rr0, nv0, om);
+        if (p1 >= 0) rb_update<float, G>(tB, tE, p1, coef, lh2, rr1, nv1, om);
+        __syncthreads();
+    }
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         tB[c * G::CS + p0] = nv0[c];
@@ -1057,7 +1113,10 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     __syncthreads();
     // black cells of the brick from the post-red state, then both blocks are written out
     float out[3];
-    rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out, om);
+    if constexpr (ZERO)  // black cells read only red neighbours (their black neighbours are 0)
+        black_after_zero<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out, om);
+    else
+        rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out, om);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         e_out[((size_t)own * 3 + c) * B3 + cb] = out[c];
