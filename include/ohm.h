@@ -118,7 +118,9 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out);
 
 /* Copies eta (> 0 and finite, [nblocks][8][8][8], every block including covered ones) into
  * the hierarchy and derives the coarse-fine eta ghosts and the multigrid eta (mean of the 8
- * children, Sec. 2.2).  Returns OHM_ERR_INVALID for a NULL pointer. */
+ * children, Sec. 2.2).  When eta is already set and the new values are bit-identical, only the
+ * comparison runs (one pass over eta and a wait for its result) and the derived data are kept.
+ * Returns OHM_ERR_INVALID for a NULL pointer. */
 int ohm_set_eta(ohm_hier *h, const double *eta_dev);
 
 /* One theta-scheme step, Sec. 2.1-2.3: S = b - (1-lambda) dt div f(b) (Eq. 14), then

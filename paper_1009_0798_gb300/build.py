@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libohm.so")
-SOURCES = ["ohm_kernels.cu", "ohm_host.cpp", "ohm_static.cu", "ohm_server.cpp"]
+SOURCES = ["ohm_kernels.cu", "ohm_host.cpp", "ohm_static.cu", "ohm_server.cpp", "ohm_util.cu"]
 HEADERS = ["ohm_internal.h", os.path.join("..", "..", "include", "ohm.h"),
            os.path.join("..", "..", "include", "ohm_server.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

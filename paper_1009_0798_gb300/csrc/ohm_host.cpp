@@ -1743,6 +1743,18 @@ int ohm_set_eta(ohm_hier *h, const double *eta_dev) {
         h->eta_set = true;
         return OHM_OK;
     }
+    if (h->eta_set) {
+        // the same values again (a time loop passing its eta every step): the coarse levels,
+        // ghosts and inverse diagonals derived from them are still valid
+        int *flag = (int *)(h->dnorm + 6);
+        CK(cudaMemsetAsync(flag, 0, sizeof(int), h->s));
+        CK(launch_differs(eta_dev, h->eta64, (size_t)h->nblocks * B3, flag, h->s));
+        CK(cudaMemcpyAsync(h->hnorm + 24, flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        int differs;
+        memcpy(&differs, h->hnorm + 24, sizeof(int));
+        if (!differs) return OHM_OK;
+    }
     CK(cudaMemcpyAsync(h->eta64, eta_dev, (size_t)h->nblocks * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     int st = h->mixed ? eta_derive<float>(h) : eta_derive<double>(h);
     if (st) return st;

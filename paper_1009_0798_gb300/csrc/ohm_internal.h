@@ -175,6 +175,9 @@ cudaError_t launch_small_setup(const SmallDev<T> &sm, double lamdt, bool eta_cha
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS *src, TD *dst, size_t n, cudaStream_t s);
 
+// *flag = 1 if the n float64 values of a and b differ in any bit (flag is not cleared here)
+cudaError_t launch_differs(const double *a, const double *b, size_t n, int *flag, cudaStream_t s);
+
 // Krylov vector operations (float32 fields [nblk][3][512]); at most KMAX vectors at once.
 constexpr int KMAX = 12;
 struct VecSet {

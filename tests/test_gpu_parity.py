@@ -338,6 +338,35 @@ def test_relaxed_sweeps_reach_the_same_solution(ohm, orc, precision, krylov, nu_
     assert rel_err(host(B), want.ravel()) < (1e-11 if precision == 0 else 1e-9)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_eta_again_same_and_changed_values(ohm, precision):
+    """Setting eta values that are already set keeps the derived data; changing a single value
+    (in another buffer) re-derives everything: each step gives the bits of a fresh hierarchy
+    set once with that eta."""
+    h = HIERS["amr_2level"]()
+    b, eta = rand_fields(h, 31, 1.0)
+    eta2 = eta.copy()
+    eta2[h.nblocks // 2, 0, 3, 4, 5] *= 1.5
+    dt = 3.0 * h.dx(h.nlevels - 1) ** 2
+
+    def fresh(e):
+        g = make(ohm, h, precision=precision, max_outer=60)
+        B = dev(b)
+        ohm.ohm_cn_step(g, B, dev(e), dt, 1e-10)
+        return host(B)
+
+    g = make(ohm, h, precision=precision, max_outer=60)
+    out = []
+    for e in (eta, eta.copy(), eta2, eta2.copy()):
+        B = dev(b)
+        ohm.ohm_cn_step(g, B, dev(e), dt, 1e-10)
+        out.append(host(B))
+    want1, want2 = fresh(eta), fresh(eta2)
+    assert np.array_equal(out[0], want1) and np.array_equal(out[1], want1)
+    assert np.array_equal(out[2], want2) and np.array_equal(out[3], want2)
+    assert not np.array_equal(want1, want2)
+
+
 def test_fgmres_takes_fewer_cycles_than_defect_correction(ohm):
     """Same converged tolerance, fewer V-cycles with the Krylov-accelerated inner solve on a
     stiff case (3-decade eta, dt = 100x the explicit limit)."""
