@@ -1805,9 +1805,9 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
     double best = INFINITY;
     ohm_tune_result br{};
     int ncand = 0;
-    for (int a = 0; a < 6 && (st == OHM_OK || st == OHM_ERR_NOT_CONVERGED); a++)
-        for (int c = 0; c < 2; c++)
-            for (int sm = 0; sm < (h->mixed ? 2 : 1); sm++) {
+    for (int a = 0; a < 6 && st != OHM_ERR_CUDA && (st == OHM_OK || st == OHM_ERR_NOT_CONVERGED); a++)
+        for (int c = 0; c < 2 && st != OHM_ERR_CUDA; c++)
+            for (int sm = 0; sm < (h->mixed ? 2 : 1) && st != OHM_ERR_CUDA; sm++) {
                 h->d.nu_pre = nus[a][0];
                 h->d.nu_post = nus[a][1];
                 h->d.n_coarse = ncs[c];
