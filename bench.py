@@ -7,9 +7,13 @@ largest eta, consecutive CN steps each converged to ||R||/||S|| <= 1e-9.  One be
 one CN step (source, defect-correction cycles of residual + V-cycle + update).
 
 Metric: cell-steps/s = cells x CN steps / device time.  `value` is the mixed-precision path
-(FP32 multigrid inside FP64 defect correction); the plain FP64 path is reported beside it.
-The oracle (FP64 CPU reference) is timed on the host cores as `cpu_baseline`, and is the
-`--impl reference` arm.
+(FP32 multigrid, FGMRES-accelerated, inside FP64 iterative refinement; red-black SOR sweeps
+with V(3,2) on level 0 and V(1,0) below); the plain FP64 path (the paper's Gauss-Seidel defect
+correction), the same with the paper's defect correction in mixed precision, and the
+float-float outer residual (OHM_MIXED_FF) are reported beside it.  `e2e` repeats the step
+through the public API with pinned host buffers.  The oracle (FP64 CPU reference) is timed on
+the host cores as `cpu_baseline`, and is the `--impl reference` arm.  `--workload batched512`
+and `--workload serving` measure the batched hierarchies and the solve service.
 """
 from __future__ import annotations
 
@@ -80,7 +84,7 @@ def peaks():
 # i.e. 1.2 TFLOP/s): the "alu" roofline denominator for float64 stencil kernels.
 FP64_PEAK_TFLOPS = 1.20
 
-# Algorithmic work per cell of one launch (see DESIGN.md: bytes that must cross HBM, flops
+# Algorithmic work per cell of one launch (bytes that must cross HBM, flops
 # that the stencil must execute), by kernel kind and precision of its multigrid arrays.
 #   smooth pass:   e in, r, eta, inv in, e out  -> 13 words of the multigrid type
 #                  57 flops per cell (114 per updated cell, half the cells per pass)

@@ -5,7 +5,7 @@
 // cannot do that -- code that runs while a CUDA stream is being captured into a graph (an
 // allocation there is not allowed), hosts that own every device allocation themselves
 // (plugins and embedding applications with their own memory pool), and real-time loops that
-// must not enter the driver's allocator.  This entry point keeps its scratch (block
+// must not enter the CUDA allocator.  This entry point keeps its scratch (block
 // coordinate index, neighbour table, per-block norm partials, reduction scratch) in one
 // file-scope device array of fixed size instead.
 //
