@@ -66,6 +66,8 @@ def args_parse():
                    help="batched512 / serving: FGMRES restart length of each instance's inner solve (0: defect correction)")
     p.add_argument("--requests", type=int, default=600, help="serving: requests in the stream")
     p.add_argument("--serve-nu-coarse", default="1,1", help="serving: pre,post sweeps on the grids coarser than level 0")
+    p.add_argument("--serve-max-batch", type=int, default=8, help="serving: slots per batched hierarchy")
+    p.add_argument("--serve-workers", type=int, default=6, help="serving: batches in flight (host threads, streams)")
     p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     p.add_argument("--inner-tol", type=float, default=1e-5,
                    help="residual reduction asked of each float32 inner solve (mixed precision)")
@@ -840,7 +842,8 @@ def run_serving(args):
     budget = 60 << 30
     # V(4,4) with 4 coarsest sweeps, omega 1.3 and V(1,1) on the coarser grids: the schedule the
     # autotuner picks for most classes of the batched workload
-    cfg = dict(hbm_budget_bytes=budget, max_batch=8, n_workers=6, precision=1, tol=1e-9, use_graphs=True,
+    cfg = dict(hbm_budget_bytes=budget, max_batch=args.serve_max_batch, n_workers=args.serve_workers, precision=1,
+               tol=1e-9, use_graphs=True,
                nu_pre=4, nu_post=4, n_coarse=4, max_outer=400, krylov=args.batch_krylov, omega=1.3,
                nu_coarse=tuple(int(v) for v in args.serve_nu_coarse.split(",")))
     # warm-up service: one request per class (kernels loaded, batches of each class built once)
