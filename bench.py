@@ -240,7 +240,7 @@ def time_oracle_sample(wl, gpu_cycles=None):
     cells = wl.hier.leaf_cells()
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": cells / per_step, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": (f"one 256^3 step's source+residual ({t0:.1f} s) and one defect-correction cycle "
+            "sample": (f"one {n}^3 step's source+residual ({t0:.1f} s) and one defect-correction cycle "
                        f"({t1 - t0:.1f} s) on the full input; step = source + {cycles} cycles ({src})"),
             "seconds_per_step": per_step}
 
