@@ -64,7 +64,9 @@ typedef struct {
     double lambda;              /* theta parameter of Eq. 7: 0.5 Crank-Nicolson, 1 backward
                                    Euler; any value in (0, 1]                                  */
     int32_t precision;          /* OHM_FP64, OHM_MIXED or OHM_MIXED_FF                         */
-    int32_t nu_pre, nu_post;    /* red-black sweeps before / after coarse correction (>= 0)   */
+    int32_t nu_pre, nu_post;    /* red-black sweeps before / after coarse correction (>= 0):
+                                   on every grid, or on level 0 and the refined levels when
+                                   nu_coarse_pre / nu_coarse_post are set                      */
     int32_t n_coarse;           /* red-black sweeps on the coarsest grid (>= 1)               */
     int32_t max_outer;          /* V-cycles allowed per step (>= 1)                           */
     int32_t krylov;             /* OHM_MIXED(_FF) only: 0 = the float32 inner solve is defect
