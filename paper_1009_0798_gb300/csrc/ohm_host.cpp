@@ -1825,7 +1825,8 @@ int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol,
                 cudaEventElapsedTime(&ms, ev[0], ev[1]);
                 if (r == OHM_OK && ms < best) {
                     best = ms;
-                    br = ohm_tune_result{h->d.nu_pre, h->d.nu_post, h->d.n_coarse, h->smoother, ms, 0};
+                    br = ohm_tune_result{h->d.nu_pre, h->d.nu_post, h->d.n_coarse, h->smoother, ms, 0, h->d.omega,
+                                         h->d.nu_coarse_pre, h->d.nu_coarse_post};
                 }
             }
     if ((st != OHM_OK && st != OHM_ERR_NOT_CONVERGED) || !(best < INFINITY)) {
