@@ -654,6 +654,13 @@ int orc_set_eta(orc_hier *H, const double *eta_user) {
     return 0;
 }
 
+/* the eta of base multigrid grid m (dense [z][y][x]) as derived by orc_set_eta */
+int orc_mg_eta(const orc_hier *H, int m, double *out) {
+    if (m < 0 || m >= H->nmg) return -1;
+    memcpy(out, H->mg[m]->eta, sizeof(double) * ncell(H->mg[m]));
+    return 0;
+}
+
 /* out = (div F)(B) on leaf cells, 0 on covered blocks; B synced first (Eq. 8 + refluxing) */
 int orc_div_flux(orc_hier *H, const double *B_user, double *out_user) {
     double *tb[MAXL], *tr[MAXL];

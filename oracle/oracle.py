@@ -27,6 +27,7 @@ def lib():
         L.orc_nmg.argtypes = [C.c_void_p]
         L.orc_mg_dims.argtypes = [C.c_void_p, C.c_int, ip]
         L.orc_set_eta.argtypes = [C.c_void_p, dp]
+        L.orc_mg_eta.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_div_flux.argtypes = [C.c_void_p, dp, dp]
         L.orc_apply_L.argtypes = [C.c_void_p, dp, C.c_double, dp]
         L.orc_source.argtypes = [C.c_void_p, dp, C.c_double, dp]
@@ -86,6 +87,13 @@ class Oracle:
         eta = _f64(eta)
         assert eta.size == self.nb * 512
         lib().orc_set_eta(self._h, eta)
+
+    def mg_eta(self, m: int) -> np.ndarray:
+        """eta of base multigrid grid m, dense [nz][ny][nx] (grid 0 is the base level)."""
+        nx, ny, nz = self.mg_dims(m)
+        out = np.zeros((nz, ny, nx))
+        assert lib().orc_mg_eta(self._h, m, out) == 0
+        return out
 
     def div_flux(self, B) -> np.ndarray:
         out = np.zeros((self.nb, 3, 8, 8, 8))

@@ -409,3 +409,142 @@ def test_implicit_agrees_with_explicit_at_second_order(oracle_mod):
         gaps.append(np.abs(B - Be).max())
     assert gaps[0] / gaps[1] == pytest.approx(4.0, rel=0.25)
     assert gaps[1] < 1e-3 * np.abs(B0).max()
+
+
+# --------------------------------------------------------------------------- multigrid transfers
+# Sec. 2.2 names averaging restriction and full-weight prolongation; these pins hold the
+# oracle's two transfers and the coarse-grid eta to properties that fix them: exactness on
+# the data each must reproduce, conservation, and commutation with periodic shifts (which
+# sends data across the periodic seam).
+TDIMS = (32, 16, 24)  # base multigrid grid 0; grid 1 is 16 x 8 x 12
+
+
+def transfer_oracle(oracle_mod):
+    h = dense_grid(list(TDIMS), 0.05)
+    return h, oracle_mod.Oracle(h, 0.5)
+
+
+def centres(dims, dx):
+    """Cell-centre coordinates (x, y, z), each of shape [nz][ny][nx]."""
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * dx, (np.arange(ny) + 0.5) * dx, (np.arange(nx) + 0.5) * dx,
+                          indexing="ij")
+    return x, y, z
+
+
+def test_prolongation_exact_for_linear_fields_away_from_seam(oracle_mod):
+    """Trilinear cell-centred interpolation reproduces a field linear in x, y and z exactly at
+    every fine cell whose 2x2x2 coarse stencil does not wrap around the periodic box; swapped
+    3/4 and 1/4 weights, or a child taking its neighbour on the wrong side, fail this."""
+    h, o = transfer_oracle(oracle_mod)
+    dx = h.dx0
+    cdims = o.mg_dims(1)
+    a0, a = 0.7, np.array([1.3, -2.1, 0.45])
+    cx = centres(cdims, 2 * dx)
+    coarse = np.stack([a0 + c + a[0] * cx[0] + a[1] * cx[1] + a[2] * cx[2] for c in range(3)])
+    got = o.grid_prolong_add(0, coarse, np.zeros((3,) + TDIMS[::-1]))
+    fx = centres(TDIMS, dx)
+    want = np.stack([a0 + c + a[0] * fx[0] + a[1] * fx[1] + a[2] * fx[2] for c in range(3)])
+    inner = (slice(None), slice(1, -1), slice(1, -1), slice(1, -1))
+    assert np.abs(got[inner] - want[inner]).max() < 1e-13 * np.abs(want).max()
+    # a constant coarse field is reproduced everywhere, the seam included
+    got_c = o.grid_prolong_add(0, np.full((3,) + cdims[::-1], 2.5), np.zeros((3,) + TDIMS[::-1]))
+    assert np.abs(got_c - 2.5).max() < 1e-14
+
+
+def test_prolongation_adds_and_commutes_with_periodic_shifts(oracle_mod):
+    """fine += P coarse (the fine field is added to, not replaced), and P commutes with periodic
+    translation: shifting the coarse field by one coarse cell shifts P coarse by two fine cells."""
+    h, o = transfer_oracle(oracle_mod)
+    rng = np.random.default_rng(31)
+    cdims = o.mg_dims(1)
+    coarse = rng.standard_normal((3,) + cdims[::-1])
+    fine = rng.standard_normal((3,) + TDIMS[::-1])
+    P0 = o.grid_prolong_add(0, coarse, np.zeros_like(fine))
+    assert np.abs(o.grid_prolong_add(0, coarse, fine) - (fine + P0)).max() < 1e-14 * np.abs(fine + P0).max()
+    for ax in (1, 2, 3):  # z, y, x of the dense layout
+        shifted = o.grid_prolong_add(0, np.roll(coarse, 1, axis=ax), np.zeros_like(fine))
+        assert np.abs(shifted - np.roll(P0, 2, axis=ax)).max() < 1e-14 * np.abs(P0).max()
+
+
+def test_restriction_octet_constant_linear_and_conservative(oracle_mod):
+    """Averaging restriction maps a field constant on each 2x2x2 octet to that constant, a
+    linear field to its values at the coarse centres, and keeps sum f dV; it commutes with
+    periodic shifts (two fine cells = one coarse cell)."""
+    h, o = transfer_oracle(oracle_mod)
+    dx = h.dx0
+    cdims = o.mg_dims(1)
+    rng = np.random.default_rng(32)
+    c = rng.standard_normal((3,) + cdims[::-1])
+    octet = np.repeat(np.repeat(np.repeat(c, 2, axis=1), 2, axis=2), 2, axis=3)
+    assert np.abs(o.grid_restrict(0, octet, 3) - c).max() < 1e-15 * np.abs(c).max() + 1e-300
+    fx, cx = centres(TDIMS, dx), centres(cdims, 2 * dx)
+    lin = 0.3 + 1.7 * fx[0] - 0.6 * fx[1] + 2.2 * fx[2]
+    want = 0.3 + 1.7 * cx[0] - 0.6 * cx[1] + 2.2 * cx[2]
+    assert np.abs(o.grid_restrict(0, lin[None], 1)[0] - want).max() < 1e-14 * np.abs(want).max()
+    f = rng.standard_normal((3,) + TDIMS[::-1])
+    R = o.grid_restrict(0, f, 3)
+    for comp in range(3):
+        assert abs(R[comp].sum() * (2 * dx) ** 3 - f[comp].sum() * dx ** 3) < 1e-13 * np.abs(f[comp]).sum() * dx ** 3
+    for ax in (1, 2, 3):
+        assert np.abs(o.grid_restrict(0, np.roll(f, 2, axis=ax), 3) - np.roll(R, 1, axis=ax)).max() < 1e-15 * np.abs(R).max()
+
+
+def test_coarse_grid_eta_is_mean_of_children(oracle_mod):
+    """The multigrid eta (Sec. 2.2 coarse operator reading): on every coarser grid it equals the
+    mean of the fine cells it covers.  Checked on eta constant on each 2^m cube (grid m then holds
+    exactly those constants) and on a positive linear eta (reproduced at the coarse centres)."""
+    h = dense_grid(list(TDIMS), 0.05)
+    o = oracle_mod.Oracle(h, 0.5)
+    nmg = o.n_mg
+    assert nmg >= 3
+    rng = np.random.default_rng(33)
+    d2 = o.mg_dims(2)
+    vals = 10 ** rng.uniform(-1, 1, d2[::-1])
+    eta = np.repeat(np.repeat(np.repeat(vals, 4, axis=0), 4, axis=1), 4, axis=2)
+    o.set_eta(W.dense_to_blocks(h, eta[None]))
+    assert np.array_equal(o.mg_eta(0), eta)
+    assert np.abs(o.mg_eta(2) - vals).max() <= 1e-15 * vals.max()
+    assert np.abs(o.mg_eta(1) - np.repeat(np.repeat(np.repeat(vals, 2, axis=0), 2, axis=1), 2, axis=2)).max() <= 1e-15 * vals.max()
+    fx = centres(TDIMS, h.dx0)
+    lin = 2.0 + fx[0] + 0.5 * fx[1] + 0.25 * fx[2]
+    o.set_eta(W.dense_to_blocks(h, lin[None]))
+    for m in range(1, nmg):
+        cx = centres(o.mg_dims(m), h.dx0 * 2 ** m)
+        want = 2.0 + cx[0] + 0.5 * cx[1] + 0.25 * cx[2]
+        assert np.abs(o.mg_eta(m) - want).max() < 1e-14 * want.max()
+
+
+def test_residual_norms_are_leaf_only_and_volume_weighted(oracle_mod):
+    """The stopping norm (Sec. 3.1 uses max |R|; the solver also reports the volume-weighted
+    L2 ratio): on a 3-level hierarchy, ||R||^2 = sum over leaf cells of R^2 h_l^3, likewise
+    ||S||, and max |R| over leaf cells, with S made nonzero and large on covered blocks (which
+    must not count) and scaled per level (so a missing volume weight changes the ratio)."""
+    c = np.array([0.5, 0.5, 0.5])
+
+    def sphere(r):
+        return lambda lo, hi: float(np.sum((np.clip(c, lo, hi) - c) ** 2)) < r * r
+
+    h = W.refined(16, 16, 16, 1.0 / 16, [sphere(0.3), sphere(0.12)])
+    assert h.nlevels == 3
+    rng = np.random.default_rng(34)
+    B = rng.standard_normal((h.nblocks, 3, 8, 8, 8))
+    S = rng.standard_normal((h.nblocks, 3, 8, 8, 8)) * (1.0 + 3.0 * h.blocks[:, 0])[:, None, None, None, None]
+    leaf = h.is_leaf()
+    S[~leaf] *= 1e3
+    eta = np.exp(rng.uniform(-1, 1, (h.nblocks, 1, 8, 8, 8)))
+    o = oracle_mod.Oracle(h, 0.5, eta)
+    dt = 2.0 * h.dx(2) ** 2
+    R, n = o.residual(B, S, dt)
+    assert np.all(R[~leaf] == 0.0)
+    dv = np.array([h.dx(l) ** 3 for l in h.blocks[:, 0]])[leaf]
+    sr = float((R[leaf] ** 2).sum(axis=(1, 2, 3, 4)) @ dv)
+    ss = float((S[leaf] ** 2).sum(axis=(1, 2, 3, 4)) @ dv)
+    assert n["l2_R"] == pytest.approx(math.sqrt(sr), rel=1e-13)
+    assert n["l2_S"] == pytest.approx(math.sqrt(ss), rel=1e-13)
+    assert n["rel_l2"] == pytest.approx(math.sqrt(sr / ss), rel=1e-13)
+    assert n["max_abs"] == np.abs(R[leaf]).max()
+    # R itself on leaf cells is S - B - lambda dt div F(B) with the oracle's own flux divergence
+    # (pinned above by the Fourier symbol, refluxing and the continuous operator)
+    div = o.div_flux(o.sync_down(B))
+    assert np.abs(R[leaf] - (S - B - 0.5 * dt * div)[leaf]).max() < 1e-12 * np.abs(S[leaf]).max()
