@@ -263,25 +263,30 @@ int64_t ohm_launch_count(const ohm_hier *h);
 /* ---------------------------------------------------------------------------------------
  * Allocation-free residual (the paper has no counterpart: this is a deployment interface).
  *
- * For callers that cannot allocate device memory: code that runs while a stream is being
- * captured into a CUDA graph, hosts that own every device allocation through their own pool,
- * and real-time loops that must not enter the allocator.  ohm_create_hierarchy allocates, so
- * those callers use this entry point, which needs no hierarchy and allocates nothing: its
- * scratch (block index, neighbour table, norm partials and reduction scratch, about 0.6 MB) is
- * one fixed array that every device loading the library holds until the process exits.
+ * For callers that cannot allocate device memory: hosts that own every device allocation
+ * through their own pool (a library-side cudaMalloc would escape their accounting and limits)
+ * and real-time loops that must not enter the CUDA allocator (unbounded latency, possible
+ * device synchronisation).  ohm_create_hierarchy allocates, so those callers use this entry
+ * point, which needs no hierarchy and allocates nothing: its scratch (block index, neighbour
+ * table, norm partials and reduction scratch, about 0.6 MB) is one fixed array that every
+ * device loading the library holds until the process exits.
  *
  * Computes R = S - B - lambda dt div F(B) (Eqs. 13, 20) on ONE uniform periodic grid of
  * base_cells (multiples of 8) with cell width dx, the same arithmetic as ohm_op_residual.
  * block_ijk (host) lists every 8^3 block of the grid exactly once as (bi, bj, bk); B_dev, S_dev,
  * R_dev are [nblocks][3][8][8][8] and eta_dev [nblocks][8][8][8] in that order (caller owned).
  * norms (host, may be NULL) receives {||R||/||S||, max|R|, ||R||, ||S||}.  Work is issued on
- * `stream` (a cudaStream_t, NULL = legacy default) and the call synchronises it.
- * Limits and errors: at most 4096 blocks (2,097,152 cells, e.g. 128^3); more, a grid that the
- * list does not tile exactly, or a bad argument return OHM_ERR_INVALID before any work.
- * The first call on a device looks up the scratch array's address; make that first call
- * before any stream capture.  All calls share the scratch array (it keeps the last call's
- * contents; what must start at zero is cleared by each call), so calls whose work overlaps on
- * the GPU race with each other and must be serialised by the caller. */
+ * `stream` (a cudaStream_t, NULL = legacy default); the call copies block_ijk to the device,
+ * reads the norms back and synchronises the stream before returning.
+ * Limits and errors: at most 4096 blocks (2,097,152 cells, e.g. 128^3); more, a list with a
+ * coordinate out of range or a block twice (checked on the host), or a bad argument return
+ * OHM_ERR_INVALID before any work is enqueued.
+ * The first call on a device looks up the scratch array's address and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not call after a
+ * cudaDeviceReset of that device (the kept address is then stale).  All calls share the scratch
+ * array (it keeps the last call's contents; what must start at zero is cleared by each call),
+ * so calls whose work overlaps on the GPU race with each other and must be serialised by the
+ * caller. */
 int ohm_residual_static(const int32_t base_cells[3], double dx, double lambda, double dt, int64_t nblocks,
                         const int32_t *block_ijk, const double *B_dev, const double *S_dev,
                         const double *eta_dev, double *R_dev, double *norms, void *stream);

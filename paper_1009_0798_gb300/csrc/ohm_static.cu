@@ -2,18 +2,21 @@
 // periodic grid, computed without allocating anything.
 //
 // Why it exists: ohm_create_hierarchy allocates its scratch with cudaMalloc, and some callers
-// cannot do that -- code that runs while a CUDA stream is being captured into a graph (an
-// allocation there is not allowed), hosts that own every device allocation themselves
-// (plugins and embedding applications with their own memory pool), and real-time loops that
-// must not enter the CUDA allocator.  This entry point keeps its scratch (block
-// coordinate index, neighbour table, per-block norm partials, reduction scratch) in one
-// file-scope device array of fixed size instead.
+// cannot do that -- hosts that own every device allocation themselves (plugins and embedding
+// applications that hand out memory only from their own pool, so a library-side cudaMalloc
+// would bypass their accounting or fail under their limits), and real-time loops that must not
+// enter the CUDA allocator (its latency is unbounded and it may synchronise the device).  This
+// entry point keeps its scratch (block coordinate index, neighbour table, per-block norm
+// partials, reduction scratch) in one file-scope device array of fixed size instead.
 //
 // Scratch rules: the array lives on every device that loads the library until the process
 // exits; every call shares it and it keeps the last call's contents (the parts that must
 // start at zero are cleared by each call).  Calls whose work overlaps on the GPU (other
 // streams, other host threads) race on it.  The first call on a device looks up the array's
-// device address; make that first call before any stream capture.
+// device address and keeps it for the life of the process; make that first call before any
+// stream capture.  A device reset (cudaDeviceReset) invalidates the kept address, so the call
+// must not be used on a device after it has been reset.  Every call copies the block list to the
+// device, reads the norms back and synchronises its stream before it returns.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -102,6 +105,18 @@ extern "C" int ohm_residual_static(const int32_t base_cells[3], double dx, doubl
     const int64_t ncount = (int64_t)nbx * nby * nbz;
     if (nblocks != ncount || ncount > STATIC_MAX_BLOCKS) return OHM_ERR_INVALID;  // whole grid, at most 4096 blocks
     const int n = (int)nblocks;
+    // the block list must tile the grid exactly: every coordinate in range, every block once
+    // (checked here, on the host, before any work is enqueued)
+    {
+        uint64_t seen[STATIC_MAX_BLOCKS / 64] = {};
+        for (int b = 0; b < n; b++) {
+            const int i = block_ijk[3 * b], j = block_ijk[3 * b + 1], k = block_ijk[3 * b + 2];
+            if (i < 0 || j < 0 || k < 0 || i >= nbx || j >= nby || k >= nbz) return OHM_ERR_INVALID;
+            const int q = (k * nby + j) * nbx + i;
+            if (seen[q >> 6] & (1ull << (q & 63))) return OHM_ERR_INVALID;
+            seen[q >> 6] |= 1ull << (q & 63);
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return OHM_ERR_CUDA;
@@ -132,7 +147,7 @@ extern "C" int ohm_residual_static(const int32_t base_cells[3], double dx, doubl
     if (cudaStreamSynchronize(s) != cudaSuccess) return OHM_ERR_CUDA;
     int e;
     memcpy(&e, &h[4], sizeof(int));
-    if (e) return OHM_ERR_INVALID;  // duplicate or out-of-range block coordinates
+    if (e) return OHM_ERR_INVALID;  // second check of the block list (the host check above passed)
     if (norms) {
         norms[0] = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
         norms[1] = h[2];

@@ -1,11 +1,13 @@
 """The allocation-free residual entry point, ohm_residual_static.
 
-It serves callers that cannot allocate device memory -- code running while a stream is
-captured into a CUDA graph, hosts that own every device allocation, real-time loops that must
-not enter the allocator.  Its scratch is one fixed device array shared by all calls, so the
-test checks that two calls in a row (different inputs) each reproduce the residual and norms
-of the hierarchy path (ohm_op_residual) within the parity tolerance, and that grids beyond its
-4096-block limit are refused.  This file is named so that pytest collects it last.
+It serves callers that cannot allocate device memory -- hosts that hand out device memory only
+from their own pool (a library-side cudaMalloc would escape their accounting) and real-time
+loops that must not enter the CUDA allocator (unbounded latency).  Its scratch is one fixed
+device array shared by all calls, so the test checks that two calls in a row (different
+inputs) each reproduce the residual and norms of the hierarchy path (ohm_op_residual) within
+the parity tolerance, and that grids beyond its 4096-block limit and block lists that do not
+tile the grid (wrong length, a duplicated block, a coordinate out of range) are refused before
+any work.  This file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -68,3 +70,35 @@ def test_static_residual_refuses_grids_beyond_its_limit(ohm):
     st = f((C.c_int32 * 3)(16, 16, 16), 1.0 / 16, 0.5, 1e-4, 7, ijk.ctypes.data_as(C.POINTER(C.c_int32)), p, p, p, p,
            None, None)
     assert st == ohm.OHM_ERR_INVALID
+
+
+def test_static_residual_refuses_bad_block_lists_on_the_host(ohm):
+    """A list of the right length with a duplicated block or a negative / too large coordinate
+    is refused by the host check, before anything is enqueued (one-block buffers suffice)."""
+    import ctypes as C
+    small = torch.zeros(1536, dtype=torch.float64, device="cuda")
+    f = ohm.lib().ohm_residual_static
+    f.argtypes = [C.POINTER(C.c_int32), C.c_double, C.c_double, C.c_double, C.c_int64, C.POINTER(C.c_int32),
+                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    good = np.ascontiguousarray(h.blocks[:, 1:4], dtype=np.int32)
+    p = C.c_void_p(small.data_ptr())
+    cells = (C.c_int32 * 3)(16, 16, 16)
+    bad_lists = []
+    dup = good.copy()
+    dup[3] = dup[5]
+    bad_lists.append(dup)
+    neg = good.copy()
+    neg[2, 1] = -1
+    bad_lists.append(neg)
+    far = good.copy()
+    far[6, 2] = -5
+    bad_lists.append(far)
+    big = good.copy()
+    big[1, 0] = 2
+    bad_lists.append(big)
+    for ijk in bad_lists:
+        st = f(cells, 1.0 / 16, 0.5, 1e-4, len(ijk), ijk.ctypes.data_as(C.POINTER(C.c_int32)), p, p, p, p, None, None)
+        assert st == ohm.OHM_ERR_INVALID
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(small).item() == 0
