@@ -230,6 +230,34 @@ int ohm_op_grid_residual(ohm_hier *h, int m, const double *e_dev, const double *
 int ohm_op_grid_restrict(ohm_hier *h, int m, const double *fine_dev, double *coarse_dev, int ncomp);
 int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double *fine_dev);
 
+/* Float32 single-grid steps of the mixed-precision inner solve (OHM_MIXED / OHM_MIXED_FF
+ * hierarchies; the same grids, layouts and rules as above, every array float32), each run by
+ * the kernel the V-cycle launches on that grid:
+ *   sweep_f32: one full red-black sweep (Eq. 19 with alpha from Eqs. 21-23; the red colour pass
+ *              from the pre-sweep state, then the black pass from the post-red state, each
+ *              update relaxed by the hierarchy's omega) from e_in (NULL = from e = 0, the first
+ *              pre-smoothing sweep of a level) into e_out; variant 0 = the fused red+black sweep
+ *              (block pairs where the grid's blocks pair up along x, else single blocks),
+ *              variant 1 = two colour passes;
+ *   resid_restrict_f32: t = r - (e + lambda dt div F(e)) (Eq. 20 on the grid) into t_dev and its
+ *              restriction (mean of the 8 children, Sec. 2.2) into coarse_dev, either may be
+ *              NULL; coarse_dev has grid m+1's layout: blocked, or lexicographic
+ *              [3][nz][ny][nx] when grid m+1 is below the last blocked grid;
+ *   prolong_add_f32: fine grid m += trilinear interpolation of grid m+1 (Sec. 2.2; grid m+1
+ *              blocked or lexicographic as above). */
+int ohm_op_grid_sweep_f32(ohm_hier *h, int m, const float *e_in_dev, float *e_out_dev, const float *r_dev,
+                          const float *eta_dev, double dt, int variant);
+int ohm_op_grid_resid_restrict_f32(ohm_hier *h, int m, const float *e_dev, const float *r_dev, const float *eta_dev,
+                                   double dt, float *t_dev, float *coarse_dev);
+int ohm_op_grid_prolong_add_f32(ohm_hier *h, int m, const float *coarse_dev, float *fine_dev);
+
+/* out = L X = X + lambda dt div F(X) (Eq. 13) on leaf blocks, in float32: the operator the
+ * float32 inner solve applies (covered cells of a private copy of X set to the mean of their
+ * children, coarse-fine ghosts interpolated from the parent level, refluxing through float64
+ * flux registers, Sec. 4).  X_dev, out_dev float32 [nblocks][3][8][8][8]; out_dev is 0 on covered
+ * blocks.  OHM_MIXED(_FF) hierarchies after ohm_set_eta. */
+int ohm_op_apply_L_f32(ohm_hier *h, const float *X_dev, double dt, float *out_dev);
+
 /* ---------------------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper): launch counting and CUDA-event timing of
  * one kernel kind, used by the benchmark to measure a kernel inside a running step.

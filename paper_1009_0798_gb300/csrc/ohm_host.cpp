@@ -2111,4 +2111,77 @@ int ohm_op_grid_prolong_add(ohm_hier *h, int m, const double *coarse_dev, double
     return OHM_OK;
 }
 
+// Float32 single-grid steps of the mixed-precision inner solve (OHM_MIXED / OHM_MIXED_FF
+// hierarchies), each through the kernel the V-cycle itself launches on that grid.
+static int grid_setup32(ohm_hier *h, int m, const float *eta_dev, double dt, GridRef &G) {
+    if (!h || h->batched || !h->mixed || m < 0 || m > (int)h->mg.size() || !eta_dev || !(dt > 0)) return OHM_ERR_INVALID;
+    if (m == 0 && h->nlev > 1) return OHM_ERR_INVALID;
+    G = base_ref<float>(h, m);
+    CK(cudaMemcpyAsync(G.eta, eta_dev, (size_t)G.g->n() * B3 * sizeof(float), cudaMemcpyDeviceToDevice, h->s));
+    CK(launch_invdiag<float>(gdev(h, *G.g), (const float *)G.eta, nullptr, h->d.lambda * dt, (float *)G.inv, h->s));
+    h->eta_set = false;
+    h->inv_dt = NAN;
+    return OHM_OK;
+}
+
+int ohm_op_grid_sweep_f32(ohm_hier *h, int m, const float *e_in_dev, float *e_out_dev, const float *r_dev,
+                          const float *eta_dev, double dt, int variant) {
+    if (!e_out_dev || !r_dev || (variant != 0 && variant != 1)) return OHM_ERR_INVALID;
+    GridRef G;
+    int st;
+    if ((st = grid_setup32(h, m, eta_dev, dt, G))) return st;
+    const size_t bytes = (size_t)G.g->n() * 3 * B3 * sizeof(float);
+    CK(cudaMemcpyAsync(G.r, r_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    if (e_in_dev) CK(cudaMemcpyAsync(G.e, e_in_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    const int keep = h->smoother;
+    h->smoother = variant;
+    st = sweeps<float>(h, G, 1, h->d.lambda * dt, e_in_dev == nullptr);
+    h->smoother = keep;
+    if (st) return st;
+    CK(cudaMemcpyAsync(e_out_dev, G.e, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+int ohm_op_grid_resid_restrict_f32(ohm_hier *h, int m, const float *e_dev, const float *r_dev, const float *eta_dev,
+                                   double dt, float *t_dev, float *coarse_dev) {
+    if (!e_dev || !r_dev || (!t_dev && !coarse_dev)) return OHM_ERR_INVALID;
+    GridRef G;
+    int st;
+    if ((st = grid_setup32(h, m, eta_dev, dt, G))) return st;
+    const bool next_blocked = m < (int)h->mg.size();
+    CK(launch_resid_restrict<float>(gdev(h, *G.g), e_dev, r_dev, (const float *)G.eta, nullptr, nullptr, h->d.lambda * dt,
+                                    t_dev, next_blocked ? coarse_dev : nullptr, next_blocked ? nullptr : coarse_dev,
+                                    h->small[0].data(), h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+int ohm_op_grid_prolong_add_f32(ohm_hier *h, int m, const float *coarse_dev, float *fine_dev) {
+    if (!h || h->batched || !h->mixed || !fine_dev || !coarse_dev) return OHM_ERR_INVALID;
+    if (m < 0 || m > (int)h->mg.size() || (m == 0 && h->nlev > 1)) return OHM_ERR_INVALID;
+    const HGrid &g = m == 0 ? h->amr[0] : h->mg[m - 1];
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    if (m == (int)h->mg.size())
+        CK(launch_prolong_add<float>(gdev(h, g), nullptr, nullptr, coarse_dev, h->small[0].data(), fine_dev, h->d_err, h->s));
+    else if (g.octet)
+        CK(launch_prolong_add8<float>(gdev(h, h->mg[m]), coarse_dev, fine_dev, h->s));
+    else
+        CK(launch_prolong_add<float>(gdev(h, g), &h->mg[m].dev, coarse_dev, nullptr, nullptr, fine_dev, h->d_err, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
+int ohm_op_apply_L_f32(ohm_hier *h, const float *X_dev, double dt, float *out_dev) {
+    if (!h || h->batched || !h->mixed || !X_dev || !out_dev || !(dt > 0) || !h->eta_set) return OHM_ERR_INVALID;
+    const size_t bytes = (size_t)h->nblocks * 3 * B3 * sizeof(float);
+    float *x = (float *)h->eacc;  // private copy: its covered cells are overwritten by their children's mean
+    CK(cudaMemcpyAsync(x, X_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemsetAsync(out_dev, 0, bytes, h->s));  // covered blocks are not written by the operator
+    int st;
+    if ((st = apply_L32(h, x, nullptr, 1.0, h->d.lambda * dt, 0.0, out_dev, h->d.lambda * dt))) return st;
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
 }  // extern "C"

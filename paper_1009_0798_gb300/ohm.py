@@ -81,6 +81,10 @@ def lib():
         L.ohm_op_grid_residual.argtypes = [vp, C.c_int, vp, vp, vp, dp, vp]
         L.ohm_op_grid_restrict.argtypes = [vp, C.c_int, vp, vp, C.c_int]
         L.ohm_op_grid_prolong_add.argtypes = [vp, C.c_int, vp, vp]
+        L.ohm_op_grid_sweep_f32.argtypes = [vp, C.c_int, vp, vp, vp, vp, dp, C.c_int]
+        L.ohm_op_grid_resid_restrict_f32.argtypes = [vp, C.c_int, vp, vp, vp, dp, vp, vp]
+        L.ohm_op_grid_prolong_add_f32.argtypes = [vp, C.c_int, vp, vp]
+        L.ohm_op_apply_L_f32.argtypes = [vp, vp, dp, vp]
         L.ohm_prof_enable.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ohm_prof_read.argtypes = [vp, C.POINTER(dp), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.ohm_launch_count.argtypes = [vp]
@@ -105,6 +109,16 @@ def _ptr(t, numel=None, name="tensor"):
         raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ptr32(t, name="tensor"):
+    """float32 CUDA tensor (the mixed-precision inner solve's arrays) or None -> pointer."""
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
     return C.c_void_p(t.data_ptr())
 
 
@@ -295,6 +309,27 @@ def ohm_op_grid_restrict(h: Hierarchy, m: int, fine, coarse, ncomp: int = 3) -> 
 
 def ohm_op_grid_prolong_add(h: Hierarchy, m: int, coarse, fine) -> None:
     _check(lib().ohm_op_grid_prolong_add(h.handle, m, _ptr(coarse), _ptr(fine)), "ohm_op_grid_prolong_add")
+
+
+def ohm_op_grid_sweep_f32(h: Hierarchy, m: int, e_in, e_out, r, eta, dt: float, variant: int = 0) -> None:
+    """One float32 red-black sweep on grid m (e_in None = from zero); variant 0 fused, 1 two passes."""
+    _check(lib().ohm_op_grid_sweep_f32(h.handle, m, _ptr32(e_in, "e_in"), _ptr32(e_out, "e_out"), _ptr32(r, "r"),
+                                       _ptr32(eta, "eta"), float(dt), int(variant)), "ohm_op_grid_sweep_f32")
+
+
+def ohm_op_grid_resid_restrict_f32(h: Hierarchy, m: int, e, r, eta, dt: float, t=None, coarse=None) -> None:
+    _check(lib().ohm_op_grid_resid_restrict_f32(h.handle, m, _ptr32(e, "e"), _ptr32(r, "r"), _ptr32(eta, "eta"),
+                                                float(dt), _ptr32(t, "t"), _ptr32(coarse, "coarse")),
+           "ohm_op_grid_resid_restrict_f32")
+
+
+def ohm_op_grid_prolong_add_f32(h: Hierarchy, m: int, coarse, fine) -> None:
+    _check(lib().ohm_op_grid_prolong_add_f32(h.handle, m, _ptr32(coarse, "coarse"), _ptr32(fine, "fine")),
+           "ohm_op_grid_prolong_add_f32")
+
+
+def ohm_op_apply_L_f32(h: Hierarchy, X, dt: float, out) -> None:
+    _check(lib().ohm_op_apply_L_f32(h.handle, _ptr32(X, "X"), float(dt), _ptr32(out, "out")), "ohm_op_apply_L_f32")
 
 
 def ohm_prof_enable(h: Hierarchy, kernel: int, min_blocks: int = 0, max_launches: int = 4096) -> None:
