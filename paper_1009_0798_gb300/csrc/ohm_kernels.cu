@@ -787,28 +787,76 @@ struct G12 {
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
+// The point update of one colour pass (Eq. 19 with R from Eq. 20 and alpha from Eqs. 21-23),
+// written against an accessor that returns component C of the field, or eta, at a compile-time
+// offset (DX, DY, DZ) from the updated cell.  Every sweep kernel goes through this one function,
+// whatever its staging: the rounding of each update is the same in all of them.
+template <typename T, int AX, bool LO, class A>
+__device__ __forceinline__ void face_acc(const A &a, T &phi1, T &phi2) {
+    // the face between the cells P (low side) and Q = P + e_AX: P = -e_AX for the low face of
+    // the updated cell, P = 0 for its high face; flux components along B1 < B2, the other axes
+    constexpr int PX = (LO && AX == 0) ? -1 : 0, PY = (LO && AX == 1) ? -1 : 0, PZ = (LO && AX == 2) ? -1 : 0;
+    constexpr int QX = PX + (AX == 0), QY = PY + (AX == 1), QZ = PZ + (AX == 2);
+    constexpr int B1 = AX == 0 ? 1 : 0, B2 = AX == 2 ? 1 : 2;
+    constexpr int UX = B1 == 0, UY = B1 == 1, UZ = B1 == 2;  // unit step along B1
+    constexpr int VX = B2 == 0, VY = B2 == 1, VZ = B2 == 2;  // unit step along B2
+    const T es = a.template E<PX, PY, PZ>() + a.template E<QX, QY, QZ>();
+    T n1 = a.template B<B1, QX, QY, QZ>() - a.template B<B1, PX, PY, PZ>();
+    T t1 = (a.template B<AX, QX + UX, QY + UY, QZ + UZ>() + a.template B<AX, PX + UX, PY + UY, PZ + UZ>()) -
+           (a.template B<AX, QX - UX, QY - UY, QZ - UZ>() + a.template B<AX, PX - UX, PY - UY, PZ - UZ>());
+    phi1 = es * (quarter(t1) - n1);
+    T n2 = a.template B<B2, QX, QY, QZ>() - a.template B<B2, PX, PY, PZ>();
+    T t2 = (a.template B<AX, QX + VX, QY + VY, QZ + VZ>() + a.template B<AX, PX + VX, PY + VY, PZ + VZ>()) -
+           (a.template B<AX, QX - VX, QY - VY, QZ - VZ>() + a.template B<AX, PX - VX, PY - VY, PZ - VZ>());
+    phi2 = es * (quarter(t2) - n2);
+}
+
+template <typename T, class A>
+__device__ __forceinline__ T rb_one(const A &a, T ev, T rr, T dv, T al, T coef, T omega) {
+    (void)a;
+    T res = rr - ev - coef * dv;
+    return ev + fast_div(omega * res, T(1) + al);
+}
+
+template <typename T, class A>
+__device__ __forceinline__ void rb_update_acc(const A &a, T coef, T lh2, const T rr[3], T out[3], T omega) {
+    T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
+    face_acc<T, 0, true>(a, xl1, xl2);
+    face_acc<T, 0, false>(a, xh1, xh2);
+    face_acc<T, 1, true>(a, yl1, yl2);
+    face_acc<T, 1, false>(a, yh1, yh2);
+    face_acc<T, 2, true>(a, zl1, zl2);
+    face_acc<T, 2, false>(a, zh1, zh2);
+    const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
+    const T e0 = a.template E<0, 0, 0>();
+    const T sx = e0 + T(0.5) * (a.template E<1, 0, 0>() + a.template E<-1, 0, 0>());
+    const T sy = e0 + T(0.5) * (a.template E<0, 1, 0>() + a.template E<0, -1, 0>());
+    const T sz = e0 + T(0.5) * (a.template E<0, 0, 1>() + a.template E<0, 0, -1>());
+    const T al[3] = {lh2 * (sy + sz), lh2 * (sz + sx), lh2 * (sx + sy)};
+    out[0] = rb_one<T>(a, a.template B<0, 0, 0, 0>(), rr[0], dv[0], al[0], coef, omega);
+    out[1] = rb_one<T>(a, a.template B<1, 0, 0, 0>(), rr[1], dv[1], al[1], coef, omega);
+    out[2] = rb_one<T>(a, a.template B<2, 0, 0, 0>(), rr[2], dv[2], al[2], coef, omega);
+}
+
+// accessor of a staged tile (geometry G: rows RRS apart, planes PS, components CS)
+template <typename T, typename G>
+struct TileAcc {
+    const T *tB, *tE;
+    int p;
+    template <int C, int DX, int DY, int DZ>
+    __device__ __forceinline__ T B() const {
+        return tB[C * G::CS + p + DX + DY * G::RRS + DZ * G::PS];
+    }
+    template <int DX, int DY, int DZ>
+    __device__ __forceinline__ T E() const {
+        return tE[p + DX + DY * G::RRS + DZ * G::PS];
+    }
+};
+
 template <typename T, typename G = G12<T>>
 __device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
                                           const T rr[3], T out[3], T omega) {
-    T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
-    face_phi_s(tB, tE, p - 1, 0, 1, G::RRS, G::PS, G::CS, xl1, xl2);
-    face_phi_s(tB, tE, p, 0, 1, G::RRS, G::PS, G::CS, xh1, xh2);
-    face_phi_s(tB, tE, p - G::RRS, 1, G::RRS, 1, G::PS, G::CS, yl1, yl2);
-    face_phi_s(tB, tE, p, 1, G::RRS, 1, G::PS, G::CS, yh1, yh2);
-    face_phi_s(tB, tE, p - G::PS, 2, G::PS, 1, G::RRS, G::CS, zl1, zl2);
-    face_phi_s(tB, tE, p, 2, G::PS, 1, G::RRS, G::CS, zh1, zh2);
-    const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
-    const T e0 = tE[p];
-    const T sx = e0 + T(0.5) * (tE[p + 1] + tE[p - 1]);
-    const T sy = e0 + T(0.5) * (tE[p + G::RRS] + tE[p - G::RRS]);
-    const T sz = e0 + T(0.5) * (tE[p + G::PS] + tE[p - G::PS]);
-    const T al[3] = {lh2 * (sy + sz), lh2 * (sz + sx), lh2 * (sx + sy)};
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        T ev = tB[c * G::CS + p];
-        T res = rr[c] - ev - coef * dv[c];
-        out[c] = ev + fast_div(omega * res, T(1) + al[c]);
-    }
+    rb_update_acc<T>(TileAcc<T, G>{tB, tE, p}, coef, lh2, rr, out, omega);
 }
 
 template <typename T>

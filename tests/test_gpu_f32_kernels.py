@@ -108,6 +108,8 @@ SWEEP_GRIDS = {
     "pairs_m1": ((64, 32, 32), 1),
     # 24 x 16 x 16: 3 blocks along x, the pairs (2q, 2q+1) are not x-neighbours (k_smooth_rb)
     "single_m0": ((24, 16, 16), 0),
+    # a larger grid: 512 blocks, 6 blocks along z (k_smooth_rb2)
+    "pairs_large": ((128, 64, 48), 0),
 }
 
 
