@@ -71,6 +71,18 @@ def args_parse():
     p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     p.add_argument("--inner-tol", type=float, default=1e-5,
                    help="residual reduction asked of each float32 inner solve (mixed precision)")
+    p.add_argument("--batch-nu", default="4,4", help="batched512 without autotuning: pre,post sweeps on level 0")
+    p.add_argument("--batch-omega", type=float, default=1.3, help="batched512 without autotuning: relaxation factor")
+    p.add_argument("--batch-nu-coarse", default="1,1",
+                   help="batched512 without autotuning: pre,post sweeps on the grids coarser than level 0")
+    p.add_argument("--batch-n-coarse", type=int, default=4, help="batched512 without autotuning: coarsest sweeps")
+    p.add_argument("--no-legs", action="store_true",
+                   help="skip the bounded batched and serving legs of the default line")
+    p.add_argument("--leg-instances", type=int, default=128, help="batched leg of the default line: instances")
+    p.add_argument("--leg-requests", type=int, default=150, help="serving leg of the default line: requests")
+    p.add_argument("--cpu-full-step", action="store_true",
+                   help="time one complete oracle CN step of the workload on the host cores (minutes at 256^3) "
+                        "beside the sampled model of cpu_baseline, print it and exit")
     return p.parse_args()
 
 
@@ -82,9 +94,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# FP64 issue rate measured on this machine's GB300 by a DFMA throughput probe (600 G DFMA/s,
-# i.e. 1.2 TFLOP/s): the "alu" roofline denominator for float64 stencil kernels.
-FP64_PEAK_TFLOPS = 1.20
+def fp64_peak_tflops(ohm):
+    """float64 FMA rate of this GPU measured by the library's DFMA probe (2 flops per FMA): the
+    "alu" roofline denominator of the float64 stencil kernels."""
+    return 2.0 * ohm.ohm_fp64_fma_rate() * 1e-12
 
 # Algorithmic work per cell of one launch (bytes that must cross HBM, flops
 # that the stencil must execute), by kernel kind and precision of its multigrid arrays.
@@ -189,7 +202,8 @@ def dist():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as td
-        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        if not td.is_initialized():
+            td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
 
 
@@ -239,10 +253,43 @@ def time_oracle_sample(wl, gpu_cycles=None):
     per_step = t0 + cycles * max(t1 - t0, 0.0)
     cells = wl.hier.leaf_cells()
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": cells / per_step, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": cells / per_step, "unit": UNIT, "cores": threads, "kind": "oracle", "extrapolated": True,
             "sample": (f"one {n}^3 step's source+residual ({t0:.1f} s) and one defect-correction cycle "
                        f"({t1 - t0:.1f} s) on the full input; step = source + {cycles} cycles ({src})"),
             "seconds_per_step": per_step}
+
+
+FULL_STEP_RECORD = os.path.join(ROOT, "profiles", "oracle_full_step_resistive_bump_{n}.json")
+
+
+def oracle_full_step_record(n: int):
+    """The committed measurement of one complete oracle step at n^3 (written by --cpu-full-step on
+    a GPU machine's host), set beside the sampled model: both its measured and its modelled seconds."""
+    path = FULL_STEP_RECORD.format(n=n)
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    return {"full_step_s": d["full_step_s"], "model_s": d["model_s"], "model_error": d["model_s"] / d["full_step_s"] - 1.0,
+            "cores": d["cores"], "cycles": d["cycles"], "source": os.path.relpath(path, ROOT)}
+
+
+def run_cpu_full_step(args):
+    """One complete oracle CN step (V(2,2), 16 coarsest sweeps, defect correction to the
+    workload's tolerance) timed on the host cores, next to the sampled model of time_oracle_sample
+    on the same input in the same process."""
+    from paper_1009_0798_gb300 import workloads as W
+    from oracle import build as obuild
+    from oracle.oracle import Oracle
+    obuild.build()
+    wl = W.resistive_bump_256(n=args.size)
+    model = time_oracle_sample(wl)
+    o = Oracle(wl.hier, wl.lam, wl.eta)
+    t = time.perf_counter()
+    _, info = o.cn_step(wl.B, wl.dt, wl.tol, 2, 2, 16, 400)
+    full = time.perf_counter() - t
+    print(json.dumps({"workload": f"resistive_bump_{args.size}^3", "full_step_s": full,
+                      "model_s": model["seconds_per_step"], "cycles": info["cycles"], "converged": info["converged"],
+                      "cores": model["cores"], "model_sample": model["sample"]}), flush=True)
 
 
 def run_reference(args):
@@ -267,7 +314,10 @@ def run_reference(args):
             "config": {"workload": f"resistive_bump_{args.size}^3", "cells": wl.hier.leaf_cells(), "tol": wl.tol,
                        "precision": "fp64 CPU oracle", "parallelism": "host cores (OpenMP)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
-                             "sample": samples[0]["sample"]},
+                             "extrapolated": True, "sample": samples[0]["sample"],
+                             "model_check": oracle_full_step_record(args.size)},
+            "timing": ("each step is a sample (one source+residual and one cycle on the full input) scaled to a "
+                       "whole step; ms_per_step is that modelled step, not the sample's own time"),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     del ge
     print(json.dumps(line), flush=True)
@@ -405,17 +455,26 @@ def run_ours(args):
     # paper's scheme: float64 V-cycles in float64 defect correction)
     others = {}
     if not args.no_fp64:
+        # plain FP64 (float64 V-cycles in float64 defect correction) with the headline's sweep
+        # counts and relaxation, and with the paper's schedule (Gauss-Seidel, the same sweeps on
+        # every grid); FP64 has no Krylov inner solve
         for name, prec, kr, om, nc in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV, args.omega, nuc),
                                        ("mixed_defect_correction", ohm.OHM_MIXED, 0, 1.0, (0, 0)),
-                                       ("fp64_plain", ohm.OHM_FP64, 0, 1.0, (0, 0))):
+                                       ("fp64_plain", ohm.OHM_FP64, 0, args.omega, nuc),
+                                       ("fp64_paper_schedule", ohm.OHM_FP64, 0, 1.0, (0, 0))):
             g2 = make(prec, kr, om, nc)
             others[name] = summary(timed(g2, prec, profile=False))
             if prec == ohm.OHM_MIXED_FF:
                 others[name]["precision"] = ("OHM_MIXED_FF: as the headline, but the outer residual in float-float "
                                              "(float32 pairs, ~48 bits) with float32-accumulated norms")
+            if prec == ohm.OHM_FP64:
+                others[name]["multigrid"] = (f"float64 V({nu[0]},{nu[1]}) on level 0, "
+                                             f"V({nc[0] or nu[0]},{nc[1] if nc != (0, 0) else nu[1]}) below, "
+                                             f"omega {om}, {args.n_coarse} coarsest sweeps, float64 defect correction")
             g2.close()
             del g2
     fp64 = others.get("fp64_plain")
+    fp64_paper = others.get("fp64_paper_schedule")
 
     # end to end through the public API with host buffers: every step uploads its inputs (B, eta)
     # from pinned host memory and downloads its result.  The steps are independent solves of the
@@ -468,6 +527,10 @@ def run_ours(args):
                "timing": "CUDA events around all steps; independent steps from the host inputs, uploads and "
                          "downloads on a copy stream overlapping the neighbouring steps' compute"}
 
+    # bounded batched and serving legs (each its own timed region, clock sample and metric)
+    legs = {}
+    if not args.no_legs:
+        legs = run_legs(args)
     if rank != 0:
         return
     # roofline of the dominant kernel, measured with events inside the timed region
@@ -479,8 +542,9 @@ def run_ours(args):
     sec = prof["ms"] * 1e-3
     if mixed["dom"] == "composite":
         achieved = algo["flops"] * prof["cells"] / sec * 1e-12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "measured FP64 DFMA rate (x2 flops)"}
+        fp64_peak = fp64_peak_tflops(ohm)
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "peak_source": "measured in this run: DFMA probe (x2 flops)"}
     else:
         achieved = algo["bytes"] * prof["cells"] / sec * 1e-9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -495,9 +559,12 @@ def run_ours(args):
         try:
             from oracle import build as obuild
             obuild.build()
-            cyc = fp64["cycles_per_step"][0] if fp64 else mixed["infos"][0]["cycles"]
+            cyc = fp64_paper["cycles_per_step"][0] if fp64_paper else mixed["infos"][0]["cycles"]
             cpu = time_oracle_sample(wl, gpu_cycles=cyc)
             cpu.pop("seconds_per_step", None)
+            chk = oracle_full_step_record(args.size)
+            if chk:
+                cpu["model_check"] = chk
         except Exception as ex:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
     lat = sorted(lat_ms)
@@ -515,16 +582,43 @@ def run_ours(args):
             "latency_ms": {"p50": statistics.median(lat), "p99": p99, "solves": len(lat)},
             "cycles_per_step": [s["cycles"] for s in mixed["infos"]],
             "final_rel_l2": [s["rel_l2"] for s in mixed["infos"]],
-            "fp64_plain": fp64,
+            "fp64_plain": fp64, "fp64_paper_schedule": fp64_paper,
+            "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
+            "fp64_fma_tflops": fp64_peak_tflops(ohm),
             "mixed_defect_correction": others.get("mixed_defect_correction"),
             "mixed_float_float_residual": others.get("mixed_float_float_residual"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": mixed["clocks"],
-            "gpu_launches": mixed["launches"]}
+            "gpu_launches": mixed["launches"], **legs}
     print(json.dumps(line), flush=True)
 
 
+def run_legs(args):
+    """The batched and serving workloads at bounded sizes inside the default run: `batched_leg`
+    (args.leg_instances instances of the 512-instance recipe, the fixed batch schedule, no
+    autotuning) and `serving_leg` (the first args.leg_requests requests of the Poisson stream).
+    Each reports its own value, solves/s, latency percentiles and clock sample."""
+    la = argparse.Namespace(**vars(args))
+    la.instances, la.no_autotune, la.no_fp64, la.no_e2e, la.no_cpu_baseline = args.leg_instances, True, True, True, True
+    la.steps, la.warmup = 3, 1
+    b = run_batched(la, emit=False)
+    ls = argparse.Namespace(**vars(args))
+    ls.requests, ls.no_cpu_baseline = args.leg_requests, True
+    v = run_serving(ls, emit=False)
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "solves_per_s", "latency_ms", "clocks", "gpu_launches")
+    out = {}
+    if b:
+        out["batched_leg"] = {**{k: b.get(k) for k in keep}, "workload": b["config"]["workload"],
+                              "classes": b["config"]["classes"], "multigrid": b["config"]["multigrid"],
+                              "mean_cycles_per_instance": b.get("mean_cycles_per_instance")}
+    if v:
+        out["serving_leg"] = {**{k: v.get(k) for k in keep}, "workload": v["config"]["workload"],
+                              "requests": v["config"]["requests"], "mix": v["config"]["mix"],
+                              "converged": v.get("converged"), "alone_vs_mix_identical": v.get("alone_vs_mix_identical")}
+    return out
+
+
 # ----------------------------------------------------------------------------- batches
-def run_batched(args):
+def run_batched(args, emit=True):
     """512 independent periodic instances (edges 16..64), one CN step each to 1e-9: one
     batched hierarchy per edge length (every launch covers all its instances, CUDA-graph
     inner iterations, autotuned schedule), the five classes stepped concurrently from five
@@ -544,7 +638,8 @@ def run_batched(args):
     ge.build()
     tol = 1e-9
     inst = W.batched_instances(args.instances, seed=4)
-    nu = tuple(int(v) for v in args.nu.split(","))
+    nu = tuple(int(v) for v in args.batch_nu.split(","))
+    bnuc = tuple(int(v) for v in args.batch_nu_coarse.split(","))
     groups = {}
     for i in inst:
         groups.setdefault(i.n, []).append(i)
@@ -560,9 +655,9 @@ def run_batched(args):
             c["eta"] = torch.from_numpy(np.concatenate([i.eta for i in lst]).reshape(-1)).cuda()
             c["B"] = torch.empty_like(c["B0"])
             c["g"] = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_MIXED,
-                                              nu_pre=nu[0], nu_post=nu[1], n_coarse=args.n_coarse, max_outer=400,
+                                              nu_pre=nu[0], nu_post=nu[1], n_coarse=args.batch_n_coarse, max_outer=400,
                                               stream=s, n_instances=len(lst), use_graphs=True,
-                                              krylov=args.batch_krylov)
+                                              krylov=args.batch_krylov, omega=args.batch_omega, nu_coarse=bnuc)
             ohm.ohm_set_eta(c["g"], c["eta"])
         C.append(c)
     torch.cuda.synchronize()
@@ -727,7 +822,7 @@ def run_batched(args):
         return
     lat = sorted(per)
     p99 = lat[min(len(lat) - 1, math.ceil(0.99 * len(lat)) - 1)]
-    line = {"metric": "cell-steps/s, 512 independent instances to rel. residual 1e-9", "value": value, "unit": UNIT,
+    line = {"metric": f"cell-steps/s, {len(inst)} independent instances to rel. residual 1e-9", "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 multigrid + f64 residual/update/norms", "data": "synthetic",
@@ -743,11 +838,22 @@ def run_batched(args):
             "latency_ms": {"p50": statistics.median(lat), "p99": p99},
             "mean_cycles_per_instance": cyc, **comp,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches}
-    print(json.dumps(line), flush=True)
+    if not args.no_autotune:
+        line["config"]["schedule_before_tuning"] = (f"V({nu[0]},{nu[1]}), V{bnuc} below, omega {args.batch_omega}, "
+                                                    f"{args.batch_n_coarse} coarsest sweeps")
+    else:
+        line["config"]["schedule"] = (f"V({nu[0]},{nu[1]}) on level 0, V{bnuc} below, omega {args.batch_omega}, "
+                                      f"{args.batch_n_coarse} coarsest sweeps")
+    for c in C:
+        c["g"].close()
+    pool.shutdown()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------- serving
-SERVE_EDGES = (32, 40, 48, 64, 80, 96, 128)  # multiples of 8 in 32..128 whose coarsest grid fits one block
+SERVE_EDGES = tuple(range(32, 129, 8))  # every multiple of 8 in 32..128
 
 
 def serving_requests(count, rate, seed=5):
@@ -821,7 +927,7 @@ def serving_cpu_baseline(reqs, inputs):
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
 
 
-def run_serving(args):
+def run_serving(args, emit=True):
     """Poisson stream of CN-solve requests through the continuous-batching service: requests
     are submitted at their arrival times (host clock) with host arrays; latency = completion
     minus submission on the service clock.  Throughput = solved cell-steps over the span from
@@ -912,13 +1018,16 @@ def run_serving(args):
             "clocks": clk.summary(), "gpu_launches": stats.get("kernel_launches"),
             "roofline": None, "roofline_note": "the service runs the kernels of the batched and headline lines",
             "cpu_baseline": serving_cpu_baseline(reqs, inputs) if not args.no_cpu_baseline else None}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
     args = args_parse()
-    if args.impl == "reference":
+    if args.cpu_full_step:
+        run_cpu_full_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched512":
         run_batched(args)

@@ -114,8 +114,9 @@ typedef struct {
 
 /* Builds the block tables, the multigrid grids below level 0 (coarsened by 2 while every
  * dimension is even and >= 4) and allocates all device scratch.  *out receives the handle
- * (NULL on failure).  The coarsest grids are solved inside one thread block; base grids
- * whose first non-multiple-of-8 coarsening has more than 16384 cells are rejected. */
+ * (NULL on failure).  Any base grid of multiples of 8 is accepted: the coarse grids below the
+ * last one made of 8^3 blocks are stepped by grid-wide launches while they have more than 16384
+ * cells and by a one-thread-block solver below that. */
 int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out);
 
 /* Copies eta (> 0 and finite, [nblocks][8][8][8], every block including covered ones) into
@@ -287,6 +288,13 @@ int ohm_prof_read(ohm_hier *h, double *total_ms, int64_t *launches, int64_t *cel
 
 /* Kernel launches this hierarchy has issued since creation (all kinds). */
 int64_t ohm_launch_count(const ohm_hier *h);
+
+/* Measured float64 FMA issue rate of the current device (no hierarchy needed): a kernel of
+ * independent DFMA chains on every SM, timed with CUDA events on `stream` (a cudaStream_t, NULL
+ * = legacy default; the call synchronises it), best of three launches after one warm-up.
+ * *dfma_per_s receives FMA instructions per second (2 flops each); the float64 stencil kernels
+ * are bound by this rate.  Changes no device setting. */
+int ohm_fp64_fma_rate(double *dfma_per_s, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free residual (the paper has no counterpart: this is a deployment interface).

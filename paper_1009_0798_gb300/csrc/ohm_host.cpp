@@ -21,6 +21,8 @@ using namespace ohm;
 namespace {
 
 constexpr int MAX_LEVELS = 8;
+// lexicographic grids of more cells than this are stepped by grid-wide launches; the rest, down
+// to the coarsest, by the one-block solver (k_bottom: one thread block per instance)
 constexpr int MAX_BOTTOM_CELLS = 16384;
 
 inline int wrapi(int v, int n) {
@@ -330,10 +332,6 @@ int build_tables(ohm_hier *H, std::string &err) {
     }
     if (H->small.empty()) {
         err = "internal: no coarsest grid";
-        return OHM_ERR_INVALID;
-    }
-    if ((int64_t)H->small[0][0] * H->small[0][1] * H->small[0][2] > MAX_BOTTOM_CELLS) {
-        err = "base grid too large for the single-block coarsest solve (first non-blocked grid exceeds 16384 cells)";
         return OHM_ERR_INVALID;
     }
     // parent / octant links from each blocked grid into the next blocked grid
@@ -787,6 +785,49 @@ int sweeps(ohm_hier *H, const GridRef &G, int n, double lamdt, bool zero = false
     }
     return OHM_OK;
 }
+// The V-cycle over the lexicographic grids below the last blocked one, for the restricted
+// residual already in r of small grid 0.  Grids of more than MAX_BOTTOM_CELLS cells take
+// grid-wide launches (the same arithmetic as the one-block solver); the one-block solver runs
+// the remaining grids, or the coarsest grid gets its sweeps grid-wide when even that is large.
+template <typename T>
+int small_vcycle(ohm_hier *H, double lamdt, int npre, int npost, int ncoarse) {
+    SmallDev<T> sm = small_dev<T>(H);
+    int s0 = 0;
+    while (s0 < sm.n && (int64_t)sm.dims[s0][0] * sm.dims[s0][1] * sm.dims[s0][2] > MAX_BOTTOM_CELLS) s0++;
+    if (s0 == 0) {
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(sm, lamdt, npre, npost, ncoarse, H->s));
+        return OHM_OK;
+    }
+    const size_t cells0 = (size_t)sm.dims[0][0] * sm.dims[0][1] * sm.dims[0][2];
+    CK(cudaMemsetAsync(sm.e[0], 0, (size_t)sm.ninst * 3 * cells0 * sizeof(T), H->s));  // from e = 0
+    const int top = std::min(s0, sm.n - 1);  // grids stepped grid-wide on the way down
+    for (int g = 0; g < top; g++) {
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_lex_sweeps<T>(sm, g, lamdt, npre, H->s));
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_lex_resid_restrict<T>(sm, g, lamdt, H->s));
+    }
+    if (s0 < sm.n) {
+        SmallDev<T> v = sm;  // grids s0 .. n-1
+        v.n = sm.n - s0;
+        for (int q = 0; q < v.n; q++) {
+            for (int a = 0; a < 3; a++) v.dims[q][a] = sm.dims[s0 + q][a];
+            v.h[q] = sm.h[s0 + q];
+            v.e[q] = sm.e[s0 + q];
+            v.r[q] = sm.r[s0 + q];
+            v.t[q] = sm.t[s0 + q];
+            v.eta[q] = sm.eta[s0 + q];
+            v.inv[q] = sm.inv[s0 + q];
+        }
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(v, lamdt, npre, npost, ncoarse, H->s));
+    } else {
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_lex_sweeps<T>(sm, sm.n - 1, lamdt, ncoarse, H->s));
+    }
+    for (int g = top - 1; g >= 0; g--) {
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_lex_prolong<T>(sm, g, H->s));
+        LAUNCH(H, OHM_K_BOTTOM, 0, launch_lex_sweeps<T>(sm, g, lamdt, npost, H->s));
+    }
+    return OHM_OK;
+}
+
 template <typename T>
 int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const ohm_hier_desc &d = H->d;
@@ -809,10 +850,10 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
     } else {
         LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
                                     nullptr, nullptr, (T *)H->smallbuf[0].r, H->small[0].data(), H->s));
-        SmallDev<T> sm = small_dev<T>(H);
         const bool csb = d.nu_coarse_pre || d.nu_coarse_post;  // the small grids are all coarser than level 0
-        LAUNCH(H, OHM_K_BOTTOM, 0, launch_bottom<T>(sm, lamdt, csb ? d.nu_coarse_pre : d.nu_pre,
-                                                    csb ? d.nu_coarse_post : d.nu_post, d.n_coarse, H->s));
+        if ((st = small_vcycle<T>(H, lamdt, csb ? d.nu_coarse_pre : d.nu_pre, csb ? d.nu_coarse_post : d.nu_post,
+                                  d.n_coarse)))
+            return st;
         LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add<T>(gdev(H, *G.g), nullptr, nullptr, (const T *)H->smallbuf[0].e, H->small[0].data(), (T *)G.e,
                                  H->d_err, H->s));
     }

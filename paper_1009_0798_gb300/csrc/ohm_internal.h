@@ -168,6 +168,16 @@ template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post,
                           int n_coarse, cudaStream_t s);
 
+// Grid-wide steps on lexicographic grid s of every instance (grids too large for the one-block
+// coarsest solver): nsweep red-black sweeps (e -> t -> e), residual into t and its restriction
+// into r of grid s + 1 (e of grid s + 1 zeroed), prolongation e_s += P e_{s+1}.
+template <typename T>
+cudaError_t launch_lex_sweeps(const SmallDev<T> &sm, int s, double lamdt, int nsweep, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lex_resid_restrict(const SmallDev<T> &sm, int s, double lamdt, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lex_prolong(const SmallDev<T> &sm, int s, cudaStream_t st);
+
 // lexicographic restriction between small grids and small-grid inverse diagonals
 template <typename T>
 cudaError_t launch_small_setup(const SmallDev<T> &sm, double lamdt, bool eta_chain, cudaStream_t s);

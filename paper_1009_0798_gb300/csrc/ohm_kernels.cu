@@ -2106,6 +2106,143 @@ cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int n
 template cudaError_t launch_bottom<double>(const SmallDev<double> &, double, int, int, int, cudaStream_t);
 template cudaError_t launch_bottom<float>(const SmallDev<float> &, double, int, int, int, cudaStream_t);
 
+// Lexicographic grids too large for the one-block solver, stepped by grid-wide launches over
+// all instances (thread per instance and cell): the same arithmetic as k_bottom, one kernel per
+// colour pass (e_in -> e_out, the other colour copied), per residual, per restriction and per
+// prolongation.
+template <typename T>
+__device__ __forceinline__ bool lex_cell(const SmallDev<T> &sm, int s, size_t tid, int &q, int &cell) {
+    const int n = sm.dims[s][0] * sm.dims[s][1] * sm.dims[s][2];
+    if (tid >= (size_t)sm.ninst * n) return false;
+    q = (int)(tid / n);
+    cell = (int)(tid - (size_t)q * n);
+    return !(sm.imask && !sm.imask[q]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lex_pass(SmallDev<T> sm, int s, double lamdt, int colour, int to_t) {
+    int q, cell;
+    if (!lex_cell(sm, s, blockIdx.x * (size_t)blockDim.x + threadIdx.x, q, cell)) return;
+    const LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+    const int n = G.nx * G.ny * G.nz;
+    const size_t o3 = (size_t)q * 3 * n;
+    const T *src = (to_t ? sm.e[s] : sm.t[s]) + o3;
+    T *dst = (to_t ? sm.t[s] : sm.e[s]) + o3;
+    const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
+    if (((x + y + z) & 1) != colour) {
+        for (int c = 0; c < 3; c++) dst[(size_t)c * n + cell] = src[(size_t)c * n + cell];
+        return;
+    }
+    const T coef = (T)(lamdt / (2.0 * sm.h[s] * sm.h[s]));
+    const T *r = sm.r[s] + o3, *inv = sm.inv[s] + o3, *E = sm.eta[s] + (size_t)q * n;
+    T dv[3];
+    lex_div(G, src, E, x, y, z, dv);
+    for (int c = 0; c < 3; c++) {
+        const size_t id = (size_t)c * n + cell;
+        const T d = (r[id] - src[id] - coef * dv[c]) * inv[id];
+        dst[id] = src[id] + d;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lex_resid(SmallDev<T> sm, int s, double lamdt) {
+    int q, cell;
+    if (!lex_cell(sm, s, blockIdx.x * (size_t)blockDim.x + threadIdx.x, q, cell)) return;
+    const LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+    const int n = G.nx * G.ny * G.nz;
+    const size_t o3 = (size_t)q * 3 * n;
+    const T coef = (T)(lamdt / (2.0 * sm.h[s] * sm.h[s]));
+    const T *e = sm.e[s] + o3, *r = sm.r[s] + o3, *E = sm.eta[s] + (size_t)q * n;
+    T *t = sm.t[s] + o3;
+    const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
+    T dv[3];
+    lex_div(G, e, E, x, y, z, dv);
+    for (int c = 0; c < 3; c++) {
+        const size_t id = (size_t)c * n + cell;
+        t[id] = r[id] - e[id] - coef * dv[c];
+    }
+}
+
+// r of grid s + 1 = mean of the 8 children of t on grid s; e of grid s + 1 = 0
+template <typename T>
+__global__ void __launch_bounds__(256) k_lex_restrict(SmallDev<T> sm, int s) {
+    int q, cell;
+    if (!lex_cell(sm, s + 1, blockIdx.x * (size_t)blockDim.x + threadIdx.x, q, cell)) return;
+    const LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+    const LexGrid<T> C{sm.dims[s + 1][0], sm.dims[s + 1][1], sm.dims[s + 1][2]};
+    const int n = G.nx * G.ny * G.nz, nc_ = C.nx * C.ny * C.nz;
+    const T *t = sm.t[s] + (size_t)q * 3 * n;
+    const int x = cell % C.nx, y = (cell / C.nx) % C.ny, z = cell / (C.nx * C.ny);
+    for (int c = 0; c < 3; c++) {
+        T acc = 0;
+        for (int dk = 0; dk < 2; dk++)
+            for (int dj = 0; dj < 2; dj++)
+                for (int di = 0; di < 2; di++) acc += t[G.id(c, 2 * x + di, 2 * y + dj, 2 * z + dk)];
+        const size_t id = (size_t)q * 3 * nc_ + (size_t)c * nc_ + cell;
+        sm.r[s + 1][id] = acc / T(8);
+        sm.e[s + 1][id] = T(0);
+    }
+}
+
+// e of grid s += trilinear interpolation of e of grid s + 1
+template <typename T>
+__global__ void __launch_bounds__(256) k_lex_prolong(SmallDev<T> sm, int s) {
+    int q, cell;
+    if (!lex_cell(sm, s, blockIdx.x * (size_t)blockDim.x + threadIdx.x, q, cell)) return;
+    const LexGrid<T> G{sm.dims[s][0], sm.dims[s][1], sm.dims[s][2]};
+    const LexGrid<T> C{sm.dims[s + 1][0], sm.dims[s + 1][1], sm.dims[s + 1][2]};
+    const int n = G.nx * G.ny * G.nz, nc_ = C.nx * C.ny * C.nz;
+    const T *ec = sm.e[s + 1] + (size_t)q * 3 * nc_;
+    T *e = sm.e[s] + (size_t)q * 3 * n;
+    const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
+    const int px = x >> 1, py = y >> 1, pz = z >> 1;
+    const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
+    for (int c = 0; c < 3; c++) {
+        T v = 0;
+        for (int ak = 0; ak < 2; ak++)
+            for (int aj = 0; aj < 2; aj++)
+                for (int ai = 0; ai < 2; ai++) {
+                    T wt = (ai ? T(0.25) : T(0.75)) * (aj ? T(0.25) : T(0.75)) * (ak ? T(0.25) : T(0.75));
+                    v += wt * ec[C.id(c, px + ai * sx, py + aj * sy, pz + ak * sz)];
+                }
+        e[(size_t)c * n + cell] += v;
+    }
+}
+
+template <typename T>
+static unsigned lex_grid(const SmallDev<T> &sm, int s) {
+    const size_t n = (size_t)sm.ninst * sm.dims[s][0] * sm.dims[s][1] * sm.dims[s][2];
+    return (unsigned)((n + 255) / 256);
+}
+
+template <typename T>
+cudaError_t launch_lex_sweeps(const SmallDev<T> &sm, int s, double lamdt, int nsweep, cudaStream_t st) {
+    for (int i = 0; i < nsweep; i++) {
+        k_lex_pass<T><<<lex_grid(sm, s), 256, 0, st>>>(sm, s, lamdt, 0, 1);  // e -> t: red
+        k_lex_pass<T><<<lex_grid(sm, s), 256, 0, st>>>(sm, s, lamdt, 1, 0);  // t -> e: black
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lex_resid_restrict(const SmallDev<T> &sm, int s, double lamdt, cudaStream_t st) {
+    k_lex_resid<T><<<lex_grid(sm, s), 256, 0, st>>>(sm, s, lamdt);
+    k_lex_restrict<T><<<lex_grid(sm, s + 1), 256, 0, st>>>(sm, s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lex_prolong(const SmallDev<T> &sm, int s, cudaStream_t st) {
+    k_lex_prolong<T><<<lex_grid(sm, s), 256, 0, st>>>(sm, s);
+    return cudaGetLastError();
+}
+template cudaError_t launch_lex_sweeps<double>(const SmallDev<double> &, int, double, int, cudaStream_t);
+template cudaError_t launch_lex_sweeps<float>(const SmallDev<float> &, int, double, int, cudaStream_t);
+template cudaError_t launch_lex_resid_restrict<double>(const SmallDev<double> &, int, double, cudaStream_t);
+template cudaError_t launch_lex_resid_restrict<float>(const SmallDev<float> &, int, double, cudaStream_t);
+template cudaError_t launch_lex_prolong<double>(const SmallDev<double> &, int, cudaStream_t);
+template cudaError_t launch_lex_prolong<float>(const SmallDev<float> &, int, cudaStream_t);
+
 // eta chain over the small grids (optional) and their inverse diagonals
 template <typename T>
 __global__ void __launch_bounds__(1024) k_small_setup(SmallDev<T> sm_all, double lamdt, int eta_chain) {

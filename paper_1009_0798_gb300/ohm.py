@@ -346,6 +346,20 @@ def ohm_launch_count(h: Hierarchy) -> int:
     return int(lib().ohm_launch_count(h.handle))
 
 
+def ohm_fp64_fma_rate(stream=None) -> float:
+    """Measured float64 FMA instructions per second of the current device (include/ohm.h)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    L = lib()
+    if not getattr(L.ohm_fp64_fma_rate, "argtypes", None):
+        L.ohm_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), C.c_void_p]
+    v = C.c_double()
+    _check(L.ohm_fp64_fma_rate(C.byref(v), C.c_void_p(raw)), "ohm_fp64_fma_rate")
+    return v.value
+
+
 def ohm_residual_static(base_cells, dx: float, lam: float, dt: float, block_ijk, B, S, eta, R, stream=None) -> dict:
     """Allocation-free residual on one uniform periodic grid (no hierarchy needed), for
     callers that cannot allocate device memory; see include/ohm.h.  block_ijk: int32 [n, 3]."""

@@ -157,6 +157,33 @@ def test_instance_same_bits_alone_and_in_batch(ohm, graphs, precision, sched):
         assert np.array_equal(got[q][leaf_fine], bs[q].reshape(-1, 1536)[leaf_fine])
 
 
+@pytest.mark.parametrize("graphs", [False, True])
+def test_grid_wide_coarse_grids_same_bits_alone_and_in_batch(ohm, graphs):
+    """A 56^3 base grid: its first coarsening that is not a multiple of 8 (28^3, 21952 cells) is
+    stepped by the grid-wide coarse-grid kernels, the rest by the one-block solver.  An instance
+    gives the same bits alone and in a batch of 3 with another instance inactive."""
+    h = W.uniform(56, 56, 56, 1.0 / 56)
+    K = 3
+    bs, etas = instances(h, K, 90)
+    dts = [(4.0 + q) * h.dx0 ** 2 for q in range(K)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g1 = make(ohm, h, 1, precision=1, stream=stream, use_graphs=graphs, max_outer=200)
+        ohm.ohm_set_eta(g1, dev(etas[1]))
+        B1 = dev(bs[1])
+        s1, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[1]], 1e-9)
+        gK = make(ohm, h, K, precision=1, stream=stream, use_graphs=graphs, max_outer=200)
+        ohm.ohm_set_eta(gK, dev(stack(h, etas)))
+        BK = dev(stack(h, bs))
+        sK, stK = ohm.ohm_cn_step_batch(gK, BK, dts, 1e-9, active=[1, 1, 0])
+    stream.synchronize()
+    got = unstack(h, host(BK).reshape(-1, 1536), K)
+    assert st1[0]["converged"] and stK[1]["converged"] and stK[0]["converged"]
+    assert st1[0]["cycles"] == stK[1]["cycles"]
+    assert np.array_equal(got[1], host(B1).reshape(-1, 1536))
+    assert stK[2]["cycles"] == 0 and np.array_equal(got[2], bs[2].reshape(-1, 1536))
+
+
 def test_graphs_give_same_bits(ohm):
     h = W.uniform(16, 16, 16, 1.0 / 16)
     K = 3

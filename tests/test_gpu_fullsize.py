@@ -144,3 +144,30 @@ def test_largest_grid_512(ohm, oracle_mod):
     S = o.source(wl.B, wl.dt)
     _, norms = o.residual(got, S, wl.dt)
     assert norms["rel_l2"] <= 1.05 * wl.tol
+
+
+def test_coarse_grids_beyond_one_block_120(ohm, oracle_mod):
+    """120^3 (the largest uniform serving size whose coarsening leaves the 8^3 blocks at once:
+    60^3 and 30^3 are stepped grid-wide, 15^3 by the one-block solver): a fixed-schedule FP64
+    step against the oracle element-wise, and the mixed path converged to 1e-9 with its
+    residual re-evaluated by the oracle."""
+    h = W.uniform(120, 120, 120, 1.0 / 120)
+    rng = np.random.default_rng(31)
+    b = rng.standard_normal((h.nblocks, 3, 8, 8, 8))
+    eta = 10.0 ** rng.uniform(-1, 1, (h.nblocks, 1, 8, 8, 8))
+    dt = 20.0 * h.dx0 ** 2
+    o = oracle_mod.Oracle(h, 0.5, eta)
+    g = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, nu_pre=2, nu_post=2, n_coarse=6, max_outer=2)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, -1.0)
+    want, _ = o.cn_step(b, dt, -1.0, 2, 2, 6, 2)
+    torch.cuda.synchronize()
+    assert st["cycles"] == 2
+    assert rel_err(B.cpu().numpy(), want) < 1e-12
+    gm = ohm.ohm_create_hierarchy(h.base_cells, h.dx0, h.blocks, lam=0.5, precision=ohm.OHM_MIXED, nu_pre=3,
+                                  nu_post=2, n_coarse=2, max_outer=200, krylov=6, omega=1.2, nu_coarse=(1, 0))
+    Bm = dev(b)
+    sm = ohm.ohm_cn_step(gm, Bm, dev(eta), dt, 1e-9)
+    assert sm["converged"]
+    _, norms = o.residual(Bm.cpu().numpy().reshape(b.shape), o.source(b, dt), dt)
+    assert norms["rel_l2"] <= 1.05e-9

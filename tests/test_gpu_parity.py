@@ -193,6 +193,31 @@ def test_vcycle(ohm, orc, name, nu):
     assert rel_err(host(e), want.ravel()) < TOL64
 
 
+@pytest.mark.parametrize("edge", [56, 104])
+def test_coarse_grids_beyond_one_block(ohm, orc, edge):
+    """Base grids whose first coarsening that is not a multiple of 8 has more cells than the
+    one-block coarsest solver takes (56^3 -> 28^3, 104^3 -> 52^3 and 26^3): the grid-wide coarse
+    steps.  A fixed-schedule FP64 step equals the oracle's to 1e-12, and a mixed-precision step
+    converged to 1e-9 has an oracle-evaluated residual below 1.05e-9."""
+    h = W.uniform(edge, edge, edge, 1.0 / edge)
+    b, eta = rand_fields(h, 30, 2.0)
+    dt = 20.0 * h.dx0 ** 2
+    o = orc.Oracle(h, 0.5, eta)
+    g = make(ohm, h, nu_pre=2, nu_post=2, n_coarse=6, max_outer=2)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, -1.0)
+    want, _ = o.cn_step(b, dt, -1.0, 2, 2, 6, 2)
+    assert st["cycles"] == 2
+    assert rel_err(host(B), want.ravel()) < TOL64
+    gm = make(ohm, h, precision=1, nu_pre=3, nu_post=2, n_coarse=2, max_outer=200, krylov=6, omega=1.2,
+              nu_coarse=(1, 0))
+    Bm = dev(b)
+    sm = ohm.ohm_cn_step(gm, Bm, dev(eta), dt, 1e-9)
+    assert sm["converged"]
+    _, norms = o.residual(host(Bm).reshape(b.shape), o.source(b, dt), dt)
+    assert norms["rel_l2"] <= 1.05e-9
+
+
 @pytest.mark.parametrize("name", list(HIERS))
 @pytest.mark.parametrize("lam", [0.5, 1.0])
 def test_cn_step_fixed_schedule(ohm, orc, name, lam):
