@@ -6,7 +6,10 @@ mixed precision), theta = 1/2 (Crank-Nicolson) and theta = 1 (backward Euler):
 * Sec. 3.1, Fig. 5: spatial order 2 for both theta with dt = 4e-3 (4/N)^2;
 * Sec. 3.2, Figs. 7-9: Gaussian diffusion on three levels against the exact solution;
 * Sec. 3.3, Figs. 10-11: implicit steps of dt = 0.1 agree with the explicit solution (computed
-  by the oracle's explicit predictor-corrector), and the gap closes at second order.
+  by the oracle's explicit predictor-corrector), and the gap closes at second order;
+* the nested-sphere AMR workload (base 64^3 in the benchmark, scaled here to base 32^3 with the
+  same three refinement levels, eta and current ring) against the oracle's explicit
+  predictor-corrector, level by level.
 """
 import json
 import math
@@ -156,3 +159,37 @@ def test_e7_implicit_agrees_with_explicit(ohm, oracle_mod):
     assert gaps[(0.1, 0)] < 5e-3
     assert gaps[(0.1, 0)] / gaps[(0.05, 0)] == pytest.approx(4.0, rel=0.3)
     assert gaps[(0.1, 1)] == pytest.approx(gaps[(0.1, 0)], rel=1e-3)
+
+
+def test_nested_spheres_cn_agrees_with_explicit_on_every_level(ohm, oracle_mod):
+    """Three nested refinement levels about a current ring (the AMR workload, base 32^3): CN at
+    dt = 4, 2, 1 times the finest-level explicit limit against 80 explicit predictor-corrector
+    steps at 0.1 times the limit (the oracle), to the same time.  Where the ring diffuses
+    (levels 2 and 3) the gap is above round-off and falls 4x per halving of dt (second order in
+    time, the same spatial operator on both sides); on level 1, where eta is ~1e-3 of its peak,
+    both agree to round-off.  FP64, and mixed precision (float32 inner defect correction, converged
+    to 1e-11) within 1e-10 of the FP64 gaps, through the CUDA path."""
+    wl = W.nested_spheres_64(n=32)
+    h = wl.hier
+    o = oracle_mod.Oracle(h, 0.5, wl.eta)
+    B0 = o.sync_down(wl.B)
+    dxf = h.dx(h.nlevels - 1)
+    dte = dxf * dxf / (6.0 * float(wl.eta.max()))
+    Be = B0.copy()
+    for _ in range(80):
+        Be = o.heun_step(Be, 0.1 * dte)
+    lv, leaf = h.blocks[:, 0], h.is_leaf()
+
+    def gaps(B):
+        return {l: float(np.abs(B[(lv == l) & leaf] - Be[(lv == l) & leaf]).max())
+                for l in range(1, h.nlevels) if ((lv == l) & leaf).any()}
+
+    g = {m: gaps(run(ohm, h, wl.eta, B0, 0.5, m * dte, 8 // m)) for m in (4, 2, 1)}
+    gm = gaps(run(ohm, h, wl.eta, B0, 0.5, 4 * dte, 2, precision=1, tol=1e-11))
+    assert set(g[4]) == {1, 2, 3}
+    for l in (2, 3):
+        assert g[4][l] > 1e-9
+        assert g[4][l] / g[2][l] == pytest.approx(4.0, rel=0.15)
+        assert g[2][l] / g[1][l] == pytest.approx(4.0, rel=0.15)
+        assert abs(gm[l] - g[4][l]) <= 1e-2 * g[4][l] + 1e-10
+    assert max(g[m][1] for m in g) < 1e-12 and gm[1] < 1e-10
