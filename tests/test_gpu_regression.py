@@ -188,7 +188,7 @@ def test_nested_spheres_cn_agrees_with_explicit_on_every_level(ohm, oracle_mod):
     gm = gaps(run(ohm, h, wl.eta, B0, 0.5, 4 * dte, 2, precision=1, tol=1e-11))
     assert set(g[4]) == {1, 2, 3}
     for l in (2, 3):
-        assert g[4][l] > 1e-9
+        assert g[4][l] > 1e-10  # at least 100x the solver tolerance (1e-12 of max |B| = 1)
         assert g[4][l] / g[2][l] == pytest.approx(4.0, rel=0.15)
         assert g[2][l] / g[1][l] == pytest.approx(4.0, rel=0.15)
         assert abs(gm[l] - g[4][l]) <= 1e-2 * g[4][l] + 1e-10
