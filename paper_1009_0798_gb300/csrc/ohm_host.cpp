@@ -93,10 +93,8 @@ struct ohm_hier {
     // per-block inner-product weights, multi-dot scratch and results (device and pinned host)
     float *kv[KMAX + 1] = {}, *kz[KMAX] = {};
     double *wblk = nullptr, *kpart = nullptr, *kdots = nullptr, *hdots = nullptr;
-    // batched FGMRES: per-instance products (pinned copy), coefficients (device, pinned) and the
-    // instance of every block
-    double *hdotsK = nullptr;
-    float *kcoef = nullptr, *hcoef = nullptr;
+    // batched FGMRES: per-instance coefficients (device) and the instance of every block
+    float *kcoef = nullptr;
     int *binst = nullptr;
     std::vector<double> wblk_host;
     Buffers amrbuf;               // AMR levels, all blocks
@@ -128,6 +126,13 @@ struct ohm_hier {
     cudaGraphExec_t graph = nullptr;
     bool graph_warm = false, graph_failed = false;
     int64_t graph_launches = 0;
+    // batched FGMRES: per-instance scalars on the device, a pinned staging area (target, cycles,
+    // run and live flags) and the CUDA graph of one restart cycle
+    FgState fg;
+    char *fg_host = nullptr;
+    cudaGraphExec_t fg_graph = nullptr;
+    bool fg_warm = false, fg_failed = false;
+    int64_t fg_launches = 0;
 
     // instrumentation: kernel launches issued, and CUDA-event timing of one kernel kind
     int64_t nlaunch = 0;
@@ -473,10 +478,18 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
             for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
             want((void **)&H->wblk, n * sizeof(double));
             if (H->batched) {
+                const size_t K = (size_t)H->K;
                 want((void **)&H->kpart, n * (KMAX + 1) * sizeof(double));
-                want((void **)&H->kdots, (size_t)H->K * (KMAX + 1) * sizeof(double));
-                want((void **)&H->kcoef, (size_t)H->K * (KMAX + 1) * sizeof(float));
+                want((void **)&H->kdots, K * (KMAX + 1) * sizeof(double));
+                want((void **)&H->kcoef, K * (KMAX + 1) * sizeof(float));
                 want((void **)&H->binst, n * sizeof(int));
+                want((void **)&H->fg.Hm, K * (KMAX + 1) * KMAX * sizeof(double));
+                want((void **)&H->fg.cs, K * KMAX * sizeof(double));
+                want((void **)&H->fg.sn, K * KMAX * sizeof(double));
+                want((void **)&H->fg.g, K * (KMAX + 1) * sizeof(double));
+                want((void **)&H->fg.beta0, K * 5 * sizeof(double));  // beta0, beta, brest, target, hn
+                want((void **)&H->fg.cycles, K * 2 * sizeof(int));     // cycles, jend
+                want((void **)&H->fg.live, K * 5);                     // live, arn, act, need2, run
             } else {
                 want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
                 want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
@@ -548,11 +561,27 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
             return OHM_ERR_OOM;
         }
         if (H->kcoef) {
-            if (cudaMallocHost((void **)&H->hdotsK, (size_t)H->K * (KMAX + 1) * sizeof(double)) != cudaSuccess ||
-                cudaMallocHost((void **)&H->hcoef, (size_t)H->K * (KMAX + 1) * sizeof(float)) != cudaSuccess) {
+            if (cudaMallocHost((void **)&H->fg_host, (size_t)H->K * 16) != cudaSuccess) {
                 err = "pinned allocation failed";
                 return OHM_ERR_OOM;
             }
+            FgState &f = H->fg;
+            const int K = H->K;
+            f.beta = f.beta0 + K;
+            f.brest = f.beta0 + 2 * K;
+            f.target = f.beta0 + 3 * K;
+            f.hn = f.beta0 + 4 * K;
+            f.jend = f.cycles + K;
+            f.arn = f.live + K;
+            f.act = f.live + 2 * K;
+            f.need2 = f.live + 3 * K;
+            f.run = f.live + 4 * K;
+            f.imask = H->imask_d + K;  // the inner compute mask
+            f.dots = H->kdots;
+            f.coef = H->kcoef;
+            f.K = K;
+            f.m = H->d.krylov;
+            f.max_outer = H->d.max_outer;
             std::vector<int> bi((size_t)H->nblocks, 0);
             for (int l = 0; l < H->ranges.nlev; l++)
                 for (int q = 0; q < H->K; q++)
@@ -1325,40 +1354,115 @@ int batch_scale(ohm_hier *H, const double *dt) {
 }
 
 // ---- batched FGMRES: one Arnoldi recurrence per instance, every launch covering the batch
-// Per-instance products <w, v_i> (i < S.k) and <w, w>, read back to the host: out[q][0..k].
-int mdot_inst(ohm_hier *H, const float *w, const VecSet &S, std::vector<double> &out) {
+// Per-instance products <w, v_i> (i < S.k) and <w, w> into kdots, left on the device.
+int mdot_inst_dev(ohm_hier *H, const float *w, const VecSet &S) {
     LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks,
            launch_mdot_inst(w, S, H->wblk, (int)H->nblocks, H->ranges, H->K, H->kpart, H->kdots, H->s));
-    CK(cudaMemcpyAsync(H->hdotsK, H->kdots, (size_t)H->K * (KMAX + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
-    CK(cudaStreamSynchronize(H->s));
-    out.assign(H->hdotsK, H->hdotsK + (size_t)H->K * (KMAX + 1));
     return OHM_OK;
 }
 
-// dst = (src - sum_i c[q][i] v_i) * sc[q] per instance q; c and sc are host arrays
-// ([K][KMAX] and [K]); a zero coefficient skips its vector for that instance.
-int maxpy_inst(ohm_hier *H, float *dst, const float *src, const VecSet &S, const std::vector<float> &c,
-               const std::vector<float> &sc) {
-    const int K = H->K;
-    for (int q = 0; q < K; q++) {
-        for (int i = 0; i < KMAX; i++) H->hcoef[(size_t)q * (KMAX + 1) + i] = i < S.k ? c[(size_t)q * KMAX + i] : 0.f;
-        H->hcoef[(size_t)q * (KMAX + 1) + KMAX] = sc[q];
+// dst = (src - sum_i coef[q][i] v_i) * coef[q][KMAX] with the coefficients on the device
+int maxpy_inst_dev(ohm_hier *H, float *dst, const float *src, const VecSet &S) {
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks,
+           launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s));
+    return OHM_OK;
+}
+
+#define FG(op, j) LAUNCH(H, OHM_K_KRYLOV, 0, launch_fg(H->fg, op, j, H->s))
+
+// While a kernel kind is being timed (never under graph capture), the share of instances the
+// device-side mask lets through is read back so that the timed launches count only the cells
+// they iterate.
+int fg_prof_mask(ohm_hier *H) {
+    if (H->prof_kind < 0) return OHM_OK;
+    char *hs = H->fg_host + (size_t)H->K * 13;
+    CK(cudaMemcpyAsync(hs, H->fg.imask, H->K, cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    H->active_frac = (double)std::count_if(hs, hs + H->K, [](char v) { return v != 0; }) / H->K;
+    return OHM_OK;
+}
+
+// One restart cycle of the batched FGMRES(m), stream work only: m Arnoldi steps (each: the
+// V-cycle and the operator on the active instances, classical Gram-Schmidt with one-pass
+// normalisation, or a measured norm where cancellation was large, and the Givens update), the
+// solution update x += Z y, then the true residual rhs - L x, its norm and the restart
+// decisions; finally the live flags and cycle counts are copied to pinned host memory.
+int fg_cycle(ohm_hier *H, double lamdt) {
+    const int m = H->d.krylov;
+    float *x = (float *)H->eacc, *rhs = (float *)H->rout;
+    VecSet none;
+    none.k = 0;
+    int st;
+    FG(FG_CYCLE, 0);
+    for (int j = 0; j < m; j++) {
+        FG(FG_ACT, j);
+        if ((st = fg_prof_mask(H))) return st;
+        void *r_save = H->amrbuf.r, *e_save = H->amrbuf.e;
+        H->amrbuf.r = H->kv[j];
+        H->amrbuf.e = H->kz[j];
+        st = vcycle<float>(H, lamdt);
+        H->amrbuf.r = r_save;
+        H->amrbuf.e = e_save;
+        if (st) return st;
+        if ((st = apply_L32(H, H->kz[j], nullptr, 1.0, lamdt, 0.0, H->kv[j + 1], lamdt))) return st;
+        VecSet S;
+        S.k = j + 1;
+        for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
+        if ((st = mdot_inst_dev(H, H->kv[j + 1], S))) return st;
+        FG(FG_ORTHO, j);
+        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], S))) return st;
+        if ((st = mdot_inst_dev(H, H->kv[j + 1], none))) return st;
+        FG(FG_RENORM, j);
+        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], none))) return st;
+        FG(FG_GIVENS, j);
     }
-    CK(cudaMemcpyAsync(H->kcoef, H->hcoef, (size_t)K * (KMAX + 1) * sizeof(float), cudaMemcpyHostToDevice, H->s));
-    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s));
-    // the pinned coefficients are rewritten by the next call: wait for this copy
-    CK(cudaStreamSynchronize(H->s));
+    FG(FG_SOLVE, 0);
+    VecSet Z;
+    Z.k = m;
+    for (int i = 0; i < m; i++) Z.v[i] = H->kz[i];
+    if ((st = maxpy_inst_dev(H, x, x, Z))) return st;
+    FG(FG_RESTART_MASK, 0);
+    if ((st = fg_prof_mask(H))) return st;
+    if ((st = apply_L32(H, x, rhs, -1.0, -lamdt, 1.0, H->kv[0], lamdt))) return st;
+    if ((st = mdot_inst_dev(H, H->kv[0], none))) return st;
+    FG(FG_RESTART, 0);
+    if ((st = maxpy_inst_dev(H, H->kv[0], H->kv[0], none))) return st;
+    const int K = H->K;
+    CK(cudaMemcpyAsync(H->fg_host + (size_t)K * 12, H->fg.live, K, cudaMemcpyDeviceToHost, H->s));
+    CK(cudaMemcpyAsync(H->fg_host + (size_t)K * 8, H->fg.cycles, (size_t)K * sizeof(int), cudaMemcpyDeviceToHost, H->s));
     return OHM_OK;
 }
 
-// compute mask of the batched iteration kernels from a host flag array (uploaded)
-int set_cmask(ohm_hier *H, const uint8_t *flags) {
-    uint8_t *dm = H->imask_d + H->K;  // the inner mask slot
-    memcpy(H->imask_h + H->K, flags, H->K);
-    CK(cudaMemcpyAsync(dm, H->imask_h + H->K, H->K, cudaMemcpyHostToDevice, H->s));
-    CK(cudaStreamSynchronize(H->s));  // the pinned flags are rewritten by the next call
-    H->cmask = dm;
-    H->active_frac = (double)std::count(flags, flags + H->K, 1) / H->K;
+// Runs fg_cycle eagerly, or (use_graphs, non-default stream) replays a CUDA graph captured from
+// it on its second use: every pointer, count and coefficient it needs lives on the device.
+int run_fg_cycle(ohm_hier *H, double lamdt) {
+    const bool want = H->d.use_graphs && H->s != nullptr && !H->fg_failed && H->prof_kind < 0;
+    if (!want) return fg_cycle(H, lamdt);
+    if (!H->fg_graph) {
+        if (!H->fg_warm) {
+            H->fg_warm = true;
+            return fg_cycle(H, lamdt);
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(H->s, cudaStreamCaptureModeThreadLocal));
+        const int64_t n0 = H->nlaunch;
+        const int st = fg_cycle(H, lamdt);
+        const cudaError_t ec = cudaStreamEndCapture(H->s, &g);
+        cudaError_t ei = cudaErrorUnknown;
+        if (st == OHM_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&H->fg_graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st != OHM_OK || ec != cudaSuccess || ei != cudaSuccess) {
+            cudaGetLastError();
+            H->fg_graph = nullptr;
+            H->fg_failed = true;
+            H->nlaunch = n0;
+            return fg_cycle(H, lamdt);  // the capture executed nothing: run eagerly
+        }
+        H->fg_launches = H->nlaunch - n0;
+        H->nlaunch = n0;
+    }
+    H->nlaunch += H->fg_launches;
+    CK(cudaGraphLaunch(H->fg_graph, H->s));
     return OHM_OK;
 }
 
@@ -1367,167 +1471,45 @@ int set_cmask(ohm_hier *H, const uint8_t *flags) {
 // own Arnoldi basis coefficients, Hessenberg matrix, Givens rotations, restarts and stopping
 // test (target[q], stagnation, V-cycle budget), so its iterates do not depend on the others;
 // the V-cycles, operator applications and vector kernels of all running instances share
-// launches, and instances that stopped are skipped by the compute mask.  x is left in eacc.
+// launches, and instances that stopped are skipped by the compute mask.  The scalar recurrence
+// runs on the device (k_fg), so the host waits once per restart cycle.  x is left in eacc.
 int inner_fgmres_batch(ohm_hier *H, double lamdt, const std::vector<double> &target, const uint8_t *run,
                        std::vector<int> &cycles) {
-    const int K = H->K, m = H->d.krylov;
+    const int K = H->K;
     const size_t nel = (size_t)H->nblocks * 3 * B3;
     float *x = (float *)H->eacc, *rhs = (float *)H->rout;
     int st;
+    // target (doubles), cycles (ints) and run flags in, through the pinned staging area
+    char *hs = H->fg_host;
+    memcpy(hs, target.data(), (size_t)K * sizeof(double));
+    memcpy(hs + (size_t)K * 8, cycles.data(), (size_t)K * sizeof(int));
+    memcpy(hs + (size_t)K * 12, run, K);
+    CK(cudaMemcpyAsync(H->fg.target, hs, (size_t)K * sizeof(double), cudaMemcpyHostToDevice, H->s));
+    CK(cudaMemcpyAsync(H->fg.cycles, hs + (size_t)K * 8, (size_t)K * sizeof(int), cudaMemcpyHostToDevice, H->s));
+    CK(cudaMemcpyAsync(H->fg.run, hs + (size_t)K * 12, K, cudaMemcpyHostToDevice, H->s));
     CK(cudaMemsetAsync(x, 0, nel * sizeof(float), H->s));
-    std::vector<double> nn, beta0(K, 0.0), beta(K, 0.0), brest(K, 0.0);
-    std::vector<double> Hm((size_t)K * (m + 1) * m), cs((size_t)K * m), sn((size_t)K * m), g((size_t)K * (m + 1)), y(m);
-    std::vector<uint8_t> live(K, 0), arn(K, 0), act(K, 0), need2(K, 0);
-    std::vector<int> jend(K, 0);
-    std::vector<float> c((size_t)K * KMAX, 0.f), sc(K, 1.f);
-    std::vector<double> hn(K, 0.0);
-    auto h = [&](int q, int i, int j) -> double & { return Hm[((size_t)q * (m + 1) + i) * m + j]; };
     VecSet none;
     none.k = 0;
-    if ((st = mdot_inst(H, rhs, none, nn))) return st;
-    for (int q = 0; q < K; q++) {
-        beta0[q] = beta[q] = brest[q] = std::sqrt(std::max(nn[(size_t)q * (KMAX + 1)], 0.0));
-        live[q] = run[q] && beta0[q] > 0 && std::isfinite(beta0[q]);
-        sc[q] = live[q] ? (float)(1.0 / beta0[q]) : 1.f;
+    if ((st = mdot_inst_dev(H, rhs, none))) return st;
+    FG(FG_START, 0);
+    if ((st = maxpy_inst_dev(H, H->kv[0], rhs, none))) return st;
+    CK(cudaMemcpyAsync(hs + (size_t)K * 12, H->fg.live, K, cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));  // the staging area is read back below and reused
+    H->cmask = H->fg.imask;
+    H->active_frac = 1.0;
+    bool any = std::any_of(hs + (size_t)K * 12, hs + (size_t)K * 13, [](char v) { return v != 0; });
+    while (any) {
+        st = run_fg_cycle(H, lamdt);
+        if (st) break;
+        if (cudaStreamSynchronize(H->s) != cudaSuccess) {
+            st = OHM_ERR_CUDA;
+            break;
+        }
+        any = std::any_of(hs + (size_t)K * 12, hs + (size_t)K * 13, [](char v) { return v != 0; });
     }
-    if ((st = maxpy_inst(H, H->kv[0], rhs, none, c, sc))) return st;
-    for (;;) {
-        bool any_live = false;
-        for (int q = 0; q < K; q++) {
-            arn[q] = live[q];
-            any_live |= live[q] != 0;
-            jend[q] = 0;
-            std::fill(g.begin() + (size_t)q * (m + 1), g.begin() + (size_t)(q + 1) * (m + 1), 0.0);
-            g[(size_t)q * (m + 1)] = beta[q];
-        }
-        if (!any_live) break;
-        for (int j = 0; j < m; j++) {
-            bool any = false;
-            for (int q = 0; q < K; q++) {
-                act[q] = arn[q] && cycles[q] < H->d.max_outer;
-                any |= act[q] != 0;
-            }
-            if (!any) break;
-            // z_j = V-cycle applied to v_j, w = L z_j, for the active instances
-            if ((st = set_cmask(H, act.data()))) return st;
-            void *r_save = H->amrbuf.r, *e_save = H->amrbuf.e;
-            H->amrbuf.r = H->kv[j];
-            H->amrbuf.e = H->kz[j];
-            st = vcycle<float>(H, lamdt);
-            H->amrbuf.r = r_save;
-            H->amrbuf.e = e_save;
-            if (!st) st = apply_L32(H, H->kz[j], nullptr, 1.0, lamdt, 0.0, H->kv[j + 1], lamdt);
-            H->cmask = nullptr;
-            if (st) return st;
-            for (int q = 0; q < K; q++) cycles[q] += act[q];
-            VecSet S;
-            S.k = j + 1;
-            for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
-            if ((st = mdot_inst(H, H->kv[j + 1], S, nn))) return st;
-            bool any2 = false;
-            for (int q = 0; q < K; q++) {
-                need2[q] = 0;
-                sc[q] = 1.f;
-                for (int i = 0; i < KMAX; i++) c[(size_t)q * KMAX + i] = 0.f;
-                if (!act[q]) continue;
-                const double *d = &nn[(size_t)q * (KMAX + 1)];
-                double proj = 0.0;
-                for (int i = 0; i <= j; i++) {
-                    h(q, i, j) = d[i];
-                    c[(size_t)q * KMAX + i] = (float)d[i];
-                    proj += d[i] * d[i];
-                }
-                const double ww = d[j + 1];
-                if (ww - proj > 0.01 * ww) {  // orthogonalise and normalise in one pass
-                    hn[q] = std::sqrt(ww - proj);
-                    sc[q] = (float)(1.0 / hn[q]);
-                } else {
-                    need2[q] = 1;
-                    any2 = true;
-                }
-            }
-            if ((st = maxpy_inst(H, H->kv[j + 1], H->kv[j + 1], S, c, sc))) return st;
-            if (any2) {  // the norm measured after orthogonalising, where cancellation was large
-                if ((st = mdot_inst(H, H->kv[j + 1], none, nn))) return st;
-                for (int q = 0; q < K; q++) {
-                    sc[q] = 1.f;
-                    if (!need2[q]) continue;
-                    hn[q] = std::sqrt(std::max(nn[(size_t)q * (KMAX + 1)], 0.0));
-                    if (hn[q] > 0) sc[q] = (float)(1.0 / hn[q]);
-                }
-                std::fill(c.begin(), c.end(), 0.f);
-                if ((st = maxpy_inst(H, H->kv[j + 1], H->kv[j + 1], none, c, sc))) return st;
-            }
-            for (int q = 0; q < K; q++) {
-                if (!act[q]) continue;
-                double *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
-                h(q, j + 1, j) = hn[q];
-                for (int i = 0; i < j; i++) {
-                    const double t = cq[i] * h(q, i, j) + sq[i] * h(q, i + 1, j);
-                    h(q, i + 1, j) = -sq[i] * h(q, i, j) + cq[i] * h(q, i + 1, j);
-                    h(q, i, j) = t;
-                }
-                const double den = std::hypot(h(q, j, j), h(q, j + 1, j));
-                cq[j] = den > 0 ? h(q, j, j) / den : 1.0;
-                sq[j] = den > 0 ? h(q, j + 1, j) / den : 0.0;
-                h(q, j, j) = den;
-                h(q, j + 1, j) = 0.0;
-                gq[j + 1] = -sq[j] * gq[j];
-                gq[j] = cq[j] * gq[j];
-                jend[q] = j + 1;
-                if (std::fabs(gq[j + 1]) <= target[q] * beta0[q] || !(hn[q] > 0)) {
-                    arn[q] = 0;
-                    live[q] = 0;  // converged (or breakdown): no restart
-                }
-            }
-        }
-        // x += sum_i y_i z_i per instance (R y = g)
-        int kmax = 0;
-        std::fill(c.begin(), c.end(), 0.f);
-        std::fill(sc.begin(), sc.end(), 1.f);
-        for (int q = 0; q < K; q++) {
-            const int je = jend[q];
-            kmax = std::max(kmax, je);
-            for (int i = je - 1; i >= 0; i--) {
-                double t = g[(size_t)q * (m + 1) + i];
-                for (int k2 = i + 1; k2 < je; k2++) t -= h(q, i, k2) * y[k2];
-                y[i] = h(q, i, i) != 0 ? t / h(q, i, i) : 0.0;
-            }
-            for (int i = 0; i < je; i++) c[(size_t)q * KMAX + i] = (float)(-y[i]);
-        }
-        if (kmax > 0) {
-            VecSet Z;
-            Z.k = kmax;
-            for (int i = 0; i < kmax; i++) Z.v[i] = H->kz[i];
-            if ((st = maxpy_inst(H, x, x, Z, c, sc))) return st;
-        }
-        // restart from the true residual rhs - L x where an instance is still live
-        bool any_restart = false;
-        for (int q = 0; q < K; q++) {
-            if (live[q] && (cycles[q] >= H->d.max_outer || jend[q] == 0)) live[q] = 0;
-            any_restart |= live[q] != 0;
-        }
-        if (!any_restart) break;
-        if ((st = set_cmask(H, live.data()))) return st;
-        st = apply_L32(H, x, rhs, -1.0, -lamdt, 1.0, H->kv[0], lamdt);
-        H->cmask = nullptr;
-        if (st) return st;
-        if ((st = mdot_inst(H, H->kv[0], none, nn))) return st;
-        std::fill(c.begin(), c.end(), 0.f);
-        for (int q = 0; q < K; q++) {
-            sc[q] = 1.f;
-            if (!live[q]) continue;
-            beta[q] = std::sqrt(std::max(nn[(size_t)q * (KMAX + 1)], 0.0));
-            // stop at the target, on breakdown, or when the restart cycle gained less than 2x
-            if (beta[q] <= target[q] * beta0[q] || !(beta[q] > 0) || beta[q] > 0.5 * brest[q]) {
-                live[q] = 0;
-                continue;
-            }
-            brest[q] = beta[q];
-            sc[q] = (float)(1.0 / beta[q]);
-        }
-        if ((st = maxpy_inst(H, H->kv[0], H->kv[0], none, c, sc))) return st;
-    }
+    H->cmask = nullptr;
+    if (st) return st;
+    memcpy(cycles.data(), hs + (size_t)K * 8, (size_t)K * sizeof(int));
     return OHM_OK;
 }
 
@@ -1767,12 +1749,12 @@ void ohm_destroy(ohm_hier *h) {
     if (!h) return;
     for (auto ev : h->prof_ev) cudaEventDestroy(ev);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->fg_graph) cudaGraphExecDestroy(h->fg_graph);
     if (h->pool) cudaFree(h->pool);
+    if (h->fg_host) cudaFreeHost(h->fg_host);
     if (h->hnorm) cudaFreeHost(h->hnorm);
     if (h->hnormK) cudaFreeHost(h->hnormK);
     if (h->imask_h) cudaFreeHost(h->imask_h);
-    if (h->hdotsK) cudaFreeHost(h->hdotsK);
-    if (h->hcoef) cudaFreeHost(h->hcoef);
     delete h;
 }
 
@@ -1820,6 +1802,10 @@ static void reset_graph(ohm_hier *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     h->graph_warm = false;
+    if (h->fg_graph) cudaGraphExecDestroy(h->fg_graph);
+    h->fg_graph = nullptr;
+    h->fg_warm = false;
+    h->fg.max_outer = h->d.max_outer;
 }
 
 int ohm_autotune(ohm_hier *h, const double *B_dev, const double *dt, double tol, ohm_tune_result *res) {

@@ -204,6 +204,27 @@ cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float sc
 
 cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s);
 
+// Per-instance FGMRES(m) scalars of a batched hierarchy, kept on the device so that a whole
+// restart cycle is a fixed sequence of launches (capturable in a CUDA graph): Hessenberg
+// columns, Givens rotations, residual estimates and the stopping decisions, one thread per
+// instance.  dots are the products of the last multi-dot ([K][KMAX+1]); coef receives the
+// coefficients of the next multi-axpy ([K][KMAX+1], scale in the last entry); imask is the
+// compute mask of the V-cycle and operator kernels.
+struct FgState {
+    double *Hm = nullptr;                      // [K][KMAX+1][KMAX]
+    double *cs = nullptr, *sn = nullptr;       // [K][KMAX]
+    double *g = nullptr;                       // [K][KMAX+1]
+    double *beta0 = nullptr, *beta = nullptr, *brest = nullptr, *target = nullptr, *hn = nullptr;  // [K]
+    int *cycles = nullptr, *jend = nullptr;    // [K]
+    uint8_t *live = nullptr, *arn = nullptr, *act = nullptr, *need2 = nullptr, *run = nullptr;  // [K]
+    uint8_t *imask = nullptr;                  // [K]
+    const double *dots = nullptr;
+    float *coef = nullptr;
+    int K = 0, m = 0, max_outer = 0;
+};
+enum FgOp { FG_START, FG_CYCLE, FG_ACT, FG_ORTHO, FG_RENORM, FG_GIVENS, FG_SOLVE, FG_RESTART_MASK, FG_RESTART };
+cudaError_t launch_fg(const FgState &f, FgOp op, int j, cudaStream_t s);
+
 // Batched hierarchies: per-instance products out[q][0..k] (layout [ninst][KMAX+1]; part:
 // nblk * (k+1) doubles of block partials), and dst = (src - sum_i coef[q][i] v_i) * coef[q][KMAX]
 // with q = binst[block] (coef: [ninst][KMAX+1] floats on the device).

@@ -1188,6 +1188,132 @@ cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ FGMRES scalars
+// One thread per instance: the steps of FGMRES(m) (Saad 1993) that the single-problem solver
+// takes on the host, in the same order and float64 arithmetic, for every instance of a batch.
+__global__ void __launch_bounds__(128) k_fg(FgState f, int op, int j) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= f.K) return;
+    constexpr int KC = KMAX + 1;
+    const double *d = f.dots + (size_t)q * KC;
+    float *c = f.coef + (size_t)q * KC;
+    double *H = f.Hm + (size_t)q * KC * KMAX, *cs = f.cs + (size_t)q * KMAX, *sn = f.sn + (size_t)q * KMAX;
+    double *g = f.g + (size_t)q * KC;
+    auto h = [&](int i, int k) -> double & { return H[i * KMAX + k]; };
+    auto clear = [&](float scale) {
+        for (int i = 0; i < KMAX; i++) c[i] = 0.f;
+        c[KMAX] = scale;
+    };
+    switch (op) {
+        case FG_START: {  // v_0 = rhs / beta0 for the instances that iterate
+            const double b = sqrt(fmax(d[0], 0.0));
+            f.beta0[q] = f.beta[q] = f.brest[q] = b;
+            f.live[q] = f.run[q] && b > 0 && isfinite(b);
+            clear(f.live[q] ? (float)(1.0 / b) : 1.f);
+            break;
+        }
+        case FG_CYCLE: {  // a restart cycle begins: g = beta e_0
+            f.arn[q] = f.live[q];
+            f.jend[q] = 0;
+            for (int i = 0; i < KC; i++) g[i] = 0.0;
+            g[0] = f.beta[q];
+            break;
+        }
+        case FG_ACT: {  // instances that take Arnoldi step j (their V-cycle is counted)
+            const uint8_t a = f.arn[q] && f.cycles[q] < f.max_outer;
+            f.act[q] = a;
+            f.imask[q] = a;
+            f.cycles[q] += a;
+            break;
+        }
+        case FG_ORTHO: {  // h_ij = <w, v_i>; one-pass normalisation unless cancellation is large
+            clear(1.f);
+            f.need2[q] = 0;
+            if (!f.act[q]) break;
+            double proj = 0.0;
+            for (int i = 0; i <= j; i++) {
+                h(i, j) = d[i];
+                c[i] = (float)d[i];
+                proj += d[i] * d[i];
+            }
+            const double ww = d[j + 1];
+            if (ww - proj > 0.01 * ww) {
+                f.hn[q] = sqrt(ww - proj);
+                c[KMAX] = (float)(1.0 / f.hn[q]);
+            } else {
+                f.need2[q] = 1;
+            }
+            break;
+        }
+        case FG_RENORM: {  // the norm measured after orthogonalising, where the one pass was refused
+            clear(1.f);
+            if (!f.act[q] || !f.need2[q]) break;
+            f.hn[q] = sqrt(fmax(d[0], 0.0));
+            if (f.hn[q] > 0) c[KMAX] = (float)(1.0 / f.hn[q]);
+            break;
+        }
+        case FG_GIVENS: {
+            if (!f.act[q]) break;
+            const double hnq = f.hn[q];
+            h(j + 1, j) = hnq;
+            for (int i = 0; i < j; i++) {
+                const double t = cs[i] * h(i, j) + sn[i] * h(i + 1, j);
+                h(i + 1, j) = -sn[i] * h(i, j) + cs[i] * h(i + 1, j);
+                h(i, j) = t;
+            }
+            const double den = hypot(h(j, j), h(j + 1, j));
+            cs[j] = den > 0 ? h(j, j) / den : 1.0;
+            sn[j] = den > 0 ? h(j + 1, j) / den : 0.0;
+            h(j, j) = den;
+            h(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            f.jend[q] = j + 1;
+            if (fabs(g[j + 1]) <= f.target[q] * f.beta0[q] || !(hnq > 0)) {
+                f.arn[q] = 0;
+                f.live[q] = 0;  // converged (or breakdown): no restart
+            }
+            break;
+        }
+        case FG_SOLVE: {  // x += sum y_i z_i with R y = g
+            clear(1.f);
+            const int je = f.jend[q];
+            double y[KMAX];
+            for (int i = je - 1; i >= 0; i--) {
+                double t = g[i];
+                for (int k = i + 1; k < je; k++) t -= h(i, k) * y[k];
+                y[i] = h(i, i) != 0 ? t / h(i, i) : 0.0;
+            }
+            for (int i = 0; i < je; i++) c[i] = (float)(-y[i]);
+            break;
+        }
+        case FG_RESTART_MASK: {  // restart where the instance is live and may take more cycles
+            if (f.live[q] && (f.cycles[q] >= f.max_outer || f.jend[q] == 0)) f.live[q] = 0;
+            f.imask[q] = f.live[q];
+            break;
+        }
+        case FG_RESTART: {  // stop at the target, on breakdown, or when the cycle gained < 2x
+            clear(1.f);
+            if (!f.live[q]) break;
+            const double b = sqrt(fmax(d[0], 0.0));
+            f.beta[q] = b;
+            if (b <= f.target[q] * f.beta0[q] || !(b > 0) || b > 0.5 * f.brest[q]) {
+                f.live[q] = 0;
+                break;
+            }
+            f.brest[q] = b;
+            c[KMAX] = (float)(1.0 / b);
+            break;
+        }
+    }
+}
+
+cudaError_t launch_fg(const FgState &f, FgOp op, int j, cudaStream_t s) {
+    if (f.K == 0) return cudaSuccess;
+    k_fg<<<(f.K + 127) / 128, 128, 0, s>>>(f, (int)op, j);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ inverse diagonal
 // inv_c = omega / (1 + alpha_c), alpha_c = lamdt/h^2 sum_{a != c} (eta_{-1/2} + eta_{+1/2})
 // with face eta the mean of the two cells (Eqs. 11, 21-23).

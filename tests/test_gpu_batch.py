@@ -273,24 +273,55 @@ def test_fgmres_batch_converges_to_oracle(ohm, orc, name):
         assert rel_err(got[q], want.reshape(-1, 1536)) < 1e-9, q
 
 
+@pytest.mark.parametrize("graphs", [False, True])
 @pytest.mark.parametrize("precision", [1, 2])
-def test_fgmres_batch_same_bits_alone_and_in_batch(ohm, precision):
+def test_fgmres_batch_same_bits_alone_and_in_batch(ohm, precision, graphs):
+    """Per-instance FGMRES(4): an instance gives the same bits alone and in a batch, with the
+    restart cycles run eagerly or replayed from a CUDA graph (two steps: the second replays)."""
     h = amr_two_level(16)
     K = 4
     bs, etas = instances(h, K, 95)
     dts = [(2.0 + q) * h.dx(1) ** 2 for q in range(K)]
-    g1 = make(ohm, h, 1, precision=precision, krylov=4)
-    ohm.ohm_set_eta(g1, dev(etas[1]))
-    B1 = dev(bs[1])
-    _, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[1]], 1e-9)
-    gK = make(ohm, h, K, precision=precision, krylov=4)
-    ohm.ohm_set_eta(gK, dev(stack(h, etas)))
-    BK = dev(stack(h, bs))
-    _, stK = ohm.ohm_cn_step_batch(gK, BK, dts, 1e-9, active=[1, 1, 0, 1])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g1 = make(ohm, h, 1, precision=precision, krylov=4, stream=stream, use_graphs=graphs)
+        ohm.ohm_set_eta(g1, dev(etas[1]))
+        B1 = dev(bs[1])
+        _, st1 = ohm.ohm_cn_step_batch(g1, B1, [dts[1]], 1e-9)
+        _, st1b = ohm.ohm_cn_step_batch(g1, B1, [dts[1]], 1e-9)
+        gK = make(ohm, h, K, precision=precision, krylov=4, stream=stream, use_graphs=graphs)
+        ohm.ohm_set_eta(gK, dev(stack(h, etas)))
+        BK = dev(stack(h, bs))
+        _, stK = ohm.ohm_cn_step_batch(gK, BK, dts, 1e-9, active=[1, 1, 0, 1])
+        _, stKb = ohm.ohm_cn_step_batch(gK, BK, dts, 1e-9, active=[1, 1, 0, 1])
+    stream.synchronize()
     got = unstack(h, host(BK).reshape(-1, 1536), K)
     assert st1[0]["converged"] and stK[1]["converged"] and st1[0]["cycles"] == stK[1]["cycles"]
+    assert st1b[0]["converged"] and st1b[0]["cycles"] == stKb[1]["cycles"]
     assert np.array_equal(got[1], host(B1).reshape(-1, 1536))
-    assert stK[2]["cycles"] == 0
+    assert stK[2]["cycles"] == 0 and stKb[2]["cycles"] == 0
+
+
+def test_fgmres_batch_graphs_give_same_bits(ohm):
+    """The batched FGMRES restart cycle replayed from a CUDA graph gives the bits of the eager
+    launches (three steps of a 3-instance batch)."""
+    h = W.uniform(16, 16, 16, 1.0 / 16)
+    K = 3
+    bs, etas = instances(h, K, 97)
+    dts = [(4.0 + q) * h.dx0 ** 2 for q in range(K)]
+    outs = []
+    for graphs in (False, True):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            g = make(ohm, h, K, precision=1, krylov=5, stream=stream, use_graphs=graphs)
+            ohm.ohm_set_eta(g, dev(stack(h, etas)))
+            B = dev(stack(h, bs))
+            for _ in range(3):
+                status, st = ohm.ohm_cn_step_batch(g, B, dts, 1e-9)
+                assert status == ohm.OHM_OK
+        stream.synchronize()
+        outs.append(host(B))
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_fgmres_batch_takes_fewer_cycles(ohm):
