@@ -86,9 +86,10 @@ typedef struct {
                                    of that level one instance after another (for one-level
                                    hierarchies: instance after instance).  With krylov = m
                                    each instance runs its own FGMRES(m) recurrence.             */
-    int32_t use_graphs;         /* batches only: 1 = the inner iteration (V-cycle, update and
-                                   residual) is captured once into a CUDA graph and replayed.
-                                   Needs a non-NULL stream; ignored otherwise.                  */
+    int32_t use_graphs;         /* batches only: 1 = the defect-correction inner iteration
+                                   (V-cycle, update and residual) and, with krylov > 0, every
+                                   FGMRES restart cycle are captured once into a CUDA graph and
+                                   replayed.  Needs a non-NULL stream; ignored otherwise.      */
     void *stream;               /* cudaStream_t used for all work, NULL = legacy default      */
     double omega;               /* relaxation factor of the red-black sweeps: each colour update
                                    becomes e + omega (e_GS - e) (red-black SOR).  0 selects 1,

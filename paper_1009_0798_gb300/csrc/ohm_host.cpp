@@ -477,22 +477,25 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
             for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * sizeof(float));
             for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
             want((void **)&H->wblk, n * sizeof(double));
+            const size_t K = (size_t)H->K;
             if (H->batched) {
-                const size_t K = (size_t)H->K;
                 want((void **)&H->kpart, n * (KMAX + 1) * sizeof(double));
                 want((void **)&H->kdots, K * (KMAX + 1) * sizeof(double));
-                want((void **)&H->kcoef, K * (KMAX + 1) * sizeof(float));
                 want((void **)&H->binst, n * sizeof(int));
+            } else {
+                want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
+                want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
+            }
+            // batches: the FGMRES scalars of every instance on the device
+            if (H->batched) want((void **)&H->kcoef, K * (KMAX + 1) * sizeof(float));
+            if (H->batched) {
                 want((void **)&H->fg.Hm, K * (KMAX + 1) * KMAX * sizeof(double));
                 want((void **)&H->fg.cs, K * KMAX * sizeof(double));
                 want((void **)&H->fg.sn, K * KMAX * sizeof(double));
                 want((void **)&H->fg.g, K * (KMAX + 1) * sizeof(double));
                 want((void **)&H->fg.beta0, K * 5 * sizeof(double));  // beta0, beta, brest, target, hn
-                want((void **)&H->fg.cycles, K * 2 * sizeof(int));     // cycles, jend
-                want((void **)&H->fg.live, K * 5);                     // live, arn, act, need2, run
-            } else {
-                want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
-                want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
+                want((void **)&H->fg.cycles, K * 2 * sizeof(int) + sizeof(int));  // cycles, jend, any_need2
+                want((void **)&H->fg.live, K * 6);  // live, arn, act, need2, run, compute mask
             }
         }
     }
@@ -560,28 +563,7 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
             err = "pinned allocation failed";
             return OHM_ERR_OOM;
         }
-        if (H->kcoef) {
-            if (cudaMallocHost((void **)&H->fg_host, (size_t)H->K * 16) != cudaSuccess) {
-                err = "pinned allocation failed";
-                return OHM_ERR_OOM;
-            }
-            FgState &f = H->fg;
-            const int K = H->K;
-            f.beta = f.beta0 + K;
-            f.brest = f.beta0 + 2 * K;
-            f.target = f.beta0 + 3 * K;
-            f.hn = f.beta0 + 4 * K;
-            f.jend = f.cycles + K;
-            f.arn = f.live + K;
-            f.act = f.live + 2 * K;
-            f.need2 = f.live + 3 * K;
-            f.run = f.live + 4 * K;
-            f.imask = H->imask_d + K;  // the inner compute mask
-            f.dots = H->kdots;
-            f.coef = H->kcoef;
-            f.K = K;
-            f.m = H->d.krylov;
-            f.max_outer = H->d.max_outer;
+        if (H->kcoef) {  // the instance of every block (the FGMRES state is set up below)
             std::vector<int> bi((size_t)H->nblocks, 0);
             for (int l = 0; l < H->ranges.nlev; l++)
                 for (int q = 0; q < H->K; q++)
@@ -591,6 +573,30 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
                 return OHM_ERR_CUDA;
             }
         }
+    }
+    if (H->kcoef) {  // device FGMRES scalars (batches, mixed precision with krylov > 0)
+        if (cudaMallocHost((void **)&H->fg_host, (size_t)H->K * 16) != cudaSuccess) {
+            err = "pinned allocation failed";
+            return OHM_ERR_OOM;
+        }
+        FgState &f = H->fg;
+        const int K = H->K;
+        f.beta = f.beta0 + K;
+        f.brest = f.beta0 + 2 * K;
+        f.target = f.beta0 + 3 * K;
+        f.hn = f.beta0 + 4 * K;
+        f.jend = f.cycles + K;
+        f.any_need2 = f.cycles + 2 * K;
+        f.arn = f.live + K;
+        f.act = f.live + 2 * K;
+        f.need2 = f.live + 3 * K;
+        f.run = f.live + 4 * K;
+        f.imask = f.live + 5 * K;  // compute mask of the V-cycle and operator launches
+        f.dots = H->kdots;
+        f.coef = H->kcoef;
+        f.K = K;
+        f.m = H->d.krylov;
+        f.max_outer = H->d.max_outer;
     }
     if (H->wblk) {  // inner-product weights: h^3 on leaf blocks, 0 on covered ones
         std::vector<double> w((size_t)H->nblocks, 0.0);
@@ -1077,6 +1083,7 @@ constexpr double INNER_FLOOR_DEFAULT = 1e-5;
 
 double inner_floor(const ohm_hier *H) { return H->d.inner_tol > 0 ? H->d.inner_tol : INNER_FLOOR_DEFAULT; }
 
+
 // Weighted inner products <w, v_i> (i < S.k) and <w, w>, read back to the host.
 int mdot(ohm_hier *H, const float *w, const VecSet &S, double *out) {
     LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s));
@@ -1354,17 +1361,18 @@ int batch_scale(ohm_hier *H, const double *dt) {
 }
 
 // ---- batched FGMRES: one Arnoldi recurrence per instance, every launch covering the batch
-// Per-instance products <w, v_i> (i < S.k) and <w, w> into kdots, left on the device.
-int mdot_inst_dev(ohm_hier *H, const float *w, const VecSet &S) {
+// Per-instance products <w, v_i> (i < S.k) and <w, w> into kdots, left on the device; with
+// gate, nothing runs unless the device flag is set.
+int mdot_inst_dev(ohm_hier *H, const float *w, const VecSet &S, const int *gate = nullptr) {
     LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks,
-           launch_mdot_inst(w, S, H->wblk, (int)H->nblocks, H->ranges, H->K, H->kpart, H->kdots, H->s));
+           launch_mdot_inst(w, S, H->wblk, (int)H->nblocks, H->ranges, H->K, H->kpart, H->kdots, H->s, gate));
     return OHM_OK;
 }
 
 // dst = (src - sum_i coef[q][i] v_i) * coef[q][KMAX] with the coefficients on the device
-int maxpy_inst_dev(ohm_hier *H, float *dst, const float *src, const VecSet &S) {
+int maxpy_inst_dev(ohm_hier *H, float *dst, const float *src, const VecSet &S, const int *gate = nullptr) {
     LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks,
-           launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s));
+           launch_maxpy_inst(dst, src, S, H->kcoef, H->binst, (size_t)H->nblocks * 3 * B3, H->s, gate));
     return OHM_OK;
 }
 
@@ -1382,10 +1390,10 @@ int fg_prof_mask(ohm_hier *H) {
     return OHM_OK;
 }
 
-// One restart cycle of the batched FGMRES(m), stream work only: m Arnoldi steps (each: the
-// V-cycle and the operator on the active instances, classical Gram-Schmidt with one-pass
-// normalisation, or a measured norm where cancellation was large, and the Givens update), the
-// solution update x += Z y, then the true residual rhs - L x, its norm and the restart
+// One restart cycle of the batched FGMRES(m), stream work only: m Arnoldi steps (each: the V-cycle and the operator on the active instances, classical
+// Gram-Schmidt with one-pass normalisation, or a measured norm where cancellation was large --
+// that pass returns at once on the device when no instance needs it -- and the Givens update),
+// the solution update x += Z y, then the true residual rhs - L x, its norm and the restart
 // decisions; finally the live flags and cycle counts are copied to pinned host memory.
 int fg_cycle(ohm_hier *H, double lamdt) {
     const int m = H->d.krylov;
@@ -1411,9 +1419,9 @@ int fg_cycle(ohm_hier *H, double lamdt) {
         if ((st = mdot_inst_dev(H, H->kv[j + 1], S))) return st;
         FG(FG_ORTHO, j);
         if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], S))) return st;
-        if ((st = mdot_inst_dev(H, H->kv[j + 1], none))) return st;
+        if ((st = mdot_inst_dev(H, H->kv[j + 1], none, H->fg.any_need2))) return st;
         FG(FG_RENORM, j);
-        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], none))) return st;
+        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], none, H->fg.any_need2))) return st;
         FG(FG_GIVENS, j);
     }
     FG(FG_SOLVE, 0);

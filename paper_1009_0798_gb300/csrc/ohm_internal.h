@@ -196,9 +196,11 @@ struct VecSet {
     int k = 0;
 };
 // out[0..k-1] = <w, v_i>, out[k] = <w, w>, volume weighted per block by wb (0 = excluded);
-// part: scratch of nblk * (k + 1) doubles.
+// part: scratch of nblk * (k + 1) doubles.  gate (device, may be null): when it holds 0 the
+// launches return at once and out is left as it was.
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
-                        cudaStream_t s);
+                        cudaStream_t s, const int *gate = nullptr);
+
 // dst = (src - sum c_i v_i) * scale
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s);
 
@@ -220,6 +222,7 @@ struct FgState {
     uint8_t *imask = nullptr;                  // [K]
     const double *dots = nullptr;
     float *coef = nullptr;
+    int *any_need2 = nullptr;                  // 1 when some instance needs the norm pass of the step
     int K = 0, m = 0, max_outer = 0;
 };
 enum FgOp { FG_START, FG_CYCLE, FG_ACT, FG_ORTHO, FG_RENORM, FG_GIVENS, FG_SOLVE, FG_RESTART_MASK, FG_RESTART };
@@ -228,9 +231,10 @@ cudaError_t launch_fg(const FgState &f, FgOp op, int j, cudaStream_t s);
 // Batched hierarchies: per-instance products out[q][0..k] (layout [ninst][KMAX+1]; part:
 // nblk * (k+1) doubles of block partials), and dst = (src - sum_i coef[q][i] v_i) * coef[q][KMAX]
 // with q = binst[block] (coef: [ninst][KMAX+1] floats on the device).
+// gate as for launch_mdot.
 cudaError_t launch_mdot_inst(const float *w, const VecSet &V, const double *wb, int nblk, const InstRanges &R, int ninst,
-                             double *part, double *out, cudaStream_t s);
+                             double *part, double *out, cudaStream_t s, const int *gate = nullptr);
 cudaError_t launch_maxpy_inst(float *dst, const float *src, const VecSet &V, const float *coef, const int *binst,
-                              size_t n, cudaStream_t s);
+                              size_t n, cudaStream_t s, const int *gate = nullptr);
 
 }  // namespace ohm

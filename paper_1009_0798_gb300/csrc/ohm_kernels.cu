@@ -1220,6 +1220,7 @@ __global__ void __launch_bounds__(128) k_fg(FgState f, int op, int j) {
             break;
         }
         case FG_ACT: {  // instances that take Arnoldi step j (their V-cycle is counted)
+            if (q == 0) *f.any_need2 = 0;
             const uint8_t a = f.arn[q] && f.cycles[q] < f.max_outer;
             f.act[q] = a;
             f.imask[q] = a;
@@ -1242,6 +1243,7 @@ __global__ void __launch_bounds__(128) k_fg(FgState f, int op, int j) {
                 c[KMAX] = (float)(1.0 / f.hn[q]);
             } else {
                 f.need2[q] = 1;
+                atomicOr(f.any_need2, 1);  // the norm pass after orthogonalising runs
             }
             break;
         }
@@ -1900,7 +1902,8 @@ __device__ __forceinline__ void warp_block_dots(const float *__restrict__ w, con
 // the 8 warps of a thread block are folded in warp order into part[blockIdx][col]
 template <int NV>
 __global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
-                                              int nblk, double *__restrict__ part) {
+                                              int nblk, double *__restrict__ part, const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ double sred[8][NV + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + warp;
@@ -1917,7 +1920,9 @@ __global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSe
 }
 
 // column sums of part[nrow][ncol] in a fixed order (one thread block per column)
-__global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part, int nrow, int ncol, double *__restrict__ out) {
+__global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part, int nrow, int ncol, double *__restrict__ out,
+                                                const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ double red[32];
     const int c = blockIdx.x;
     double a = 0.0;
@@ -1967,12 +1972,12 @@ __global__ void __launch_bounds__(256) k_maxpy(float4 *dst, const float4 *src, V
     }
 
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
-                        cudaStream_t s) {
+                        cudaStream_t s, const int *gate) {
     const int grid = (nblk + 7) / 8;
-#define OHM_MDOT(N) k_mdot<N><<<grid, 256, 0, s>>>(w, V, wb, nblk, part)
+#define OHM_MDOT(N) k_mdot<N><<<grid, 256, 0, s>>>(w, V, wb, nblk, part, gate)
     OHM_NV_SWITCH(V.k, OHM_MDOT)
 #undef OHM_MDOT
-    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out);
+    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out, gate);
     return cudaGetLastError();
 }
 
@@ -1987,11 +1992,13 @@ cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float sc
     return cudaGetLastError();
 }
 
+
 // Per-instance Krylov vector kernels of batched hierarchies.  Block partials: one warp per
 // block writes its weighted products (no folding across blocks, so no sum mixes instances).
 template <int NV>
 __global__ void __launch_bounds__(256) k_mdot_blocks(const float *__restrict__ w, VecSet V, const double *__restrict__ wb,
-                                                     int nblk, double *__restrict__ part) {
+                                                     int nblk, double *__restrict__ part, const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + warp;
     if (b >= nblk) return;
@@ -2003,7 +2010,8 @@ __global__ void __launch_bounds__(256) k_mdot_blocks(const float *__restrict__ w
 
 // out[q][c] = sum of part[b][c] over instance q's blocks of every level, in a fixed order
 __global__ void __launch_bounds__(256) k_colsum_inst(const double *__restrict__ part, InstRanges R, int ncol,
-                                                     double *__restrict__ out) {
+                                                     double *__restrict__ out, const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     __shared__ double red[32];
     const int q = blockIdx.x;
     for (int c = 0; c < ncol; c++) {
@@ -2018,11 +2026,11 @@ __global__ void __launch_bounds__(256) k_colsum_inst(const double *__restrict__ 
 }
 
 cudaError_t launch_mdot_inst(const float *w, const VecSet &V, const double *wb, int nblk, const InstRanges &R, int ninst,
-                             double *part, double *out, cudaStream_t s) {
-#define OHM_MDOTB(N) k_mdot_blocks<N><<<(nblk + 7) / 8, 256, 0, s>>>(w, V, wb, nblk, part)
+                             double *part, double *out, cudaStream_t s, const int *gate) {
+#define OHM_MDOTB(N) k_mdot_blocks<N><<<(nblk + 7) / 8, 256, 0, s>>>(w, V, wb, nblk, part, gate)
     OHM_NV_SWITCH(V.k, OHM_MDOTB)
 #undef OHM_MDOTB
-    k_colsum_inst<<<ninst, 256, 0, s>>>(part, R, V.k + 1, out);
+    k_colsum_inst<<<ninst, 256, 0, s>>>(part, R, V.k + 1, out, gate);
     return cudaGetLastError();
 }
 
@@ -2031,7 +2039,8 @@ cudaError_t launch_mdot_inst(const float *w, const VecSet &V, const double *wb, 
 template <int NV>
 __global__ void __launch_bounds__(256) k_maxpy_inst(float4 *dst, const float4 *src, VecSet V,
                                                     const float *__restrict__ coef, const int *__restrict__ binst,
-                                                    size_t n4) {
+                                                    size_t n4, const int *__restrict__ gate) {
+    if (gate && !*gate) return;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
         const float *cq = coef + (size_t)binst[e / 384] * (KMAX + 1);
         float4 x = src[e];
@@ -2056,12 +2065,12 @@ __global__ void __launch_bounds__(256) k_maxpy_inst(float4 *dst, const float4 *s
 }
 
 cudaError_t launch_maxpy_inst(float *dst, const float *src, const VecSet &V, const float *coef, const int *binst,
-                              size_t n, cudaStream_t s) {
+                              size_t n, cudaStream_t s, const int *gate) {
     const size_t n4 = n / 4;
     const int grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
     float4 *d4 = reinterpret_cast<float4 *>(dst);
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
-#define OHM_MAXPYI(N) k_maxpy_inst<N><<<grid, 256, 0, s>>>(d4, s4, V, coef, binst, n4)
+#define OHM_MAXPYI(N) k_maxpy_inst<N><<<grid, 256, 0, s>>>(d4, s4, V, coef, binst, n4, gate)
     OHM_NV_SWITCH(V.k, OHM_MAXPYI)
 #undef OHM_MAXPYI
     return cudaGetLastError();
