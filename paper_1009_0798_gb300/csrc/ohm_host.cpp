@@ -101,6 +101,7 @@ struct ohm_hier {
     std::vector<Buffers> mgbuf;   // blocked multigrid grids
     Buffers smallbuf[MAX_SMALL];  // small grids (t stored in e2)
     double *hnorm = nullptr;      // pinned host copy: 4 doubles + error word
+    int *flag_dev = nullptr;      // device address of the eta-comparison flag in hnorm (mapped)
 
     bool eta_set = false;
     double inv_dt = NAN;
@@ -557,6 +558,11 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
         return OHM_ERR_OOM;
     }
     H->hdots = H->hnorm + 8;
+    // the eta comparison's flag, written by the kernel straight into pinned host memory
+    if (cudaHostGetDevicePointer((void **)&H->flag_dev, H->hnorm + 24, 0) != cudaSuccess) {
+        cudaGetLastError();
+        H->flag_dev = nullptr;
+    }
     if (H->batched) {
         if (cudaMallocHost((void **)&H->hnormK, (size_t)H->K * 4 * sizeof(double)) != cudaSuccess ||
             cudaMallocHost((void **)&H->imask_h, (size_t)H->K * 2) != cudaSuccess) {
@@ -1776,15 +1782,22 @@ int ohm_set_eta(ohm_hier *h, const double *eta_dev) {
     }
     if (h->eta_set) {
         // the same values again (a time loop passing its eta every step): the coarse levels,
-        // ghosts and inverse diagonals derived from them are still valid
-        int *flag = (int *)(h->dnorm + 6);
-        CK(cudaMemsetAsync(flag, 0, sizeof(int), h->s));
-        CK(launch_differs(eta_dev, h->eta64, (size_t)h->nblocks * B3, flag, h->s));
-        CK(cudaMemcpyAsync(h->hnorm + 24, flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        // ghosts and inverse diagonals derived from them are still valid.  The comparison
+        // writes its flag straight into pinned host memory (device-accessible under unified
+        // addressing), so reading it waits only for this stream, never for a copy engine that
+        // another stream keeps busy with a large transfer.
+        volatile int *flag = reinterpret_cast<volatile int *>(h->hnorm + 24);
+        *flag = 0;  // no earlier comparison is in flight: each is waited for before its call returns
+        if (h->flag_dev) {
+            CK(launch_differs(eta_dev, h->eta64, (size_t)h->nblocks * B3, h->flag_dev, h->s));
+        } else {  // pinned memory not mapped into the device: copy the flag back
+            int *dflag = (int *)(h->dnorm + 6);
+            CK(cudaMemsetAsync(dflag, 0, sizeof(int), h->s));
+            CK(launch_differs(eta_dev, h->eta64, (size_t)h->nblocks * B3, dflag, h->s));
+            CK(cudaMemcpyAsync((void *)flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        }
         CK(cudaStreamSynchronize(h->s));
-        int differs;
-        memcpy(&differs, h->hnorm + 24, sizeof(int));
-        if (!differs) return OHM_OK;
+        if (!*flag) return OHM_OK;
     }
     CK(cudaMemcpyAsync(h->eta64, eta_dev, (size_t)h->nblocks * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     int st = h->mixed ? eta_derive<float>(h) : eta_derive<double>(h);
