@@ -456,3 +456,42 @@ def test_nonfinite_eta_reports_nonfinite(ohm):
     with pytest.raises(ohm.OhmError) as ei:
         ohm.ohm_cn_step(g, dev(b), eta, 0.01, 1e-9)
     assert ei.value.status == ohm.OHM_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vanishing_dt_leaves_the_field_and_takes_no_cycle(ohm, orc, precision):
+    """dt -> 0: L = I and S = b, so the first residual is already below tolerance (Eqs. 13-14):
+    B is returned as b (after syncing covered cells) with zero V-cycles."""
+    h = amr_two_level(16)
+    b, eta = rand_fields(h, 13, 2.0)
+    b = orc.Oracle(h, 0.5, eta).sync_down(b)
+    g = make(ohm, h, precision=precision, max_outer=5)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), 1e-14 * h.dx(1) ** 2, 1e-9)
+    assert st["converged"] and st["cycles"] == 0
+    assert rel_err(host(B), b.ravel()) < 1e-12
+
+
+@pytest.mark.parametrize("precision,krylov,stiff", [(0, 0, 1e3), (1, 6, 1e3), (1, 6, 1e4)])
+def test_very_stiff_step_converges_to_the_oracle(ohm, orc, precision, krylov, stiff):
+    """dt = 1e3 and 1e4 times the explicit limit with two decades of eta per cell: the step
+    converges (the paper's defect correction takes ~125 V-cycles at 1e3 -- the oracle's count --
+    and is left to FGMRES at 1e4, where it needs more than 400), and its float64 residual
+    evaluated by the oracle meets the tolerance."""
+    h = W.uniform(32, 32, 32, 1.0 / 32)
+    b, eta = rand_fields(h, 14, 2.0)
+    dt = stiff * h.dx0 ** 2 / (6.0 * float(eta.max()))
+    o = orc.Oracle(h, 0.5, eta)
+    g = make(ohm, h, precision=precision, krylov=krylov, max_outer=400)
+    B = dev(b)
+    st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-9)
+    assert st["converged"]
+    _, n = o.residual(host(B).reshape(b.shape), o.source(b, dt), dt)
+    assert n["rel_l2"] <= 1.05e-9
+
+
+def test_fp64_fma_rate_probe(ohm):
+    """The float64 FMA-rate probe returns a rate between 10 G and 100 T FMA/s on any GPU this
+    library runs on (the roofline denominator of the float64 kernels)."""
+    r = ohm.ohm_fp64_fma_rate()
+    assert 1e10 < r < 1e14
