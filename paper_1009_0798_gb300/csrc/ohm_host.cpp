@@ -102,6 +102,7 @@ struct ohm_hier {
     Buffers smallbuf[MAX_SMALL];  // small grids (t stored in e2)
     double *hnorm = nullptr;      // pinned host copy: 4 doubles + error word
     int *flag_dev = nullptr;      // device address of the eta-comparison flag in hnorm (mapped)
+    double *hnorm_dev = nullptr;  // device address of hnorm itself (mapped), null if not mapped
 
     bool eta_set = false;
     double inv_dt = NAN;
@@ -558,11 +559,14 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
         return OHM_ERR_OOM;
     }
     H->hdots = H->hnorm + 8;
-    // the eta comparison's flag, written by the kernel straight into pinned host memory
-    if (cudaHostGetDevicePointer((void **)&H->flag_dev, H->hnorm + 24, 0) != cudaSuccess) {
+    // the eta comparison's flag, the norms and the Krylov products, written by the kernels
+    // straight into pinned host memory: the host then reads them after synchronising its stream,
+    // without a copy that could wait behind another stream's large transfer
+    if (cudaHostGetDevicePointer((void **)&H->hnorm_dev, H->hnorm, 0) != cudaSuccess) {
         cudaGetLastError();
-        H->flag_dev = nullptr;
+        H->hnorm_dev = nullptr;
     }
+    H->flag_dev = H->hnorm_dev ? reinterpret_cast<int *>(H->hnorm_dev + 24) : nullptr;
     if (H->batched) {
         if (cudaMallocHost((void **)&H->hnormK, (size_t)H->K * 4 * sizeof(double)) != cudaSuccess ||
             cudaMallocHost((void **)&H->imask_h, (size_t)H->K * 2) != cudaSuccess) {
@@ -974,7 +978,8 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
         if (H->batched)
             LAUNCH(H, OHM_K_NORM, 0, launch_norm_inst(H->partials, H->ranges, H->K, H->dnormK, H->s));
         else
-            LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->redscr, H->dnorm, H->s));
+            LAUNCH(H, OHM_K_NORM, 0, launch_norm_reduce(H->partials, (int)H->nblocks, H->redscr, H->dnorm, H->s,
+                                                        H->hnorm_dev, H->d_err));
     }
     return OHM_OK;
 }
@@ -1012,8 +1017,19 @@ int fill_ghosts_t(ohm_hier *H, const T *x, T *ghost) {
     return OHM_OK;
 }
 
+// The error word alone, for operations that end without a norm reduction.
+int read_err(ohm_hier *H, int *err_flag) {
+    CK(cudaMemcpyAsync(H->hnorm + 4, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    memcpy(err_flag, &H->hnorm[4], sizeof(int));
+    return OHM_OK;
+}
+
+// The norms of the last norm reduction and the error word as that reduction saw it (the
+// reduction must be the last kernel on the stream that can set the error word).
 int read_norms(ohm_hier *H, double out[4], int *err_flag) {
-    CK(cudaMemcpyAsync(H->hnorm, H->dnorm, 40, cudaMemcpyDeviceToHost, H->s));
+    // the norm kernel wrote its sums and the error word into hnorm when it is mapped
+    if (!H->hnorm_dev) CK(cudaMemcpyAsync(H->hnorm, H->dnorm, 40, cudaMemcpyDeviceToHost, H->s));
     CK(cudaStreamSynchronize(H->s));
     double sr = H->hnorm[0], ss = H->hnorm[1];
     out[0] = ss > 0 ? std::sqrt(sr / ss) : std::sqrt(sr);
@@ -1092,8 +1108,10 @@ double inner_floor(const ohm_hier *H) { return H->d.inner_tol > 0 ? H->d.inner_t
 
 // Weighted inner products <w, v_i> (i < S.k) and <w, w>, read back to the host.
 int mdot(ohm_hier *H, const float *w, const VecSet &S, double *out) {
-    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s));
-    CK(cudaMemcpyAsync(H->hdots, H->kdots, (S.k + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s, nullptr,
+                                                         H->hnorm_dev ? H->hnorm_dev + 8 : nullptr));
+    if (!H->hnorm_dev)
+        CK(cudaMemcpyAsync(H->hdots, H->kdots, (S.k + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
     CK(cudaStreamSynchronize(H->s));
     memcpy(out, H->hdots, (S.k + 1) * sizeof(double));
     return OHM_OK;
@@ -2004,10 +2022,12 @@ static int op_composite(ohm_hier *h, const double *X, const double *Y, double a,
     if ((st = fill_ghosts_B(h, h->Bscr))) return st;
     if ((st = composite<double>(h, h->Bscr, Y, a, c, d, out, norms != nullptr))) return st;
     for (auto &g : h->amr) CK(launch_zero_covered(g.dev, out + (size_t)g.off * 3 * B3, h->s));
-    double nr[4];
     int ef = 0;
-    if ((st = read_norms(h, nr, &ef))) return st;
-    if (norms) memcpy(norms, nr, sizeof(nr));
+    if (norms) {
+        if ((st = read_norms(h, norms, &ef))) return st;
+    } else if ((st = read_err(h, &ef))) {
+        return st;
+    }
     return ef ? OHM_ERR_INVALID : OHM_OK;
 }
 
@@ -2036,9 +2056,8 @@ int ohm_op_vcycle(ohm_hier *h, const double *R_dev, double dt, double *e_dev) {
     if ((st = vcycle<double>(h, h->d.lambda * dt))) return st;
     CK(cudaMemcpyAsync(e_dev, h->amrbuf.e, (size_t)h->nblocks * 3 * B3 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     for (auto &g : h->amr) CK(launch_zero_covered(g.dev, e_dev + (size_t)g.off * 3 * B3, h->s));
-    double nr[4];
     int ef = 0;
-    if ((st = read_norms(h, nr, &ef))) return st;
+    if ((st = read_err(h, &ef))) return st;
     return ef ? OHM_ERR_INVALID : OHM_OK;
 }
 

@@ -162,7 +162,11 @@ cudaError_t launch_invdiag(const GridDev &g, const T *eta, const T *Geta, double
 
 // scratch: NORM_SCRATCH_BYTES, zero-filled once before first use (it resets itself)
 constexpr size_t NORM_SCRATCH_BYTES = 128 * 3 * sizeof(double) + 16;
-cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s);
+// host_out (optional): pinned host memory mapped into the device that also receives the three
+// sums and, as an int at host_out + 4, the word *err (the caller reads them after synchronising,
+// without a copy)
+cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s,
+                               double *host_out = nullptr, const int *err = nullptr);
 
 template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post,
@@ -199,7 +203,7 @@ struct VecSet {
 // part: scratch of nblk * (k + 1) doubles.  gate (device, may be null): when it holds 0 the
 // launches return at once and out is left as it was.
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
-                        cudaStream_t s, const int *gate = nullptr);
+                        cudaStream_t s, const int *gate = nullptr, double *host_out = nullptr);
 
 // dst = (src - sum c_i v_i) * scale
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s);

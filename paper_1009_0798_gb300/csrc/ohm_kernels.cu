@@ -1755,7 +1755,8 @@ cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s) {
 // (atomic ticket) folds the per-chunk results in chunk order.
 constexpr int NRED = 128;
 __global__ void __launch_bounds__(256) k_norm_reduce(const double *__restrict__ part, int n, double *__restrict__ chunk,
-                                                     unsigned int *__restrict__ ticket, double *__restrict__ out) {
+                                                     unsigned int *__restrict__ ticket, double *__restrict__ out,
+                                                     double *__restrict__ host_out, const int *__restrict__ err) {
     __shared__ double red[32];
     __shared__ bool last;
     const int per = (n + gridDim.x - 1) / gridDim.x;
@@ -1792,14 +1793,21 @@ __global__ void __launch_bounds__(256) k_norm_reduce(const double *__restrict__ 
         out[0] = sa;
         out[1] = sb;
         out[2] = sm;
+        if (host_out) {  // pinned host memory mapped into the device: no copy needed to read them
+            host_out[0] = sa;
+            host_out[1] = sb;
+            host_out[2] = sm;
+            reinterpret_cast<volatile int *>(host_out + 4)[0] = err ? *err : 0;
+        }
         *ticket = 0u;
     }
 }
 
 // scratch: NRED * 3 doubles followed by one unsigned ticket (zero on first use)
-cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s) {
+cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scratch, double *out, cudaStream_t s,
+                               double *host_out, const int *err) {
     int grid = nblocks < NRED * 64 ? (nblocks + 63) / 64 : NRED;
-    k_norm_reduce<<<grid, 256, 0, s>>>(partials, nblocks, scratch, (unsigned int *)(scratch + 3 * NRED), out);
+    k_norm_reduce<<<grid, 256, 0, s>>>(partials, nblocks, scratch, (unsigned int *)(scratch + 3 * NRED), out, host_out, err);
     return cudaGetLastError();
 }
 
@@ -1921,14 +1929,17 @@ __global__ void __launch_bounds__(256) k_mdot(const float *__restrict__ w, VecSe
 
 // column sums of part[nrow][ncol] in a fixed order (one thread block per column)
 __global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part, int nrow, int ncol, double *__restrict__ out,
-                                                const int *__restrict__ gate) {
+                                                const int *__restrict__ gate, double *__restrict__ host_out) {
     if (gate && !*gate) return;
     __shared__ double red[32];
     const int c = blockIdx.x;
     double a = 0.0;
     for (int b = threadIdx.x; b < nrow; b += blockDim.x) a += part[(size_t)b * ncol + c];
     double s = block_sum(a, red);
-    if (threadIdx.x == 0) out[c] = s;
+    if (threadIdx.x == 0) {
+        out[c] = s;
+        if (host_out) host_out[c] = s;  // mapped pinned host memory
+    }
 }
 
 // dst = (src - sum_i c_i v_i) * scale (dst may equal src); float4 over n/4 groups
@@ -1972,12 +1983,12 @@ __global__ void __launch_bounds__(256) k_maxpy(float4 *dst, const float4 *src, V
     }
 
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
-                        cudaStream_t s, const int *gate) {
+                        cudaStream_t s, const int *gate, double *host_out) {
     const int grid = (nblk + 7) / 8;
 #define OHM_MDOT(N) k_mdot<N><<<grid, 256, 0, s>>>(w, V, wb, nblk, part, gate)
     OHM_NV_SWITCH(V.k, OHM_MDOT)
 #undef OHM_MDOT
-    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out, gate);
+    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out, gate, host_out);
     return cudaGetLastError();
 }
 
