@@ -434,7 +434,8 @@ def run_ours(args):
                               "n_coarse": args.n_coarse, "krylov": KRYLOV if args.only.startswith("fgmres") else 0,
                               "inner_tol": args.inner_tol, "omega": args.omega if fg else 1.0,
                               "nu_coarse": nuc if fg else (0, 0),
-                              "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos]}),
+                              "ms_per_step": ms / args.steps, "cycles_per_step": [s["cycles"] for s in infos],
+                              "final_rel_l2": [s["rel_l2"] for s in infos]}),
                   flush=True)
         return
 

@@ -782,60 +782,138 @@ struct G12 {
     static constexpr int S = 12, RRS = 12, PS = S * RRS, CS = S * PS, OFF = 0;
     __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
 };
-// smoother division: the hardware reciprocal in float32 (a smoothing weight needs no
-// correctly rounded quotient), exact division in float64
-__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+// Constants of the point update (Eqs. 19-23): ncoef = -lamdt / (2 h^2) scales the flux
+// divergence of the scaled fluxes Phi = 2 h F; the relaxed diagonal is carried as
+// den_c = (1 + alpha_c) / omega = kb + ka (S_a + S_b), ka = lamdt / (2 h^2 omega), kb = 1 / omega,
+// where S_a = (eta_lo + eta) + (eta + eta_hi) is the sum of the cell's two face eta sums along
+// axis a (alpha_c = lamdt / h^2 times the sum, over the axes a != c, of the mean face eta on both
+// sides).  The host computes all three in float64 and rounds them once.
+template <typename T>
+struct RbK {
+    T ncoef, ka, kb;
+};
+template <typename T>
+RbK<T> rb_constants(double lamdt, double h, double omega) {
+    const double coef = lamdt / (2.0 * h * h);
+    return RbK<T>{(T)-coef, (T)(coef / omega), (T)(1.0 / omega)};
+}
+
+// Arithmetic of the point update, every operation rounded once (never contracted by the
+// compiler), in float32 or float64.
+__device__ __forceinline__ float v_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float v_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float v_mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double v_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double v_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double v_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double v_mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename V>
+__device__ __forceinline__ V v_splat(float x) {
+    return V(x);
+}
+template <typename V>
+__device__ __forceinline__ V v_zero() {
+    return v_splat<V>(0.0f);
+}
+
+// The relaxed update ev + res / den: float32 through the hardware's approximate reciprocal
+// (rcp.approx, relative error below 2^-23; a smoothing weight needs no correctly rounded
+// quotient) and one FMA, float64 with an exact division.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rb_relax(float ev, float res, float den) { return v_mad(res, rcp_approx(den), ev); }
+__device__ __forceinline__ double rb_relax(double ev, double res, double den) { return v_add(ev, __ddiv_rn(res, den)); }
 
 // The point update of one colour pass (Eq. 19 with R from Eq. 20 and alpha from Eqs. 21-23),
 // written against an accessor that returns component C of the field, or eta, at a compile-time
-// offset (DX, DY, DZ) from the updated cell.  Every sweep kernel goes through this one function,
-// whatever its staging: the rounding of each update is the same in all of them.
-template <typename T, int AX, bool LO, class A>
-__device__ __forceinline__ void face_acc(const A &a, T &phi1, T &phi2) {
-    // the face between the cells P (low side) and Q = P + e_AX: P = -e_AX for the low face of
-    // the updated cell, P = 0 for its high face; flux components along B1 < B2, the other axes
-    constexpr int PX = (LO && AX == 0) ? -1 : 0, PY = (LO && AX == 1) ? -1 : 0, PZ = (LO && AX == 2) ? -1 : 0;
-    constexpr int QX = PX + (AX == 0), QY = PY + (AX == 1), QZ = PZ + (AX == 2);
-    constexpr int B1 = AX == 0 ? 1 : 0, B2 = AX == 2 ? 1 : 2;
-    constexpr int UX = B1 == 0, UY = B1 == 1, UZ = B1 == 2;  // unit step along B1
-    constexpr int VX = B2 == 0, VY = B2 == 1, VZ = B2 == 2;  // unit step along B2
-    const T es = a.template E<PX, PY, PZ>() + a.template E<QX, QY, QZ>();
-    T n1 = a.template B<B1, QX, QY, QZ>() - a.template B<B1, PX, PY, PZ>();
-    T t1 = (a.template B<AX, QX + UX, QY + UY, QZ + UZ>() + a.template B<AX, PX + UX, PY + UY, PZ + UZ>()) -
-           (a.template B<AX, QX - UX, QY - UY, QZ - UZ>() + a.template B<AX, PX - UX, PY - UY, PZ - UZ>());
-    phi1 = es * (quarter(t1) - n1);
-    T n2 = a.template B<B2, QX, QY, QZ>() - a.template B<B2, PX, PY, PZ>();
-    T t2 = (a.template B<AX, QX + VX, QY + VY, QZ + VZ>() + a.template B<AX, PX + VX, PY + VY, PZ + VZ>()) -
-           (a.template B<AX, QX - VX, QY - VY, QZ - VZ>() + a.template B<AX, PX - VX, PY - VY, PZ - VZ>());
-    phi2 = es * (quarter(t2) - n2);
+// offset (DX, DY, DZ) from the updated cell.  Every fused sweep kernel goes through these
+// functions, whatever its staging: the rounding of each update is the same in all of them.
+//
+// face_pair: the divergence contribution of flux component C through the cell's two faces along
+// axis AX, es_hi Q_hi - es_lo Q_lo with Phi = es Q, Q = T / 4 - N (Eqs. 9-10).  The tangential
+// sums of the two faces (Eq. 10) share their middle difference, so they are formed as
+//   T_hi = D(+AX) + D(0),  T_lo = D(0) + D(-AX),  D(s) = B_AX(s + e_C) - B_AX(s - e_C),
+// the same four values each, regrouped (4 additions for both faces instead of 6).  The low face
+// carries -Q (N - T/4, the same bits negated), so no operation needs a negated operand.
+template <typename V, int AX, int C, class A>
+__device__ __forceinline__ V face_pair(const A &a, V es_lo, V es_hi) {
+    constexpr int AXX = AX == 0, AXY = AX == 1, AXZ = AX == 2;
+    constexpr int CX = C == 0, CY = C == 1, CZ = C == 2;
+    const V d0 = v_sub(a.template B<AX, CX, CY, CZ>(), a.template B<AX, -CX, -CY, -CZ>());
+    const V dp = v_sub(a.template B<AX, AXX + CX, AXY + CY, AXZ + CZ>(), a.template B<AX, AXX - CX, AXY - CY, AXZ - CZ>());
+    const V dm = v_sub(a.template B<AX, CX - AXX, CY - AXY, CZ - AXZ>(), a.template B<AX, -CX - AXX, -CY - AXY, -CZ - AXZ>());
+    const V c0 = a.template B<C, 0, 0, 0>();
+    const V q_hi = v_mad(v_add(dp, d0), v_splat<V>(0.25f), v_sub(c0, a.template B<C, AXX, AXY, AXZ>()));
+    const V mq_lo = v_mad(v_add(d0, dm), v_splat<V>(-0.25f), v_sub(c0, a.template B<C, -AXX, -AXY, -AXZ>()));
+    return v_mad(es_hi, q_hi, v_mul(es_lo, mq_lo));
 }
 
-template <typename T, class A>
-__device__ __forceinline__ T rb_one(const A &a, T ev, T rr, T dv, T al, T coef, T omega) {
-    (void)a;
-    T res = rr - ev - coef * dv;
-    return ev + fast_div(omega * res, T(1) + al);
+// face sums of eta (eta_lo + eta on the low face, eta + eta_hi on the high face) and den_c
+template <typename V, class A>
+__device__ __forceinline__ void rb_faces_den(const A &a, const RbK<V> &K, V es[6], V den[3]) {
+    const V e0 = a.template E<0, 0, 0>();
+    es[0] = v_add(a.template E<-1, 0, 0>(), e0);
+    es[1] = v_add(e0, a.template E<1, 0, 0>());
+    es[2] = v_add(a.template E<0, -1, 0>(), e0);
+    es[3] = v_add(e0, a.template E<0, 1, 0>());
+    es[4] = v_add(a.template E<0, 0, -1>(), e0);
+    es[5] = v_add(e0, a.template E<0, 0, 1>());
+    const V sx = v_add(es[0], es[1]), sy = v_add(es[2], es[3]), sz = v_add(es[4], es[5]);
+    den[0] = v_mad(K.ka, v_add(sy, sz), K.kb);
+    den[1] = v_mad(K.ka, v_add(sz, sx), K.kb);
+    den[2] = v_mad(K.ka, v_add(sx, sy), K.kb);
 }
 
-template <typename T, class A>
-__device__ __forceinline__ void rb_update_acc(const A &a, T coef, T lh2, const T rr[3], T out[3], T omega) {
-    T xl1, xl2, xh1, xh2, yl1, yl2, yh1, yh2, zl1, zl2, zh1, zh2;
-    face_acc<T, 0, true>(a, xl1, xl2);
-    face_acc<T, 0, false>(a, xh1, xh2);
-    face_acc<T, 1, true>(a, yl1, yl2);
-    face_acc<T, 1, false>(a, yh1, yh2);
-    face_acc<T, 2, true>(a, zl1, zl2);
-    face_acc<T, 2, false>(a, zh1, zh2);
-    const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
-    const T e0 = a.template E<0, 0, 0>();
-    const T sx = e0 + T(0.5) * (a.template E<1, 0, 0>() + a.template E<-1, 0, 0>());
-    const T sy = e0 + T(0.5) * (a.template E<0, 1, 0>() + a.template E<0, -1, 0>());
-    const T sz = e0 + T(0.5) * (a.template E<0, 0, 1>() + a.template E<0, 0, -1>());
-    const T al[3] = {lh2 * (sy + sz), lh2 * (sz + sx), lh2 * (sx + sy)};
-    out[0] = rb_one<T>(a, a.template B<0, 0, 0, 0>(), rr[0], dv[0], al[0], coef, omega);
-    out[1] = rb_one<T>(a, a.template B<1, 0, 0, 0>(), rr[1], dv[1], al[1], coef, omega);
-    out[2] = rb_one<T>(a, a.template B<2, 0, 0, 0>(), rr[2], dv[2], al[2], coef, omega);
+template <typename V, class A>
+__device__ __forceinline__ void rb_update_acc(const A &a, const RbK<V> &K, const V rr[3], V out[3]) {
+    V es[6], den[3];
+    rb_faces_den<V>(a, K, es, den);
+    const V dv[3] = {v_add(face_pair<V, 1, 0>(a, es[2], es[3]), face_pair<V, 2, 0>(a, es[4], es[5])),
+                     v_add(face_pair<V, 0, 1>(a, es[0], es[1]), face_pair<V, 2, 1>(a, es[4], es[5])),
+                     v_add(face_pair<V, 0, 2>(a, es[0], es[1]), face_pair<V, 1, 2>(a, es[2], es[3]))};
+    const V ev[3] = {a.template B<0, 0, 0, 0>(), a.template B<1, 0, 0, 0>(), a.template B<2, 0, 0, 0>()};
+#pragma unroll
+    for (int c = 0; c < 3; c++) out[c] = rb_relax(ev[c], v_mad(K.ncoef, dv[c], v_sub(rr[c], ev[c])), den[c]);
+}
+
+// The first sweep from e = 0, where the red colour pass reduces to e = r / den (every flux of the
+// pre-pass state vanishes) and the black pass sees red values at the face neighbours of a black
+// cell and zeros at its edge neighbours and at itself.  The two updates below are
+// rb_update_acc with those zeros folded in: every dropped term is an exact +-0 there, so the
+// results are the same bits (up to the sign of a zero).  The tangential difference of a black
+// cell is the same for its two faces along an axis (D(+-AX) = 0), so a black update reads 31
+// tile values instead of about 46.
+template <typename V, class A>
+__device__ __forceinline__ void red_from_zero_acc(const A &a, const RbK<V> &K, const V rr[3], V out[3]) {
+    V es[6], den[3];
+    rb_faces_den<V>(a, K, es, den);
+#pragma unroll
+    for (int c = 0; c < 3; c++) out[c] = rb_relax(v_zero<V>(), rr[c], den[c]);
+}
+
+template <typename V, int AX, int C, class A>
+__device__ __forceinline__ V face_pair_zero(const A &a, V es_lo, V es_hi) {
+    constexpr int AXX = AX == 0, AXY = AX == 1, AXZ = AX == 2;
+    constexpr int CX = C == 0, CY = C == 1, CZ = C == 2;
+    const V d0 = v_sub(a.template B<AX, CX, CY, CZ>(), a.template B<AX, -CX, -CY, -CZ>());
+    const V q_hi = v_sub(v_mul(d0, v_splat<V>(0.25f)), a.template B<C, AXX, AXY, AXZ>());
+    const V mq_lo = v_sub(v_mul(d0, v_splat<V>(-0.25f)), a.template B<C, -AXX, -AXY, -AXZ>());
+    return v_mad(es_hi, q_hi, v_mul(es_lo, mq_lo));
+}
+
+template <typename V, class A>
+__device__ __forceinline__ void black_after_zero_acc(const A &a, const RbK<V> &K, const V rr[3], V out[3]) {
+    V es[6], den[3];
+    rb_faces_den<V>(a, K, es, den);
+    const V dv[3] = {v_add(face_pair_zero<V, 1, 0>(a, es[2], es[3]), face_pair_zero<V, 2, 0>(a, es[4], es[5])),
+                     v_add(face_pair_zero<V, 0, 1>(a, es[0], es[1]), face_pair_zero<V, 2, 1>(a, es[4], es[5])),
+                     v_add(face_pair_zero<V, 0, 2>(a, es[0], es[1]), face_pair_zero<V, 1, 2>(a, es[2], es[3]))};
+#pragma unroll
+    for (int c = 0; c < 3; c++) out[c] = rb_relax(v_zero<V>(), v_mad(K.ncoef, dv[c], rr[c]), den[c]);
 }
 
 // accessor of a staged tile (geometry G: rows RRS apart, planes PS, components CS)
@@ -854,14 +932,14 @@ struct TileAcc {
 };
 
 template <typename T, typename G = G12<T>>
-__device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef, T lh2,
-                                          const T rr[3], T out[3], T omega) {
-    rb_update_acc<T>(TileAcc<T, G>{tB, tE, p}, coef, lh2, rr, out, omega);
+__device__ __forceinline__ void rb_update(const T *__restrict__ tB, const T *__restrict__ tE, int p, const RbK<T> &K,
+                                          const T rr[3], T out[3]) {
+    rb_update_acc<T>(TileAcc<T, G>{tB, tE, p}, K, rr, out);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restrict__ e_in, T *__restrict__ e_out,
-                                                   const T *__restrict__ r, const T *__restrict__ eta, T coef, T lh2) {
+                                                   const T *__restrict__ r, const T *__restrict__ eta, RbK<T> K) {
     using G = G12<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tB = reinterpret_cast<T *>(smem_raw);  // [3][12 planes][12 rows][RRS]
@@ -917,7 +995,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
         const int off = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8 + (li - 8 * di);
         const T rr[3] = {r[(size_t)src * 3 * B3 + off], r[(size_t)src * 3 * B3 + B3 + off], r[(size_t)src * 3 * B3 + 2 * B3 + off]};
         np[s4] = G::at(li + 2, lj + 2, lk + 2);
-        rb_update(tB, tE, np[s4], coef, lh2, rr, nv[s4], (T)g.omega);
+        rb_update(tB, tE, np[s4], K, rr, nv[s4]);
     }
     __syncthreads();
 #pragma unroll
@@ -933,7 +1011,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb(GridDev g, const T *__restric
     const T rr[3] = {r[(size_t)b * 3 * B3 + cb], r[(size_t)b * 3 * B3 + B3 + cb], r[(size_t)b * 3 * B3 + 2 * B3 + cb]};
     T out[3];
     const int pb = G::at(ib + 2, j + 2, k + 2), pr = G::at(ir + 2, j + 2, k + 2);
-    rb_update(tB, tE, pb, coef, lh2, rr, out, (T)g.omega);
+    rb_update(tB, tE, pb, K, rr, out);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         e_out[((size_t)b * 3 + c) * B3 + cb] = out[c];
@@ -949,69 +1027,13 @@ cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T 
     // set once per process (thread-safe static initialisation)
     static const bool attr = (cudaFuncSetAttribute(k_smooth_rb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), true);
     (void)attr;
-    k_smooth_rb<T><<<g.nblk, 256, sm, s>>>(g, e_in, e_out, r, eta, (T)(lamdt / (2.0 * g.h * g.h)),
-                                          (T)(lamdt / (g.h * g.h)));
+    k_smooth_rb<T><<<g.nblk, 256, sm, s>>>(g, e_in, e_out, r, eta, rb_constants<T>(lamdt, g.h, g.omega));
     return cudaGetLastError();
 }
 template cudaError_t launch_smooth_rb<float>(const GridDev &, const float *, float *, const float *, const float *, double,
                                              cudaStream_t);
 template cudaError_t launch_smooth_rb<double>(const GridDev &, const double *, double *, const double *, const double *,
                                               double, cudaStream_t);
-
-// The first sweep from e = 0, where the red colour pass reduces to e = omega r / (1 + alpha)
-// (every flux of the pre-pass state vanishes) and the black pass sees red values at the face
-// neighbours of a black cell and zeros at its edge neighbours and at itself.  The two updates
-// below are rb_update with those zeros folded in: every dropped term is an exact +-0 in
-// rb_update, so the results are the same bits (up to the sign of a zero).  The tangential
-// difference of a black cell is the same for its two faces along an axis, so a black update
-// reads 31 tile values instead of about 52.
-template <typename T, typename G>
-__device__ __forceinline__ void alpha_of(const T *__restrict__ tE, int p, T lh2, T al[3]) {
-    const T e0 = tE[p];
-    const T sx = e0 + T(0.5) * (tE[p + 1] + tE[p - 1]);
-    const T sy = e0 + T(0.5) * (tE[p + G::RRS] + tE[p - G::RRS]);
-    const T sz = e0 + T(0.5) * (tE[p + G::PS] + tE[p - G::PS]);
-    al[0] = lh2 * (sy + sz);
-    al[1] = lh2 * (sz + sx);
-    al[2] = lh2 * (sx + sy);
-}
-
-template <typename T, typename G>
-__device__ __forceinline__ void red_from_zero(const T *__restrict__ tE, int p, T lh2, const T rr[3], T out[3],
-                                              T omega) {
-    T al[3];
-    alpha_of<T, G>(tE, p, lh2, al);
-#pragma unroll
-    for (int c = 0; c < 3; c++) out[c] = fast_div(omega * rr[c], T(1) + al[c]);
-}
-
-template <typename T, typename G>
-__device__ __forceinline__ void black_after_zero(const T *__restrict__ tB, const T *__restrict__ tE, int p, T coef,
-                                                 T lh2, const T rr[3], T out[3], T omega) {
-    const T *Bx = tB, *By = tB + G::CS, *Bz = tB + 2 * G::CS;
-    const int sx = 1, sy = G::RRS, sz = G::PS;
-    const T e0 = tE[p];
-    // x faces: flux components y (tangential difference along y) and z
-    const T txy = Bx[p + sy] - Bx[p - sy], txz = Bx[p + sz] - Bx[p - sz];
-    const T exl = tE[p - sx] + e0, exh = e0 + tE[p + sx];
-    const T xl1 = exl * (quarter(txy) - (-By[p - sx])), xl2 = exl * (quarter(txz) - (-Bz[p - sx]));
-    const T xh1 = exh * (quarter(txy) - By[p + sx]), xh2 = exh * (quarter(txz) - Bz[p + sx]);
-    // y faces: components x and z
-    const T tyx = By[p + sx] - By[p - sx], tyz = By[p + sz] - By[p - sz];
-    const T eyl = tE[p - sy] + e0, eyh = e0 + tE[p + sy];
-    const T yl1 = eyl * (quarter(tyx) - (-Bx[p - sy])), yl2 = eyl * (quarter(tyz) - (-Bz[p - sy]));
-    const T yh1 = eyh * (quarter(tyx) - Bx[p + sy]), yh2 = eyh * (quarter(tyz) - Bz[p + sy]);
-    // z faces: components x and y
-    const T tzx = Bz[p + sx] - Bz[p - sx], tzy = Bz[p + sy] - Bz[p - sy];
-    const T ezl = tE[p - sz] + e0, ezh = e0 + tE[p + sz];
-    const T zl1 = ezl * (quarter(tzx) - (-Bx[p - sz])), zl2 = ezl * (quarter(tzy) - (-By[p - sz]));
-    const T zh1 = ezh * (quarter(tzx) - Bx[p + sz]), zh2 = ezh * (quarter(tzy) - By[p + sz]);
-    const T dv[3] = {(yh1 - yl1) + (zh1 - zl1), (xh1 - xl1) + (zh2 - zl2), (xh2 - xl2) + (yh2 - yl2)};
-    T al[3];
-    alpha_of<T, G>(tE, p, lh2, al);
-#pragma unroll
-    for (int c = 0; c < 3; c++) out[c] = fast_div(omega * (rr[c] - coef * dv[c]), T(1) + al[c]);
-}
 
 // ------------------------------------------------------------------ fused sweep on brick pairs
 // The fused sweep above for two x-adjacent blocks A = 2q and B = 2q + 1 per thread block (512
@@ -1075,8 +1097,8 @@ __device__ const Ring2 g_ring2 = make_ring2();
 // only eta is staged, the red pass is pointwise and the black pass reads only red values.
 template <bool ZERO>
 __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *__restrict__ e_in, float *__restrict__ e_out,
-                                                    const float *__restrict__ r, const float *__restrict__ eta, float coef,
-                                                    float lh2) {
+                                                    const float *__restrict__ r, const float *__restrict__ eta,
+                                                    RbK<float> K) {
     using G = G20;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tB = reinterpret_cast<float *>(smem_raw);  // [3][12 planes][12 rows][RRS]
@@ -1144,13 +1166,12 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     // red: the brick's 512 (one per thread), then the 384 of its ring, from the pre-sweep state
     float nv0[3], nv1[3];
     const int p0 = G::at(ir + 2, j + 2, k + 2);
-    const float om = (float)g.omega;
     if constexpr (ZERO) {  // nothing of e is read: no barrier before the red values are stored
-        red_from_zero<float, G>(tE, p0, lh2, rr0, nv0, om);
-        if (p1 >= 0) red_from_zero<float, G>(tE, p1, lh2, rr1, nv1, om);
+        red_from_zero_acc<float>(TileAcc<float, G>{tB, tE, p0}, K, rr0, nv0);
+        if (p1 >= 0) red_from_zero_acc<float>(TileAcc<float, G>{tB, tE, p1}, K, rr1, nv1);
     } else {
-        rb_update<float, G>(tB, tE, p0, coef, lh2, rr0, nv0, om);
-        if (p1 >= 0) rb_update<float, G>(tB, tE, p1, coef, lh2, rr1, nv1, om);
+        rb_update<float, G>(tB, tE, p0, K, rr0, nv0);
+        if (p1 >= 0) rb_update<float, G>(tB, tE, p1, K, rr1, nv1);
         __syncthreads();
     }
 #pragma unroll
@@ -1162,9 +1183,9 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     // black cells of the brick from the post-red state, then both blocks are written out
     float out[3];
     if constexpr (ZERO)  // black cells read only red neighbours (their black neighbours are 0)
-        black_after_zero<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out, om);
+        black_after_zero_acc<float>(TileAcc<float, G>{tB, tE, G::at(ib + 2, j + 2, k + 2)}, K, rrb, out);
     else
-        rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), coef, lh2, rrb, out, om);
+        rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), K, rrb, out);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         e_out[((size_t)own * 3 + c) * B3 + cb] = out[c];
@@ -1180,11 +1201,11 @@ cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out,
                               cudaFuncSetAttribute(k_smooth_rb2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                               true);
     (void)attr;
-    const float coef = (float)(lamdt / (2.0 * g.h * g.h)), lh2 = (float)(lamdt / (g.h * g.h));
+    const RbK<float> K = rb_constants<float>(lamdt, g.h, g.omega);
     if (e_in)
-        k_smooth_rb2<false><<<g.nblk / 2, 512, sm, s>>>(g, e_in, e_out, r, eta, coef, lh2);
+        k_smooth_rb2<false><<<g.nblk / 2, 512, sm, s>>>(g, e_in, e_out, r, eta, K);
     else  // from e = 0
-        k_smooth_rb2<true><<<g.nblk / 2, 512, sm, s>>>(g, nullptr, e_out, r, eta, coef, lh2);
+        k_smooth_rb2<true><<<g.nblk / 2, 512, sm, s>>>(g, nullptr, e_out, r, eta, K);
     return cudaGetLastError();
 }
 
