@@ -873,6 +873,19 @@ int small_vcycle(ohm_hier *H, double lamdt, int npre, int npost, int ncoarse) {
     return OHM_OK;
 }
 
+// Residual t = r - L e of a base-grid level and its restriction into the next blocked grid
+// (coarse) or the first lexicographic grid (lex, dims ld); t_out receives t when not null.
+// float32 brick grids whose children sit in Morton octets take the block-pair kernel.
+template <typename T>
+cudaError_t resid_restrict_base(ohm_hier *H, const HGrid &g, const T *e, const T *r, const T *eta, double lamdt,
+                                T *t_out, T *coarse, T *lex, const int *ld) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (g.brick && !lex && (!coarse || g.octet))
+            return launch_pair_op(gdev(H, g), e, r, eta, -lamdt / (2.0 * g.h * g.h), false, t_out, coarse, H->s);
+    }
+    return launch_resid_restrict<T>(gdev(H, g), e, r, eta, nullptr, nullptr, lamdt, t_out, coarse, lex, ld, H->s);
+}
+
 template <typename T>
 int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const ohm_hier_desc &d = H->d;
@@ -885,8 +898,9 @@ int base_vcycle(ohm_hier *H, int m, double lamdt) {
     const bool next_blocked = m < (int)H->mg.size();
     if (next_blocked) {
         GridRef C = base_ref<T>(H, m + 1);
-        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(), launch_resid_restrict<T>(gdev(H, *G.g), (const T *)G.e, (const T *)G.r, (const T *)G.eta, nullptr, nullptr, lamdt,
-                                    nullptr, (T *)C.r, nullptr, nullptr, H->s));
+        LAUNCH(H, OHM_K_RESID_RESTRICT, G.g->n(),
+               resid_restrict_base<T>(H, *G.g, (const T *)G.e, (const T *)G.r, (const T *)G.eta, lamdt, nullptr, (T *)C.r,
+                                      nullptr, nullptr));
         if ((st = base_vcycle<T>(H, m + 1, lamdt))) return st;
         if (G.g->octet)
             LAUNCH(H, OHM_K_PROLONG, G.g->n(), launch_prolong_add8<T>(gdev(H, *C.g), (const T *)C.e, (T *)G.e, H->s));
@@ -965,6 +979,17 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
                                         outS ? reinterpret_cast<dfloat *>(outS) + o3 : nullptr, c2)));
             continue;
           }
+        }
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TO, float>::value) {
+            // the float32 operator (a = 1, d = 0, no Y) or residual (a = -1, d = 1) of a single-level
+            // brick grid without norms: block-pair kernel
+            const bool apply = !Y && a == 1.0 && dcoef == 0.0, resid = Y && a == -1.0 && dcoef == 1.0;
+            if (H->nlev == 1 && g.brick && !norms && !out2 && !outS && (apply || resid)) {
+                LAUNCH(H, OHM_K_COMPOSITE, g.n(),
+                       launch_pair_op(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3,
+                                      c / (2.0 * g.h * g.h), apply, out + o3, nullptr, H->s));
+                continue;
+            }
         }
         {
             LAUNCH(H, OHM_K_COMPOSITE, g.n(),
@@ -2217,9 +2242,9 @@ int ohm_op_grid_resid_restrict_f32(ohm_hier *h, int m, const float *e_dev, const
     int st;
     if ((st = grid_setup32(h, m, eta_dev, dt, G))) return st;
     const bool next_blocked = m < (int)h->mg.size();
-    CK(launch_resid_restrict<float>(gdev(h, *G.g), e_dev, r_dev, (const float *)G.eta, nullptr, nullptr, h->d.lambda * dt,
-                                    t_dev, next_blocked ? coarse_dev : nullptr, next_blocked ? nullptr : coarse_dev,
-                                    h->small[0].data(), h->s));
+    CK(resid_restrict_base<float>(h, *G.g, e_dev, r_dev, (const float *)G.eta, h->d.lambda * dt, t_dev,
+                                  next_blocked ? coarse_dev : nullptr, next_blocked ? nullptr : coarse_dev,
+                                  h->small[0].data()));
     CK(cudaStreamSynchronize(h->s));
     return OHM_OK;
 }

@@ -106,6 +106,12 @@ cudaError_t launch_smooth_rb(const GridDev &g, const T *e_in, T *e_out, const T 
 // sweep starts from e = 0 (nothing is read for e).
 cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out, const float *r, const float *eta,
                               double lamdt, cudaStream_t s);
+// float32 operator or residual on block pairs of a brick grid (every block pair x-adjacent, all
+// neighbours present): apply: out = X + kc divF(X); else out = (Y - X) + kc divF(X) (out may be
+// null) with, when coarse is not null, its octet means written into the coarser grid (children
+// in Morton octets: block b's parent b / 8, octant b % 8)
+cudaError_t launch_pair_op(const GridDev &g, const float *X, const float *Y, const float *eta, double kc, bool apply,
+                           float *out, float *coarse, cudaStream_t s);
 
 // t = r - (e + lamdt divF(e)); restricted (mean of 8) into the coarser grid: blocked
 // (coarse != nullptr, by parent/octant) or lexicographic (lex != nullptr, dims ldims).

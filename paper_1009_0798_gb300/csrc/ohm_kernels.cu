@@ -852,9 +852,9 @@ __device__ __forceinline__ V face_pair(const A &a, V es_lo, V es_hi) {
     return v_mad(es_hi, q_hi, v_mul(es_lo, mq_lo));
 }
 
-// face sums of eta (eta_lo + eta on the low face, eta + eta_hi on the high face) and den_c
+// face sums of eta: eta_lo + eta on the low face, eta + eta_hi on the high face, along x, y, z
 template <typename V, class A>
-__device__ __forceinline__ void rb_faces_den(const A &a, const RbK<V> &K, V es[6], V den[3]) {
+__device__ __forceinline__ void face_sums(const A &a, V es[6]) {
     const V e0 = a.template E<0, 0, 0>();
     es[0] = v_add(a.template E<-1, 0, 0>(), e0);
     es[1] = v_add(e0, a.template E<1, 0, 0>());
@@ -862,6 +862,20 @@ __device__ __forceinline__ void rb_faces_den(const A &a, const RbK<V> &K, V es[6
     es[3] = v_add(e0, a.template E<0, 1, 0>());
     es[4] = v_add(a.template E<0, 0, -1>(), e0);
     es[5] = v_add(e0, a.template E<0, 0, 1>());
+}
+
+// the flux divergence of the cell (Eq. 8) from its face sums
+template <typename V, class A>
+__device__ __forceinline__ void cell_divergence(const A &a, const V es[6], V dv[3]) {
+    dv[0] = v_add(face_pair<V, 1, 0>(a, es[2], es[3]), face_pair<V, 2, 0>(a, es[4], es[5]));
+    dv[1] = v_add(face_pair<V, 0, 1>(a, es[0], es[1]), face_pair<V, 2, 1>(a, es[4], es[5]));
+    dv[2] = v_add(face_pair<V, 0, 2>(a, es[0], es[1]), face_pair<V, 1, 2>(a, es[2], es[3]));
+}
+
+// face sums and den_c
+template <typename V, class A>
+__device__ __forceinline__ void rb_faces_den(const A &a, const RbK<V> &K, V es[6], V den[3]) {
+    face_sums<V>(a, es);
     const V sx = v_add(es[0], es[1]), sy = v_add(es[2], es[3]), sz = v_add(es[4], es[5]);
     den[0] = v_mad(K.ka, v_add(sy, sz), K.kb);
     den[1] = v_mad(K.ka, v_add(sz, sx), K.kb);
@@ -870,11 +884,9 @@ __device__ __forceinline__ void rb_faces_den(const A &a, const RbK<V> &K, V es[6
 
 template <typename V, class A>
 __device__ __forceinline__ void rb_update_acc(const A &a, const RbK<V> &K, const V rr[3], V out[3]) {
-    V es[6], den[3];
+    V es[6], den[3], dv[3];
     rb_faces_den<V>(a, K, es, den);
-    const V dv[3] = {v_add(face_pair<V, 1, 0>(a, es[2], es[3]), face_pair<V, 2, 0>(a, es[4], es[5])),
-                     v_add(face_pair<V, 0, 1>(a, es[0], es[1]), face_pair<V, 2, 1>(a, es[4], es[5])),
-                     v_add(face_pair<V, 0, 2>(a, es[0], es[1]), face_pair<V, 1, 2>(a, es[2], es[3]))};
+    cell_divergence<V>(a, es, dv);
     const V ev[3] = {a.template B<0, 0, 0, 0>(), a.template B<1, 0, 0, 0>(), a.template B<2, 0, 0, 0>()};
 #pragma unroll
     for (int c = 0; c < 3; c++) out[c] = rb_relax(ev[c], v_mad(K.ncoef, dv[c], v_sub(rr[c], ev[c])), den[c]);
@@ -1206,6 +1218,116 @@ cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out,
         k_smooth_rb2<false><<<g.nblk / 2, 512, sm, s>>>(g, e_in, e_out, r, eta, K);
     else  // from e = 0
         k_smooth_rb2<true><<<g.nblk / 2, 512, sm, s>>>(g, nullptr, e_out, r, eta, K);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ residual on brick pairs
+// The float32 operator and residual of the inner solve on the same x-adjacent block pairs as
+// the pair sweep (512 threads, one thread block per pair), with the flux divergence formed per
+// cell by the sweep's face_pair (Eqs. 8-10) instead of through face-flux arrays: no flux
+// arrays, one barrier, a 18 x 10 x 10 tile (one-cell halo; rows staged as 16-byte words with
+// the block interiors 16-byte aligned at OFF = 3).  Modes:
+//   APPLY:    out = X + kc divF(X)                    (L X, the Krylov operator)
+//   residual: out = (Y - X) + kc divF(X), kc = -lamdt / (2 h^2)   (Eq. 20)
+// and RESTRICT: the residual's octet means written into the coarser grid (Sec. 2.2), for grids
+// whose children sit in Morton octets (block b's parent is b / 8, its octant b % 8).  A warp
+// takes 8 cells of a row x 2 rows x 2 planes of one block: every 2^3 octet is in one warp (sums
+// by three shuffles), and with rows 24 and planes 240 floats apart (240 = 16 mod 32) its
+// shared-memory reads at one offset fall on 32 distinct banks.
+struct G18 {
+    static constexpr int S = 10, RRS = 24, PS = S * RRS, CS = S * PS, OFF = 3;
+    __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
+};
+
+template <bool APPLY, bool RESTRICT>
+__global__ void __launch_bounds__(512, 4) k_pair_op(GridDev g, const float *__restrict__ X, const float *__restrict__ Y,
+                                                 const float *__restrict__ eta, float kc, float *__restrict__ out,
+                                                 float *__restrict__ coarse) {
+    using G = G18;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tB = reinterpret_cast<float *>(smem_raw);  // [3][10 planes][10 rows][RRS]
+    float *tE = tB + 3 * G::CS;
+    __shared__ int snb[36];
+    const int A = 2 * blockIdx.x;
+    if (skip_block(g, A)) return;
+    if (threadIdx.x < 36) {
+        const int bx = threadIdx.x % 4 - 1, dj = (threadIdx.x / 4) % 3 - 1, dk = threadIdx.x / 12 - 1;
+        const int base = bx <= 1 ? A : A + 1, dx = bx <= 1 ? bx : 1;
+        snb[threadIdx.x] = __ldg(g.nbr + base * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (dx + 1));
+    }
+    __syncthreads();
+    // one task per (field component, tile row): 1 + 8 + 8 + 1 values, the interiors as 16-byte words
+    if (threadIdx.x < 400) {
+        const int c = threadIdx.x / 100, u = threadIdx.x - c * 100;
+        const int tk = u / 10, tj = u - 10 * tk;
+        const int lj = tj - 1, lk = tk - 1;
+        const int dj = lj < 0 ? -1 : (lj > 7 ? 1 : 0), dk = lk < 0 ? -1 : (lk > 7 ? 1 : 0);
+        const int rowoff = ((lk - 8 * dk) * 8 + (lj - 8 * dj)) * 8;
+        const int *nb = snb + (dk + 1) * 12 + (dj + 1) * 4;
+        const float *F = c < 3 ? X : eta;
+        const int nc = c < 3 ? 3 : 1, cc = c < 3 ? c : 0;
+        float *row = (c < 3 ? tB + c * G::CS : tE) + tk * G::PS + tj * G::RRS + G::OFF;
+        const float lo = __ldg(F + ((size_t)nb[0] * nc + cc) * B3 + rowoff + 7);
+        const float4 *pa = reinterpret_cast<const float4 *>(F + ((size_t)nb[1] * nc + cc) * B3 + rowoff);
+        const float4 *pb = reinterpret_cast<const float4 *>(F + ((size_t)nb[2] * nc + cc) * B3 + rowoff);
+        const float hi = __ldg(F + ((size_t)nb[3] * nc + cc) * B3 + rowoff);
+        const float4 a0 = __ldg(pa), a1 = __ldg(pa + 1), b0 = __ldg(pb), b1 = __ldg(pb + 1);
+        row[0] = lo;
+        float4 *r4 = reinterpret_cast<float4 *>(row + 1);
+        r4[0] = a0;
+        r4[1] = a1;
+        r4[2] = b0;
+        r4[3] = b1;
+        row[17] = hi;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = lane & 7, y = 2 * (w & 3) + ((lane >> 3) & 1), z = 2 * ((w >> 2) & 3) + (lane >> 4);
+    const int cell = (z * 8 + y) * 8 + x;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {  // the same cell of block A, then of block B
+        const int b = A + h;
+        const TileAcc<float, G> acc{tB, tE, G::at(1 + 8 * h + x, 1 + y, 1 + z)};
+        float es[6], dv[3];
+        face_sums<float>(acc, es);
+        cell_divergence<float>(acc, es, dv);
+        const float ev[3] = {acc.template B<0, 0, 0, 0>(), acc.template B<1, 0, 0, 0>(), acc.template B<2, 0, 0, 0>()};
+        float o[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const size_t id = ((size_t)b * 3 + c) * B3 + cell;
+            o[c] = v_mad(kc, dv[c], APPLY ? ev[c] : v_sub(Y[id], ev[c]));
+            if (out) out[id] = o[c];
+        }
+        if constexpr (RESTRICT) {
+            const int oct = b & 7, pb = b >> 3;
+            const int cx = 4 * (oct & 1) + (x >> 1), cy = 4 * ((oct >> 1) & 1) + (y >> 1), cz = 4 * (oct >> 2) + (z >> 1);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float sum = v_add(o[c], __shfl_xor_sync(0xffffffffu, o[c], 1));
+                sum = v_add(sum, __shfl_xor_sync(0xffffffffu, sum, 8));
+                sum = v_add(sum, __shfl_xor_sync(0xffffffffu, sum, 16));
+                if ((lane & 0x19) == 0) coarse[((size_t)pb * 3 + c) * B3 + (cz * 8 + cy) * 8 + cx] = v_mul(sum, 0.125f);
+            }
+        }
+    }
+}
+
+cudaError_t launch_pair_op(const GridDev &g, const float *X, const float *Y, const float *eta, double kc, bool apply,
+                           float *out, float *coarse, cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    const size_t sm = 4 * G18::CS * sizeof(float);
+    static const bool attr = (cudaFuncSetAttribute(k_pair_op<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              cudaFuncSetAttribute(k_pair_op<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              cudaFuncSetAttribute(k_pair_op<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              true);
+    (void)attr;
+    if (apply)
+        k_pair_op<true, false><<<g.nblk / 2, 512, sm, s>>>(g, X, nullptr, eta, (float)kc, out, nullptr);
+    else if (coarse)
+        k_pair_op<false, true><<<g.nblk / 2, 512, sm, s>>>(g, X, Y, eta, (float)kc, out, coarse);
+    else
+        k_pair_op<false, false><<<g.nblk / 2, 512, sm, s>>>(g, X, Y, eta, (float)kc, out, nullptr);
     return cudaGetLastError();
 }
 
