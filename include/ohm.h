@@ -35,8 +35,13 @@ extern "C" {
 #define OHM_ERR_CUDA          -5  /* a CUDA call or kernel launch failed                    */
 
 #define OHM_FP64  0  /* every kernel in float64                                             */
-#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the residual
-                        R = S - L B, the update B += e, refluxed fluxes and norms stay float64 */
+#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the source S,
+                        the first residual R = S - L B and every residual that ends a step, the
+                        update B += e and refluxed fluxes stay float64; an intermediate
+                        residual that the preceding correction is not expected to bring below
+                        tol (it only sets the next inner solve's right-hand side) is evaluated
+                        in float-float as under OHM_MIXED_FF, and one that meets tol all the
+                        same is re-evaluated in float64 before the step ends               */
 #define OHM_MIXED_FF 2 /* as OHM_MIXED, but the outer residual R = S - L B is evaluated in
                         float-float arithmetic (pairs of float32, about 48 significant bits,
                         on the float32 pipe, which GB300 issues 58x faster than float64) and

@@ -962,12 +962,20 @@ int fill_ghosts_B(ohm_hier *H, const double *B) {
 // fine fluxes are in the registers before the coarser level reads them), computed in TC.
 template <typename TC, typename TO>
 int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *Gx, const TC *Geta, double a, double c,
-                double dcoef, TO *out, TO *out2, bool norms, double *outS = nullptr, double c2 = 0.0) {
+                double dcoef, TO *out, TO *out2, bool norms, double *outS = nullptr, double c2 = 0.0, bool ff64 = false) {
     for (int l = H->nlev - 1; l >= 0; l--) {
         const HGrid &g = H->amr[l];
         double vol = g.h * g.h * g.h;
         const size_t o3 = (size_t)g.off * 3 * B3;
         if constexpr (std::is_same<TC, double>::value && std::is_same<TO, float>::value) {
+          if (ff64) {
+            // an intermediate outer residual of OHM_MIXED: float-float arithmetic, Y in float64
+            LAUNCH(H, OHM_K_COMPOSITE, g.n(),
+                   launch_composite_df(gdev(H, g), X + o3, Y ? Y + o3 : nullptr, eta + (size_t)g.off * B3, Gx, Geta, a,
+                                       c, dcoef, out + o3, out2 ? out2 + o3 : nullptr, H->reg, H->d_rsrc,
+                                       norms ? H->partials + (size_t)g.off * 3 : nullptr, vol, H->s));
+            continue;
+          }
           if (H->ff) {
             // outer residual of OHM_MIXED_FF: float-float arithmetic, Y and outS hold the source
             // in float-float form
@@ -1012,8 +1020,9 @@ int composite_t(ohm_hier *H, const TC *X, const TC *Y, const TC *eta, const TC *
 // float64 composite operator on B-like fields (eta and ghosts of the state)
 template <typename TO>
 int composite(ohm_hier *H, const double *X, const double *Y, double a, double c, double dcoef, TO *out, bool norms,
-              TO *out2 = nullptr) {
-    return composite_t<double, TO>(H, X, Y, H->eta64, H->ghostB, H->ghostEta64, a, c, dcoef, out, out2, norms);
+              TO *out2 = nullptr, bool ff64 = false) {
+    return composite_t<double, TO>(H, X, Y, H->eta64, H->ghostB, H->ghostEta64, a, c, dcoef, out, out2, norms, nullptr,
+                                   0.0, ff64);
 }
 
 // The first residual of a step and its source from one flux divergence of b (Eqs. 14, 20):
@@ -1276,13 +1285,23 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
     const size_t nbytes = (size_t)H->nblocks * 3 * B3 * sizeof(T);
     int cycles = 0, result = OHM_OK;
     double nr[4] = {0, 0, 0, 0}, first = 0;
-    for (int outer = 0;; outer++) {
-        if ((st = outer == 0 ? source_and_residual<T>(H, B, lam, dt, r, rout)
-                             : composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, rout)))
-            return st;
+    // The source and the first residual are float64, and so is every residual that ends the step:
+    // an outer residual that the last correction is not expected to bring below tol only sets the
+    // next inner solve's right-hand side, and is evaluated in float-float (error about 2^-48 of
+    // the operands, far below any tol it is compared with), unless the hierarchy is OHM_MIXED_FF
+    // (all in float-float).  A float-float residual that meets tol is confirmed in float64.
+    auto outer_residual = [&](int outer, bool ff) -> int {
+        int s2 = outer == 0 ? source_and_residual<T>(H, B, lam, dt, r, rout)
+                            : composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, rout, ff);
+        if (s2) return s2;
         int ef = 0;
-        if ((st = read_norms(H, nr, &ef))) return st;
-        if (ef) return OHM_ERR_INVALID;
+        if ((s2 = read_norms(H, nr, &ef))) return s2;
+        return ef ? OHM_ERR_INVALID : OHM_OK;
+    };
+    bool ff = false;
+    for (int outer = 0;; outer++) {
+        if ((st = outer_residual(outer, ff))) return st;
+        if (ff && tol >= 0 && nr[0] <= tol && (st = outer_residual(outer, false))) return st;
         if (outer == 0) first = nr[0];
         if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) {
             result = OHM_ERR_NONFINITE;
@@ -1295,11 +1314,13 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
         }
         const double fl = inner_floor(H);
         const double target = tol >= 0 ? std::max(fl, 0.3 * tol / std::max(nr[0], 1e-300)) : fl;
+        ff = !H->ff && !(tol >= 0 && nr[0] * target <= tol);
         if (H->d.krylov > 0) {
             if ((st = inner_fgmres(H, lamdt, target, &cycles))) return st;
         } else {
         CK(cudaMemsetAsync(eacc, 0, nbytes, H->s));
         double prev = 1.0;
+        int ef = 0;
         while (cycles < H->d.max_outer) {
             if ((st = vcycle<T>(H, lamdt))) return st;
             for (auto &g : H->amr)

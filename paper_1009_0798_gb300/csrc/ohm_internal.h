@@ -89,6 +89,12 @@ cudaError_t launch_composite_df(const GridDev &g, const double *X, const dfloat 
                                 const double *Gx, const double *Geta, double a, double c, double d, float *out,
                                 float *out2, double *reg, const int *rsrc_tab, double *partials, double vol,
                                 cudaStream_t s, dfloat *outS, double c2);
+// the same float-float evaluation with Y a float64 field (split into float-float values as it
+// is read); no source output
+cudaError_t launch_composite_df(const GridDev &g, const double *X, const double *Y, const double *eta,
+                                const double *Gx, const double *Geta, double a, double c, double d, float *out,
+                                float *out2, double *reg, const int *rsrc_tab, double *partials, double vol,
+                                cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_smooth(const GridDev &g, const T *e_in, T *e_out, const T *r, const T *eta,

@@ -520,9 +520,9 @@ struct CompTypes<dfloat> {
     static constexpr int minb = 3;
 };
 
-template <typename TC, typename TO, bool NORMS>
+template <typename TC, typename TO, bool NORMS, typename YT = TC>
 __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
-    k_composite(GridDev g, const typename CompTypes<TC>::In *__restrict__ X, const TC *__restrict__ Y,
+    k_composite(GridDev g, const typename CompTypes<TC>::In *__restrict__ X, const YT *__restrict__ Y,
                 const typename CompTypes<TC>::In *__restrict__ eta, const typename CompTypes<TC>::In *__restrict__ Gx,
                 const typename CompTypes<TC>::In *__restrict__ Geta, TC a, TC coef, TC d, TO *__restrict__ out,
                 TO *__restrict__ out2, double *__restrict__ reg, const int *__restrict__ rsrc_tab,
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         size_t id = ((size_t)b * 3 + c) * B3 + cell;
-        TC y = Y ? Y[id] : TC(0);
+        TC y = Y ? tile_val<TC, YT>(Y[id]) : TC(0);
         // ymx: a = -1, d = 1 (a residual), one operation less per component
         TC o = ymx ? (y - tB[c * G::CS + p]) + coef * dv[c] : a * tB[c * G::CS + p] + coef * dv[c] + d * y;
         if (sizeof(TC) == 8 && outS) {  // o is the source; the residual of X against it is coef2 divF(X)
@@ -646,8 +646,8 @@ __global__ void __launch_bounds__(512, CompTypes<TC>::minb)
     }
 }
 
-template <typename TC, typename TO>
-static cudaError_t launch_composite_t(const GridDev &g, const typename CompTypes<TC>::In *X, const TC *Y,
+template <typename TC, typename TO, typename YT = TC>
+static cudaError_t launch_composite_t(const GridDev &g, const typename CompTypes<TC>::In *X, const YT *Y,
                                      const typename CompTypes<TC>::In *eta, const typename CompTypes<TC>::In *Gx,
                                      const typename CompTypes<TC>::In *Geta, TC a, TC coef, TC d, TO *out, TO *out2,
                                      double *reg, const int *rsrc_tab, double *partials, double vol, cudaStream_t s,
@@ -655,16 +655,17 @@ static cudaError_t launch_composite_t(const GridDev &g, const typename CompTypes
     if (g.nblk == 0) return cudaSuccess;
     const size_t sm = (4 * Geo<TC>::CS + Geo<TC>::PHI + (std::is_same<TC, double>::value ? PSUM : 0)) * sizeof(TC);
     // set once per process (thread-safe static initialisation)
-    static const bool attr = (cudaFuncSetAttribute(k_composite<TC, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                              cudaFuncSetAttribute(k_composite<TC, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+    static const bool attr = (cudaFuncSetAttribute(k_composite<TC, TO, true, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              cudaFuncSetAttribute(k_composite<TC, TO, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                               true);
     (void)attr;
     if (partials)  // with norm partials (the block reductions are compiled out otherwise)
-        k_composite<TC, TO, true><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
-                                                          partials, vol, outS, coef2, 0.5 / g.h, 2.0 * g.h, ymx);
+        k_composite<TC, TO, true, YT><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
+                                                              partials, vol, outS, coef2, 0.5 / g.h, 2.0 * g.h, ymx);
     else
-        k_composite<TC, TO, false><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg, rsrc_tab,
-                                                           partials, vol, outS, coef2, 0.5 / g.h, 2.0 * g.h, ymx);
+        k_composite<TC, TO, false, YT><<<g.nblk, 512, sm, s>>>(g, X, Y, eta, Gx, Geta, a, coef, d, out, out2, reg,
+                                                               rsrc_tab, partials, vol, outS, coef2, 0.5 / g.h, 2.0 * g.h,
+                                                               ymx);
     return cudaGetLastError();
 }
 
@@ -692,6 +693,15 @@ cudaError_t launch_composite_df(const GridDev &g, const double *X, const dfloat 
     return launch_composite_t<dfloat, float>(g, X, Y, eta, Gx, Geta, df_from_host(a), df_from_host(coef),
                                              df_from_host(d), out, out2, reg, rsrc_tab, partials, vol, s, outS,
                                              df_from_host(coef2), a == -1.0 && d == 1.0);
+}
+cudaError_t launch_composite_df(const GridDev &g, const double *X, const double *Y, const double *eta,
+                                const double *Gx, const double *Geta, double a, double c, double d, float *out,
+                                float *out2, double *reg, const int *rsrc_tab, double *partials, double vol,
+                                cudaStream_t s) {
+    const double coef = c / (2.0 * g.h * g.h);
+    return launch_composite_t<dfloat, float, double>(g, X, Y, eta, Gx, Geta, df_from_host(a), df_from_host(coef),
+                                                     df_from_host(d), out, out2, reg, rsrc_tab, partials, vol, s,
+                                                     nullptr, dfloat(), a == -1.0 && d == 1.0);
 }
 #define INST_COMPOSITE(TC, TO)                                                                                        \
     template cudaError_t launch_composite<TC, TO>(const GridDev &, const TC *, const TC *, const TC *, const TC *,     \
