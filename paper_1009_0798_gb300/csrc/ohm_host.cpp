@@ -24,6 +24,9 @@ constexpr int MAX_LEVELS = 8;
 // lexicographic grids of more cells than this are stepped by grid-wide launches; the rest, down
 // to the coarsest, by the one-block solver (k_bottom: one thread block per instance)
 constexpr int MAX_BOTTOM_CELLS = 16384;
+// mixed precision: coarse grids of at most this many cells (16^3), with power-of-two extents, are
+// not blocked; the coarsest-grid solver runs them in shared memory
+constexpr int64_t MIN_BLOCKED_CELLS = 4096;
 
 inline int wrapi(int v, int n) {
     v %= n;
@@ -298,7 +301,11 @@ int build_tables(ohm_hier *H, std::string &err) {
     while (dims[0] % 2 == 0 && dims[1] % 2 == 0 && dims[2] % 2 == 0 && dims[0] >= 4 && dims[1] >= 4 && dims[2] >= 4) {
         for (int a = 0; a < 3; a++) dims[a] /= 2;
         h *= 2.0;
-        if (blocked && dims[0] % BS == 0 && dims[1] % BS == 0 && dims[2] % BS == 0) {
+        // mixed precision: a power-of-two grid of at most MIN_BLOCKED_CELLS cells and everything
+        // below it go to the coarsest-grid solver, which holds them in shared memory
+        const bool p2 = !(dims[0] & (dims[0] - 1)) && !(dims[1] & (dims[1] - 1)) && !(dims[2] & (dims[2] - 1));
+        const bool to_bottom = H->mixed && p2 && (int64_t)dims[0] * dims[1] * dims[2] <= MIN_BLOCKED_CELLS;
+        if (blocked && !to_bottom && dims[0] % BS == 0 && dims[1] % BS == 0 && dims[2] % BS == 0) {
             HGrid g;
             g.level = -1;
             g.h = h;

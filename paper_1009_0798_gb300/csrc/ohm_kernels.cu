@@ -2396,9 +2396,240 @@ __global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm_all, double lamd
     }
 }
 
+// The same V-cycle over the lexicographic grids (float32, every extent a power of two) with the
+// grids held in shared memory: e, r, t and eta of every grid are staged once (r of the first grid
+// and eta from global memory, e from zero), every pass of the cycle runs between two block
+// barriers, and only e of the first grid is written back.  The point update is the fused sweeps'
+// (face_pair flux divergence, Eqs. 8-10, and the relaxed diagonal formed from eta, Eqs. 21-23)
+// through an accessor whose periodic neighbour offsets are formed once per cell.
+struct LexAcc {
+    const float *fB, *fE;
+    int n;                    // cells of the grid (component stride)
+    int xo[3], yo[3], zo[3];  // offsets of the cells at -1, 0, +1 along x, y, z (wrapped)
+    template <int C, int DX, int DY, int DZ>
+    __device__ __forceinline__ float B() const {
+        return fB[C * n + zo[DZ + 1] + yo[DY + 1] + xo[DX + 1]];
+    }
+    template <int DX, int DY, int DZ>
+    __device__ __forceinline__ float E() const {
+        return fE[zo[DZ + 1] + yo[DY + 1] + xo[DX + 1]];
+    }
+};
+
+struct LexDims {
+    int lx, ly, lz;  // log2 of the extents
+    __device__ __forceinline__ int n() const { return 1 << (lx + ly + lz); }
+    __device__ __forceinline__ void cell(int q, int &x, int &y, int &z) const {
+        x = q & ((1 << lx) - 1);
+        y = (q >> lx) & ((1 << ly) - 1);
+        z = q >> (lx + ly);
+    }
+    __device__ __forceinline__ LexAcc acc(const float *B, const float *E, int x, int y, int z) const {
+        const int mx = (1 << lx) - 1, my = (1 << ly) - 1, mz = (1 << lz) - 1;
+        LexAcc a;
+        a.fB = B;
+        a.fE = E;
+        a.n = n();
+        a.xo[0] = (x - 1) & mx;
+        a.xo[1] = x;
+        a.xo[2] = (x + 1) & mx;
+        a.yo[0] = ((y - 1) & my) << lx;
+        a.yo[1] = y << lx;
+        a.yo[2] = ((y + 1) & my) << lx;
+        a.zo[0] = ((z - 1) & mz) << (lx + ly);
+        a.zo[1] = z << (lx + ly);
+        a.zo[2] = ((z + 1) & mz) << (lx + ly);
+        return a;
+    }
+};
+
+struct BottomSm {  // no default member initialisers: a __shared__ copy is filled by one thread
+    int n;
+    LexDims d[MAX_SMALL];
+    int base[MAX_SMALL];          // float offset of grid s in shared memory: e[3n], r[3n], t[3n], eta[n]
+    RbK<float> K[MAX_SMALL];      // update constants of grid s (the sweeps' relaxed diagonal, Eqs. 21-23)
+};
+
+// the i-th cell of colour `colour` ((x + y + z) & 1) of a grid with at least 2 cells along x
+__device__ __forceinline__ void colour_cell(const LexDims &D, int i, int colour, int &x, int &y, int &z) {
+    const int hx = D.lx - 1;
+    y = (i >> hx) & ((1 << D.ly) - 1);
+    z = i >> (hx + D.ly);
+    x = 2 * (i & ((1 << hx) - 1)) + ((y + z + colour) & 1);
+}
+
+// one colour pass of grid s (Jacobi within the colour): t = (r - L e) / den on the colour's cells,
+// then e += t
+__device__ __forceinline__ void bsm_colour(const BottomSm &P, float *sh, int s, int colour) {
+    const LexDims D = P.d[s];
+    const int n = D.n();
+    float *e = sh + P.base[s], *r = e + 3 * n, *t = r + 3 * n, *E = t + 3 * n;
+    const RbK<float> K = P.K[s];
+    const int ncol = D.lx >= 1 ? n / 2 : n;  // a grid one cell wide in x: every cell, colour checked
+    for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+        int x, y, z;
+        if (D.lx >= 1) {
+            colour_cell(D, i, colour, x, y, z);
+        } else {
+            D.cell(i, x, y, z);
+            if (((x + y + z) & 1) != colour) continue;
+        }
+        const int q = (z << (D.lx + D.ly)) | (y << D.lx) | x;
+        const LexAcc a = D.acc(e, E, x, y, z);
+        float es[6], den[3], dv[3];
+        rb_faces_den<float>(a, K, es, den);
+        cell_divergence<float>(a, es, dv);
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            t[c * n + q] = rb_relax(0.f, v_mad(K.ncoef, dv[c], v_sub(r[c * n + q], e[c * n + q])), den[c]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+        int x, y, z;
+        if (D.lx >= 1) {
+            colour_cell(D, i, colour, x, y, z);
+        } else {
+            D.cell(i, x, y, z);
+            if (((x + y + z) & 1) != colour) continue;
+        }
+        const int q = (z << (D.lx + D.ly)) | (y << D.lx) | x;
+#pragma unroll
+        for (int c = 0; c < 3; c++) e[c * n + q] = v_add(e[c * n + q], t[c * n + q]);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_bottom_sm(SmallDev<float> sm_all, BottomSm P_arg, int nu1, int nu2, int nc) {
+    if (sm_all.imask && !sm_all.imask[blockIdx.x]) return;
+    extern __shared__ __align__(16) float sh[];
+    // the grid table and this instance's global arrays in shared memory (indexed by grid below;
+    // kernel parameters are only read at compile-time indices)
+    __shared__ BottomSm P;
+    if (threadIdx.x == 0) P = P_arg;
+    // stage r of grid 0 and eta of every grid; e of grid 0 starts from zero
+#pragma unroll
+    for (int g = 0; g < MAX_SMALL; g++) {
+        if (g >= P_arg.n) break;
+        const int n = P_arg.d[g].n();
+        float *e = sh + P_arg.base[g], *r = e + 3 * n, *E = r + 6 * n;
+        const float *eta = sm_all.eta[g] + (size_t)blockIdx.x * n;
+        for (int q = threadIdx.x; q < n; q += blockDim.x) E[q] = eta[q];
+        if (g == 0) {
+            const float *r0 = sm_all.r[0] + (size_t)blockIdx.x * 3 * n;
+            for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {
+                r[q] = r0[q];
+                e[q] = 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    int s = 0;
+    for (; s < P.n - 1; s++) {
+        for (int k = 0; k < nu1; k++) {
+            bsm_colour(P, sh, s, 0);
+            bsm_colour(P, sh, s, 1);
+        }
+        const LexDims D = P.d[s], C = P.d[s + 1];
+        const int n = D.n(), ncs = C.n();
+        float *e = sh + P.base[s], *r = e + 3 * n, *t = r + 3 * n, *E = t + 3 * n;
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {  // residual t = r - L e
+            int x, y, z;
+            D.cell(q, x, y, z);
+            const LexAcc a = D.acc(e, E, x, y, z);
+            float es[6], dv[3];
+            face_sums<float>(a, es);
+            cell_divergence<float>(a, es, dv);
+#pragma unroll
+            for (int c = 0; c < 3; c++) t[c * n + q] = v_mad(P.K[s].ncoef, dv[c], v_sub(r[c * n + q], e[c * n + q]));
+        }
+        __syncthreads();
+        float *ec = sh + P.base[s + 1], *rc = ec + 3 * ncs;
+        for (int q = threadIdx.x; q < 3 * ncs; q += blockDim.x) {  // mean of the 8 children; e = 0
+            const int c = q / ncs, cq = q - c * ncs;
+            int x, y, z;
+            C.cell(cq, x, y, z);
+            float acc = 0.f;
+            for (int dk = 0; dk < 2; dk++)
+                for (int dj = 0; dj < 2; dj++)
+                    for (int di = 0; di < 2; di++)
+                        acc = v_add(acc, t[c * n + (((2 * z + dk) << (D.lx + D.ly)) | ((2 * y + dj) << D.lx) | (2 * x + di))]);
+            rc[q] = v_mul(acc, 0.125f);
+            ec[q] = 0.f;
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < nc; k++) {
+        bsm_colour(P, sh, s, 0);
+        bsm_colour(P, sh, s, 1);
+    }
+    for (s = P.n - 2; s >= 0; s--) {
+        const LexDims D = P.d[s], C = P.d[s + 1];
+        const int n = D.n(), ncs = C.n();
+        float *e = sh + P.base[s];
+        const float *ec = sh + P.base[s + 1];
+        const int cmx = (1 << C.lx) - 1, cmy = (1 << C.ly) - 1, cmz = (1 << C.lz) - 1;
+        for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {  // trilinear prolongation (weights 3/4, 1/4)
+            const int c = q / n, fq = q - c * n;
+            int x, y, z;
+            D.cell(fq, x, y, z);
+            const int px = x >> 1, py = y >> 1, pz = z >> 1;
+            const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
+            float v = 0.f;
+            for (int ak = 0; ak < 2; ak++)
+                for (int aj = 0; aj < 2; aj++)
+                    for (int ai = 0; ai < 2; ai++) {
+                        const float wt = (ai ? 0.25f : 0.75f) * (aj ? 0.25f : 0.75f) * (ak ? 0.25f : 0.75f);
+                        const int cx = (px + ai * sx) & cmx, cy = (py + aj * sy) & cmy, cz = (pz + ak * sz) & cmz;
+                        v = v_mad(wt, ec[c * ncs + ((cz << (C.lx + C.ly)) | (cy << C.lx) | cx)], v);
+                    }
+            e[q] = v_add(e[q], v);
+        }
+        __syncthreads();
+        for (int k = 0; k < nu2; k++) {
+            bsm_colour(P, sh, s, 0);
+            bsm_colour(P, sh, s, 1);
+        }
+    }
+    const int n0 = P.d[0].n();
+    float *e0 = sm_all.e[0] + (size_t)blockIdx.x * 3 * n0;
+    for (int q = threadIdx.x; q < 3 * n0; q += blockDim.x) e0[q] = sh[P.base[0] + q];
+}
+
+constexpr size_t BOTTOM_SMEM_MAX = 200 * 1024;
+
+static int ilog2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return (1 << l) == v ? l : -1;
+}
+
 template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post, int n_coarse, cudaStream_t s) {
     if (sm.n == 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+        // shared-memory solver when every extent is a power of two and the grids fit
+        BottomSm P;
+        P.n = sm.n;
+        size_t off = 0;
+        bool ok = true;
+        for (int q = 0; q < sm.n && ok; q++) {
+            const int lx = ilog2_exact(sm.dims[q][0]), ly = ilog2_exact(sm.dims[q][1]), lz = ilog2_exact(sm.dims[q][2]);
+            ok = lx >= 0 && ly >= 0 && lz >= 0;
+            P.d[q] = LexDims{lx, ly, lz};
+            P.base[q] = (int)off;
+            P.K[q] = rb_constants<float>(lamdt, sm.h[q], sm.omega);
+            off += 10 * (size_t)sm.dims[q][0] * sm.dims[q][1] * sm.dims[q][2];
+            off = (off + 3) & ~(size_t)3;
+        }
+        const size_t bytes = off * sizeof(float);
+        if (ok && bytes <= BOTTOM_SMEM_MAX) {
+            static const bool attr =
+                (cudaFuncSetAttribute(k_bottom_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BOTTOM_SMEM_MAX), true);
+            (void)attr;
+            k_bottom_sm<<<sm.ninst, 1024, bytes, s>>>(sm, P, nu_pre, nu_post, n_coarse);
+            return cudaGetLastError();
+        }
+    }
     k_bottom<T><<<sm.ninst, 1024, 0, s>>>(sm, lamdt, nu_pre, nu_post, n_coarse);
     return cudaGetLastError();
 }
