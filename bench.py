@@ -10,7 +10,8 @@ Metric: cell-steps/s = cells x CN steps / device time.  `value` is the mixed-pre
 (FP32 multigrid, FGMRES-accelerated, inside FP64 iterative refinement; red-black SOR sweeps
 with V(3,2) on level 0 and V(1,0) below); the plain FP64 path (the paper's Gauss-Seidel defect
 correction), the same with the paper's defect correction in mixed precision, and the
-float-float outer residual (OHM_MIXED_FF) are reported beside it.  `e2e` repeats the step
+float-float outer residual (OHM_MIXED_FF) and with float-float intermediate residuals checked in
+float64 (OHM_MIXED_FF_CHECKED) are reported beside it.  `e2e` repeats the step
 through the public API with pinned host buffers.  The oracle (FP64 CPU reference) is timed on
 the host cores as `cpu_baseline`, and is the `--impl reference` arm.  `--workload batched512`
 and `--workload serving` measure the batched hierarchies and the solve service.
@@ -46,7 +47,7 @@ def args_parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--only", choices=["fgmres", "fgmres_ff", "mixed", "fp64"], default=None,
+    p.add_argument("--only", choices=["fgmres", "fgmres_ff", "fgmres_ffc", "mixed", "fp64"], default=None,
                    help="run just this path for a few steps and print its timing (for profiler captures)")
     p.add_argument("--nu", default="3,2", help="pre,post red-black sweeps on level 0")
     p.add_argument("--nu-coarse", default="1,0",
@@ -421,7 +422,8 @@ def run_ours(args):
                 "ms_per_step": r["total_ms"] / args.steps, "cycles_per_step": [s["cycles"] for s in r["infos"]]}
 
     if args.only:
-        prec = {"fp64": ohm.OHM_FP64, "fgmres_ff": ohm.OHM_MIXED_FF}.get(args.only, ohm.OHM_MIXED)
+        prec = {"fp64": ohm.OHM_FP64, "fgmres_ff": ohm.OHM_MIXED_FF,
+                "fgmres_ffc": ohm.OHM_MIXED_FF_CHECKED}.get(args.only, ohm.OHM_MIXED)
         fg = args.only.startswith("fgmres")
         g1 = make(prec, KRYLOV if fg else 0, args.omega if fg else 1.0, nuc if fg else (0, 0))
         for _ in range(args.warmup):
@@ -460,14 +462,21 @@ def run_ours(args):
         # counts and relaxation, and with the paper's schedule (Gauss-Seidel, the same sweeps on
         # every grid); FP64 has no Krylov inner solve
         for name, prec, kr, om, nc in (("mixed_float_float_residual", ohm.OHM_MIXED_FF, KRYLOV, args.omega, nuc),
+                                       ("mixed_float_float_checked", ohm.OHM_MIXED_FF_CHECKED, KRYLOV, args.omega, nuc),
                                        ("mixed_defect_correction", ohm.OHM_MIXED, 0, 1.0, (0, 0)),
                                        ("fp64_plain", ohm.OHM_FP64, 0, args.omega, nuc),
                                        ("fp64_paper_schedule", ohm.OHM_FP64, 0, 1.0, (0, 0))):
             g2 = make(prec, kr, om, nc)
-            others[name] = summary(timed(g2, prec, profile=False))
+            r2 = timed(g2, prec, profile=False)
+            others[name] = summary(r2)
             if prec == ohm.OHM_MIXED_FF:
                 others[name]["precision"] = ("OHM_MIXED_FF: as the headline, but the outer residual in float-float "
                                              "(float32 pairs, ~48 bits) with float32-accumulated norms")
+            if prec == ohm.OHM_MIXED_FF_CHECKED:
+                others[name]["precision"] = ("OHM_MIXED_FF_CHECKED: as the headline, but the intermediate outer "
+                                             "residuals in float-float; the source, the first and every "
+                                             "step-ending residual in float64")
+                others[name]["final_rel_l2_max"] = max(st["rel_l2"] for st in r2["infos"])
             if prec == ohm.OHM_FP64:
                 others[name]["multigrid"] = (f"float64 V({nu[0]},{nu[1]}) on level 0, "
                                              f"V({nc[0] or nu[0]},{nc[1] if nc != (0, 0) else nu[1]}) below, "
@@ -588,6 +597,7 @@ def run_ours(args):
             "fp64_fma_tflops": fp64_peak_tflops(ohm),
             "mixed_defect_correction": others.get("mixed_defect_correction"),
             "mixed_float_float_residual": others.get("mixed_float_float_residual"),
+            "mixed_float_float_checked": others.get("mixed_float_float_checked"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": mixed["clocks"],
             "gpu_launches": mixed["launches"], **legs}
     print(json.dumps(line), flush=True)

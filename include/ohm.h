@@ -35,13 +35,8 @@ extern "C" {
 #define OHM_ERR_CUDA          -5  /* a CUDA call or kernel launch failed                    */
 
 #define OHM_FP64  0  /* every kernel in float64                                             */
-#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the source S,
-                        the first residual R = S - L B and every residual that ends a step, the
-                        update B += e and refluxed fluxes stay float64; an intermediate
-                        residual that the preceding correction is not expected to bring below
-                        tol (it only sets the next inner solve's right-hand side) is evaluated
-                        in float-float as under OHM_MIXED_FF, and one that meets tol all the
-                        same is re-evaluated in float64 before the step ends               */
+#define OHM_MIXED 1  /* multigrid in float32 inside float64 defect correction: the residual
+                        R = S - L B, the update B += e, refluxed fluxes and norms stay float64 */
 #define OHM_MIXED_FF 2 /* as OHM_MIXED, but the outer residual R = S - L B is evaluated in
                         float-float arithmetic (pairs of float32, about 48 significant bits,
                         on the float32 pipe, which GB300 issues 58x faster than float64) and
@@ -52,6 +47,15 @@ extern "C" {
                         2^64 keeps the squared norms finite); values below 2^-126 count as
                         zero, NaN and values beyond 2^128 end the step with
                         OHM_ERR_NONFINITE.  Refluxed fluxes stay float64.                    */
+#define OHM_MIXED_FF_CHECKED 3 /* as OHM_MIXED, but an intermediate outer residual (one that the
+                        preceding correction is not expected to bring below tol: it only sets
+                        the next inner solve's right-hand side) is evaluated in float-float as
+                        under OHM_MIXED_FF; the source, the first residual and every residual
+                        that ends a step stay float64, and a float-float residual that meets tol
+                        is re-evaluated in float64 before the step ends (the range limits of
+                        OHM_MIXED_FF apply to the intermediate residuals).  Batched hierarchies
+                        (n_instances >= 1) evaluate every outer residual in float64, as
+                        OHM_MIXED                                                            */
 
 typedef struct ohm_hier ohm_hier;
 
@@ -68,7 +72,7 @@ typedef struct {
                                    refined block's parent exist (proper nesting).  Copied.     */
     double lambda;              /* theta parameter of Eq. 7: 0.5 Crank-Nicolson, 1 backward
                                    Euler; any value in (0, 1]                                  */
-    int32_t precision;          /* OHM_FP64, OHM_MIXED or OHM_MIXED_FF                         */
+    int32_t precision;          /* OHM_FP64, OHM_MIXED, OHM_MIXED_FF or OHM_MIXED_FF_CHECKED   */
     int32_t nu_pre, nu_post;    /* red-black sweeps before / after coarse correction (>= 0):
                                    on every grid, or on level 0 and the refined levels when
                                    nu_coarse_pre / nu_coarse_post are set                      */

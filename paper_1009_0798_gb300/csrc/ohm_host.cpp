@@ -107,6 +107,7 @@ struct ohm_hier {
     int *flag_dev = nullptr;      // device address of the eta-comparison flag in hnorm (mapped)
     double *hnorm_dev = nullptr;  // device address of hnorm itself (mapped), null if not mapped
 
+    bool ff_mid = false;          // OHM_MIXED_FF_CHECKED: intermediate outer residuals in float-float
     bool eta_set = false;
     double inv_dt = NAN;
     bool has_S = false;
@@ -1292,11 +1293,11 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
     const size_t nbytes = (size_t)H->nblocks * 3 * B3 * sizeof(T);
     int cycles = 0, result = OHM_OK;
     double nr[4] = {0, 0, 0, 0}, first = 0;
-    // The source and the first residual are float64, and so is every residual that ends the step:
-    // an outer residual that the last correction is not expected to bring below tol only sets the
-    // next inner solve's right-hand side, and is evaluated in float-float (error about 2^-48 of
-    // the operands, far below any tol it is compared with), unless the hierarchy is OHM_MIXED_FF
-    // (all in float-float).  A float-float residual that meets tol is confirmed in float64.
+    // OHM_MIXED_FF_CHECKED: the source and the first residual are float64, and so is every
+    // residual that ends the step; an outer residual that the last correction is not expected to
+    // bring below tol only sets the next inner solve's right-hand side, and is evaluated in
+    // float-float (error about 2^-48 of the operands, far below any tol it is compared with).  A
+    // float-float residual that meets tol is confirmed in float64.
     auto outer_residual = [&](int outer, bool ff) -> int {
         int s2 = outer == 0 ? source_and_residual<T>(H, B, lam, dt, r, rout)
                             : composite<T>(H, B, H->S, -1.0, -lamdt, 1.0, r, true, rout, ff);
@@ -1321,7 +1322,7 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
         }
         const double fl = inner_floor(H);
         const double target = tol >= 0 ? std::max(fl, 0.3 * tol / std::max(nr[0], 1e-300)) : fl;
-        ff = !H->ff && !(tol >= 0 && nr[0] * target <= tol);
+        ff = H->ff_mid && !(tol >= 0 && nr[0] * target <= tol);
         if (H->d.krylov > 0) {
             if ((st = inner_fgmres(H, lamdt, target, &cycles))) return st;
         } else {
@@ -1734,7 +1735,8 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     if (d->nlevels < 1 || d->nlevels > MAX_LEVELS) { err = "nlevels out of range"; return false; }
     if (d->nblocks <= 0 || !d->block_lijk) { err = "empty block list"; return false; }
     if (!(d->lambda > 0 && d->lambda <= 1)) { err = "lambda must be in (0, 1]"; return false; }
-    if (d->precision != OHM_FP64 && d->precision != OHM_MIXED && d->precision != OHM_MIXED_FF) {
+    if (d->precision != OHM_FP64 && d->precision != OHM_MIXED && d->precision != OHM_MIXED_FF &&
+        d->precision != OHM_MIXED_FF_CHECKED) {
         err = "unknown precision";
         return false;
     }
@@ -1788,6 +1790,7 @@ int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out) {
     H->s = (cudaStream_t)d->stream;
     H->mixed = d->precision != OHM_FP64;
     H->ff = d->precision == OHM_MIXED_FF;
+    H->ff_mid = d->precision == OHM_MIXED_FF_CHECKED;
     H->nlev = d->nlevels;
     H->nblocks = d->nblocks;
     H->lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);
@@ -1817,6 +1820,7 @@ int ohm_hierarchy_bytes(const ohm_hier_desc *d, int64_t *bytes) {
     H.d.block_lijk = nullptr;
     H.mixed = d->precision != OHM_FP64;
     H.ff = d->precision == OHM_MIXED_FF;
+    H.ff_mid = d->precision == OHM_MIXED_FF_CHECKED;
     H.nlev = d->nlevels;
     H.nblocks = d->nblocks;
     H.lijk.assign(d->block_lijk, d->block_lijk + 4 * d->nblocks);

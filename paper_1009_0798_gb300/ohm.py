@@ -20,6 +20,7 @@ OHM_ERR_CUDA = -5
 OHM_FP64 = 0
 OHM_MIXED = 1
 OHM_MIXED_FF = 2
+OHM_MIXED_FF_CHECKED = 3
 OHM_K_COMPOSITE, OHM_K_SMOOTH, OHM_K_RESID_RESTRICT, OHM_K_PROLONG, OHM_K_GHOST = 0, 1, 2, 3, 4
 OHM_K_SYNC_DOWN, OHM_K_UPDATE, OHM_K_BOTTOM, OHM_K_NORM, OHM_K_KRYLOV = 5, 6, 7, 8, 9
 

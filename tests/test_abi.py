@@ -77,7 +77,7 @@ def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
     elif case == "bad_inner_tol":
         kw.update(precision=libohm.OHM_MIXED, inner_tol=1.5)
     elif case == "bad_precision":
-        kw["precision"] = libohm.OHM_MIXED_FF + 1
+        kw["precision"] = libohm.OHM_MIXED_FF_CHECKED + 1
     elif case == "omega_2":
         kw["omega"] = 2.0
     elif case == "omega_negative":

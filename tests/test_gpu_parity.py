@@ -272,10 +272,11 @@ def test_periodic_box_32_workload(ohm, orc):
 # ------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("name", ["uniform_32", "amr_3level", "sinusoid_e1"])
 @pytest.mark.parametrize("krylov", [0, 4])
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 def test_mixed_precision_matches_fp64_oracle(ohm, orc, name, krylov, precision):
     """FP32 multigrid (plain or FGMRES-accelerated) inside FP64 iterative refinement reaches
-    the FP64 solution."""
+    the FP64 solution.  OHM_MIXED_FF_CHECKED (3) ends the step on a float64 residual: the norm
+    it reports is the float64 one of its result."""
     h = HIERS[name]()
     b, eta = rand_fields(h, 8, 1.0)
     b = orc.Oracle(h, 0.5, eta).sync_down(b)
@@ -288,6 +289,8 @@ def test_mixed_precision_matches_fp64_oracle(ohm, orc, name, krylov, precision):
     assert rel_err(host(B), want.ravel()) < 1e-9
     rel, _ = ohm.ohm_residual_norm(g, B)
     assert rel <= 1e-11
+    if precision == 3:
+        assert st["rel_l2"] == pytest.approx(rel, rel=1e-9)
 
 
 # relative residual each mixed mode reports at the oracle's converged solution (float64: rounding;
@@ -325,7 +328,7 @@ def test_mixed_outer_residual_accuracy(ohm, orc, name, precision):
     assert mx0 == pytest.approx(n0["max_abs"], rel=max(norm_rel, 1e-6))
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 @pytest.mark.parametrize("bad", ["nan_eta", "inf_B", "huge_B"])
 def test_mixed_nonfinite_inputs_report_nonfinite(ohm, bad, precision):
     """NaN, infinity and (for the float-float residual, which splits float64 values into
