@@ -1165,12 +1165,16 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     const int k = t >> 6, j = (t >> 3) & 7, i2 = t & 7;
     const int ir = 2 * i2 + ((j + k) & 1), ib = 2 * i2 + ((j + k + 1) & 1);  // both in block A (i2 < 4) or B
     const int own = A + (i2 >> 2);
-    const int cr = (k * 8 + j) * 8 + (ir & 7), cb = (k * 8 + j) * 8 + (ib & 7);
+    // the red and the black cell of a thread are the x-pair (2 i2, 2 i2 + 1) of a block row:
+    // their right-hand sides come in, and their results go out, as one 8-byte word each
+    const int cpair = (k * 8 + j) * 8 + ((2 * i2) & 7);
+    const bool red_even = ((j + k) & 1) == 0;
     float rr0[3], rr1[3] = {0.f, 0.f, 0.f}, rrb[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        rr0[c] = r[((size_t)own * 3 + c) * B3 + cr];
-        rrb[c] = r[((size_t)own * 3 + c) * B3 + cb];
+        const float2 v = *reinterpret_cast<const float2 *>(r + ((size_t)own * 3 + c) * B3 + cpair);
+        rr0[c] = red_even ? v.x : v.y;
+        rrb[c] = red_even ? v.y : v.x;
     }
     int p1 = -1;
     if (t < 384) {
@@ -1209,10 +1213,9 @@ __global__ void __launch_bounds__(512, 3) k_smooth_rb2(GridDev g, const float *_
     else
         rb_update<float, G>(tB, tE, G::at(ib + 2, j + 2, k + 2), K, rrb, out);
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-        e_out[((size_t)own * 3 + c) * B3 + cb] = out[c];
-        e_out[((size_t)own * 3 + c) * B3 + cr] = nv0[c];
-    }
+    for (int c = 0; c < 3; c++)
+        *reinterpret_cast<float2 *>(e_out + ((size_t)own * 3 + c) * B3 + cpair) =
+            red_even ? make_float2(nv0[c], out[c]) : make_float2(out[c], nv0[c]);
 }
 
 cudaError_t launch_smooth_rb2(const GridDev &g, const float *e_in, float *e_out, const float *r, const float *eta,
