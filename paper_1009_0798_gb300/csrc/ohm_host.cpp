@@ -108,6 +108,7 @@ struct ohm_hier {
     double *hnorm_dev = nullptr;  // device address of hnorm itself (mapped), null if not mapped
 
     bool ff_mid = false;          // OHM_MIXED_FF_CHECKED: intermediate outer residuals in float-float
+    bool inv_all = false;         // the inverse diagonals of every grid are those of inv_dt
     bool eta_set = false;
     double inv_dt = NAN;
     bool has_S = false;
@@ -746,27 +747,38 @@ int eta_derive(ohm_hier *H) {
     return OHM_OK;
 }
 
-// inverse diagonals of every multigrid grid for lambda*dt
+// inverse diagonals of the multigrid grids for lambda*dt.  The fused float32 sweeps and the
+// shared-memory coarsest-grid solver form the diagonal from eta: with the fused smoother a float32
+// hierarchy computes inverse diagonals only for the grids swept by colour passes (ghost slots) and
+// for coarsest-grid paths that read them.
 template <typename T>
 int prepare_dt(ohm_hier *H, double dt) {
-    if (H->inv_dt == dt) return OHM_OK;
+    const bool lean = std::is_same<T, float>::value && H->smoother == 0;
+    if (H->inv_dt == dt && (H->inv_all || lean)) return OHM_OK;
     const double lamdt = H->d.lambda * dt;
     cudaStream_t s = H->s;
     // the relaxation factor is folded into the inverse diagonal (omega / (1 + alpha))
     for (auto &g : H->amr) {
+        if (lean && g.nslot == 0) continue;
         GridDev d = g.dev;
         d.omega = H->d.omega;
         CK(launch_invdiag<T>(d, amr_ptr<T>(H->amrbuf.eta, g, 1), (const T *)H->ghostEtaT, lamdt,
                              amr_ptr<T>(H->amrbuf.inv, g, 3), s));
     }
     for (size_t m = 0; m < H->mg.size(); m++) {
+        if (lean && H->mg[m].nslot == 0) continue;
         GridDev d = H->mg[m].dev;
         d.omega = H->d.omega;
         CK(launch_invdiag<T>(d, (const T *)H->mgbuf[m].eta, nullptr, lamdt, (T *)H->mgbuf[m].inv, s));
     }
     SmallDev<T> sm = small_dev<T>(H);
-    CK(launch_small_setup<T>(sm, lamdt, false, s));
+    bool small_lean = false;
+    if constexpr (std::is_same<T, float>::value)
+        small_lean = lean && (int64_t)sm.dims[0][0] * sm.dims[0][1] * sm.dims[0][2] <= MAX_BOTTOM_CELLS &&
+                     bottom_in_shared(sm);
+    if (!small_lean) CK(launch_small_setup<T>(sm, lamdt, false, s));
     H->inv_dt = dt;
+    H->inv_all = !lean;
     return OHM_OK;
 }
 

@@ -183,6 +183,10 @@ cudaError_t launch_norm_reduce(const double *partials, int nblocks, double *scra
 template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post,
                           int n_coarse, cudaStream_t s);
+// whether launch_bottom runs these float32 grids in the shared-memory solver (every extent a
+// power of two, the grids within its shared memory), which forms the diagonal from eta and does
+// not read the grids' inverse diagonals
+bool bottom_in_shared(const SmallDev<float> &sm);
 
 // Grid-wide steps on lexicographic grid s of every instance (grids too large for the one-block
 // coarsest solver): nsweep red-black sweeps (e -> t -> e), residual into t and its restriction

@@ -2606,26 +2606,38 @@ static int ilog2_exact(int v) {
     return (1 << l) == v ? l : -1;
 }
 
+// the shared-memory solver's grid table and its shared-memory bytes; false when a grid extent
+// is not a power of two or the grids do not fit
+static bool bottom_table(const SmallDev<float> &sm, double lamdt, BottomSm &P, size_t &bytes) {
+    P.n = sm.n;
+    size_t off = 0;
+    for (int q = 0; q < sm.n; q++) {
+        const int lx = ilog2_exact(sm.dims[q][0]), ly = ilog2_exact(sm.dims[q][1]), lz = ilog2_exact(sm.dims[q][2]);
+        if (lx < 0 || ly < 0 || lz < 0) return false;
+        P.d[q] = LexDims{lx, ly, lz};
+        P.base[q] = (int)off;
+        P.K[q] = rb_constants<float>(lamdt, sm.h[q], sm.omega);
+        off += 10 * (size_t)sm.dims[q][0] * sm.dims[q][1] * sm.dims[q][2];
+        off = (off + 3) & ~(size_t)3;
+    }
+    bytes = off * sizeof(float);
+    return bytes <= BOTTOM_SMEM_MAX;
+}
+
+bool bottom_in_shared(const SmallDev<float> &sm) {
+    BottomSm P;
+    size_t bytes = 0;
+    return sm.n > 0 && bottom_table(sm, 1.0, P, bytes);
+}
+
 template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post, int n_coarse, cudaStream_t s) {
     if (sm.n == 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
         // shared-memory solver when every extent is a power of two and the grids fit
         BottomSm P;
-        P.n = sm.n;
-        size_t off = 0;
-        bool ok = true;
-        for (int q = 0; q < sm.n && ok; q++) {
-            const int lx = ilog2_exact(sm.dims[q][0]), ly = ilog2_exact(sm.dims[q][1]), lz = ilog2_exact(sm.dims[q][2]);
-            ok = lx >= 0 && ly >= 0 && lz >= 0;
-            P.d[q] = LexDims{lx, ly, lz};
-            P.base[q] = (int)off;
-            P.K[q] = rb_constants<float>(lamdt, sm.h[q], sm.omega);
-            off += 10 * (size_t)sm.dims[q][0] * sm.dims[q][1] * sm.dims[q][2];
-            off = (off + 3) & ~(size_t)3;
-        }
-        const size_t bytes = off * sizeof(float);
-        if (ok && bytes <= BOTTOM_SMEM_MAX) {
+        size_t bytes = 0;
+        if (bottom_table(sm, lamdt, P, bytes)) {
             static const bool attr =
                 (cudaFuncSetAttribute(k_bottom_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BOTTOM_SMEM_MAX), true);
             (void)attr;
