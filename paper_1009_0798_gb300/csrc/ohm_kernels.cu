@@ -2399,8 +2399,7 @@ __global__ void __launch_bounds__(1024) k_bottom(SmallDev<T> sm_all, double lamd
     }
 }
 
-// The same V-cycle over the lexicographic grids (float32, every extent a power of two) with the
-// grids held in shared memory: e, r, t and eta of every grid are staged once (r of the first grid
+// The same V-cycle over the lexicographic grids (float32) with the grids held in shared memory: e, r, t and eta of every grid are staged once (r of the first grid
 // and eta from global memory, e from zero), every pass of the cycle runs between two block
 // barriers, and only e of the first grid is written back.  The point update is the fused sweeps'
 // (face_pair flux divergence, Eqs. 8-10, and the relaxed diagonal formed from eta, Eqs. 21-23)
@@ -2420,28 +2419,38 @@ struct LexAcc {
 };
 
 struct LexDims {
-    int lx, ly, lz;  // log2 of the extents
-    __device__ __forceinline__ int n() const { return 1 << (lx + ly + lz); }
+    int nx, ny, nz;
+    int lx, ly;  // log2 of nx, ny when every extent is a power of two (p2)
+    bool p2;
+    __device__ __forceinline__ int n() const { return nx * ny * nz; }
+    __device__ __forceinline__ int id(int x, int y, int z) const { return (z * ny + y) * nx + x; }
     __device__ __forceinline__ void cell(int q, int &x, int &y, int &z) const {
-        x = q & ((1 << lx) - 1);
-        y = (q >> lx) & ((1 << ly) - 1);
-        z = q >> (lx + ly);
+        if (p2) {
+            x = q & (nx - 1);
+            y = (q >> lx) & (ny - 1);
+            z = q >> (lx + ly);
+        } else {
+            const int t = q / nx;
+            x = q - t * nx;
+            z = t / ny;
+            y = t - z * ny;
+        }
     }
     __device__ __forceinline__ LexAcc acc(const float *B, const float *E, int x, int y, int z) const {
-        const int mx = (1 << lx) - 1, my = (1 << ly) - 1, mz = (1 << lz) - 1;
         LexAcc a;
         a.fB = B;
         a.fE = E;
         a.n = n();
-        a.xo[0] = (x - 1) & mx;
+        const int pl = nx * ny;
+        a.xo[0] = x > 0 ? x - 1 : nx - 1;
         a.xo[1] = x;
-        a.xo[2] = (x + 1) & mx;
-        a.yo[0] = ((y - 1) & my) << lx;
-        a.yo[1] = y << lx;
-        a.yo[2] = ((y + 1) & my) << lx;
-        a.zo[0] = ((z - 1) & mz) << (lx + ly);
-        a.zo[1] = z << (lx + ly);
-        a.zo[2] = ((z + 1) & mz) << (lx + ly);
+        a.xo[2] = x + 1 < nx ? x + 1 : 0;
+        a.yo[0] = (y > 0 ? y - 1 : ny - 1) * nx;
+        a.yo[1] = y * nx;
+        a.yo[2] = (y + 1 < ny ? y + 1 : 0) * nx;
+        a.zo[0] = (z > 0 ? z - 1 : nz - 1) * pl;
+        a.zo[1] = z * pl;
+        a.zo[2] = (z + 1 < nz ? z + 1 : 0) * pl;
         return a;
     }
 };
@@ -2453,10 +2462,11 @@ struct BottomSm {  // no default member initialisers: a __shared__ copy is fille
     RbK<float> K[MAX_SMALL];      // update constants of grid s (the sweeps' relaxed diagonal, Eqs. 21-23)
 };
 
-// the i-th cell of colour `colour` ((x + y + z) & 1) of a grid with at least 2 cells along x
+// the i-th cell of colour `colour` ((x + y + z) & 1) of a power-of-two grid with at least 2
+// cells along x
 __device__ __forceinline__ void colour_cell(const LexDims &D, int i, int colour, int &x, int &y, int &z) {
     const int hx = D.lx - 1;
-    y = (i >> hx) & ((1 << D.ly) - 1);
+    y = (i >> hx) & (D.ny - 1);
     z = i >> (hx + D.ly);
     x = 2 * (i & ((1 << hx) - 1)) + ((y + z + colour) & 1);
 }
@@ -2468,16 +2478,19 @@ __device__ __forceinline__ void bsm_colour(const BottomSm &P, float *sh, int s, 
     const int n = D.n();
     float *e = sh + P.base[s], *r = e + 3 * n, *t = r + 3 * n, *E = t + 3 * n;
     const RbK<float> K = P.K[s];
-    const int ncol = D.lx >= 1 ? n / 2 : n;  // a grid one cell wide in x: every cell, colour checked
+    // power-of-two grids at least 2 cells wide in x enumerate the colour's cells; other grids
+    // visit every cell and skip the other colour
+    const bool half = D.p2 && D.nx >= 2;
+    const int ncol = half ? n / 2 : n;
     for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
         int x, y, z;
-        if (D.lx >= 1) {
+        if (half) {
             colour_cell(D, i, colour, x, y, z);
         } else {
             D.cell(i, x, y, z);
             if (((x + y + z) & 1) != colour) continue;
         }
-        const int q = (z << (D.lx + D.ly)) | (y << D.lx) | x;
+        const int q = D.id(x, y, z);
         const LexAcc a = D.acc(e, E, x, y, z);
         float es[6], den[3], dv[3];
         rb_faces_den<float>(a, K, es, den);
@@ -2489,13 +2502,13 @@ __device__ __forceinline__ void bsm_colour(const BottomSm &P, float *sh, int s, 
     __syncthreads();
     for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
         int x, y, z;
-        if (D.lx >= 1) {
+        if (half) {
             colour_cell(D, i, colour, x, y, z);
         } else {
             D.cell(i, x, y, z);
             if (((x + y + z) & 1) != colour) continue;
         }
-        const int q = (z << (D.lx + D.ly)) | (y << D.lx) | x;
+        const int q = D.id(x, y, z);
 #pragma unroll
         for (int c = 0; c < 3; c++) e[c * n + q] = v_add(e[c * n + q], t[c * n + q]);
     }
@@ -2555,7 +2568,7 @@ __global__ void __launch_bounds__(1024) k_bottom_sm(SmallDev<float> sm_all, Bott
             for (int dk = 0; dk < 2; dk++)
                 for (int dj = 0; dj < 2; dj++)
                     for (int di = 0; di < 2; di++)
-                        acc = v_add(acc, t[c * n + (((2 * z + dk) << (D.lx + D.ly)) | ((2 * y + dj) << D.lx) | (2 * x + di))]);
+                        acc = v_add(acc, t[c * n + D.id(2 * x + di, 2 * y + dj, 2 * z + dk)]);
             rc[q] = v_mul(acc, 0.125f);
             ec[q] = 0.f;
         }
@@ -2570,7 +2583,7 @@ __global__ void __launch_bounds__(1024) k_bottom_sm(SmallDev<float> sm_all, Bott
         const int n = D.n(), ncs = C.n();
         float *e = sh + P.base[s];
         const float *ec = sh + P.base[s + 1];
-        const int cmx = (1 << C.lx) - 1, cmy = (1 << C.ly) - 1, cmz = (1 << C.lz) - 1;
+
         for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {  // trilinear prolongation (weights 3/4, 1/4)
             const int c = q / n, fq = q - c * n;
             int x, y, z;
@@ -2582,8 +2595,11 @@ __global__ void __launch_bounds__(1024) k_bottom_sm(SmallDev<float> sm_all, Bott
                 for (int aj = 0; aj < 2; aj++)
                     for (int ai = 0; ai < 2; ai++) {
                         const float wt = (ai ? 0.25f : 0.75f) * (aj ? 0.25f : 0.75f) * (ak ? 0.25f : 0.75f);
-                        const int cx = (px + ai * sx) & cmx, cy = (py + aj * sy) & cmy, cz = (pz + ak * sz) & cmz;
-                        v = v_mad(wt, ec[c * ncs + ((cz << (C.lx + C.ly)) | (cy << C.lx) | cx)], v);
+                        int cx = px + ai * sx, cy = py + aj * sy, cz = pz + ak * sz;  // periodic wrap
+                        cx = cx < 0 ? cx + C.nx : (cx >= C.nx ? cx - C.nx : cx);
+                        cy = cy < 0 ? cy + C.ny : (cy >= C.ny ? cy - C.ny : cy);
+                        cz = cz < 0 ? cz + C.nz : (cz >= C.nz ? cz - C.nz : cz);
+                        v = v_mad(wt, ec[c * ncs + C.id(cx, cy, cz)], v);
                     }
             e[q] = v_add(e[q], v);
         }
@@ -2606,15 +2622,14 @@ static int ilog2_exact(int v) {
     return (1 << l) == v ? l : -1;
 }
 
-// the shared-memory solver's grid table and its shared-memory bytes; false when a grid extent
-// is not a power of two or the grids do not fit
+// the shared-memory solver's grid table and its shared-memory bytes; false when the grids do
+// not fit
 static bool bottom_table(const SmallDev<float> &sm, double lamdt, BottomSm &P, size_t &bytes) {
     P.n = sm.n;
     size_t off = 0;
     for (int q = 0; q < sm.n; q++) {
         const int lx = ilog2_exact(sm.dims[q][0]), ly = ilog2_exact(sm.dims[q][1]), lz = ilog2_exact(sm.dims[q][2]);
-        if (lx < 0 || ly < 0 || lz < 0) return false;
-        P.d[q] = LexDims{lx, ly, lz};
+        P.d[q] = LexDims{sm.dims[q][0], sm.dims[q][1], sm.dims[q][2], lx, ly, lx >= 0 && ly >= 0 && lz >= 0};
         P.base[q] = (int)off;
         P.K[q] = rb_constants<float>(lamdt, sm.h[q], sm.omega);
         off += 10 * (size_t)sm.dims[q][0] * sm.dims[q][1] * sm.dims[q][2];
@@ -2634,7 +2649,7 @@ template <typename T>
 cudaError_t launch_bottom(const SmallDev<T> &sm, double lamdt, int nu_pre, int nu_post, int n_coarse, cudaStream_t s) {
     if (sm.n == 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
-        // shared-memory solver when every extent is a power of two and the grids fit
+        // shared-memory solver when the grids fit
         BottomSm P;
         size_t bytes = 0;
         if (bottom_table(sm, lamdt, P, bytes)) {
