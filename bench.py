@@ -67,8 +67,10 @@ def args_parse():
                    help="batched512 / serving: FGMRES restart length of each instance's inner solve (0: defect correction)")
     p.add_argument("--requests", type=int, default=600, help="serving: requests in the stream")
     p.add_argument("--serve-nu-coarse", default="1,1", help="serving: pre,post sweeps on the grids coarser than level 0")
-    p.add_argument("--serve-max-batch", type=int, default=8, help="serving: slots per batched hierarchy")
-    p.add_argument("--serve-workers", type=int, default=6, help="serving: batches in flight (host threads, streams)")
+    p.add_argument("--serve-max-batch", type=int, default=2,
+                   help="serving: slots per batched hierarchy (a batch steps until its slowest member's step "
+                        "converges; with this stream's 100x spread of dt, 2 slots serve faster than 8)")
+    p.add_argument("--serve-workers", type=int, default=16, help="serving: batches in flight (host threads, streams)")
     p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     p.add_argument("--inner-tol", type=float, default=1e-5,
                    help="residual reduction asked of each float32 inner solve (mixed precision)")
