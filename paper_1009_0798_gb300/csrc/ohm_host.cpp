@@ -494,7 +494,7 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
                 want((void **)&H->kdots, K * (KMAX + 1) * sizeof(double));
                 want((void **)&H->binst, n * sizeof(int));
             } else {
-                want((void **)&H->kpart, ((n + 7) / 8) * (KMAX + 1) * sizeof(double));
+                want((void **)&H->kpart, ((n + 1) / 2) * (KMAX + 1) * sizeof(double));  // per block pair
                 want((void **)&H->kdots, (KMAX + 1) * sizeof(double));
             }
             // batches: the FGMRES scalars of every instance on the device
@@ -1181,6 +1181,26 @@ int apply_L32(ohm_hier *H, float *x, const float *y, double a, double c, double 
                                      (const float *)H->ghostEtaT, a, c, d, out, (float *)nullptr, false);
 }
 
+// w = L z with its products <w, v_i> (i < S.k) and <w, w>: in one pass on block pairs where the
+// hierarchy is one brick grid, else the operator followed by the multi-dot.
+int apply_mdot(ohm_hier *H, const float *z, float *w, const VecSet &S, double lamdt, double *out) {
+    const HGrid &g = H->amr[0];
+    if (H->nlev == 1 && g.brick && !H->batched) {
+        LAUNCH(H, OHM_K_COMPOSITE, g.n(),
+               launch_pair_apply_dots(gdev(H, g), z, (const float *)H->amrbuf.eta, lamdt / (2.0 * g.h * g.h), w, S,
+                                      g.h * g.h * g.h, H->kpart, H->kdots, H->hnorm_dev ? H->hnorm_dev + 8 : nullptr,
+                                      H->s));
+        if (!H->hnorm_dev)
+            CK(cudaMemcpyAsync(H->hdots, H->kdots, (S.k + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+        CK(cudaStreamSynchronize(H->s));
+        memcpy(out, H->hdots, (S.k + 1) * sizeof(double));
+        return OHM_OK;
+    }
+    int st;
+    if ((st = apply_L32(H, const_cast<float *>(z), nullptr, 1.0, lamdt, 0.0, w, lamdt))) return st;
+    return mdot(H, w, S, out);
+}
+
 // Float32 inner solve of L x = rout by FGMRES(m) (Saad 1993), right-preconditioned by one
 // V-cycle per Arnoldi step, classical Gram-Schmidt in the leaf-volume inner product, Givens
 // rotations on the host, restarts from the true residual.  Stops when the residual has
@@ -1219,11 +1239,10 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             if (st) return st;
             (*cycles)++;
             // w = L z_j, orthogonalised against v_0..v_j
-            if ((st = apply_L32(H, H->kz[j], nullptr, 1.0, lamdt, 0.0, H->kv[j + 1], lamdt))) return st;
             VecSet S;
             S.k = j + 1;
             for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
-            if ((st = mdot(H, H->kv[j + 1], S, nn))) return st;
+            if ((st = apply_mdot(H, H->kz[j], H->kv[j + 1], S, lamdt, nn))) return st;
             double proj = 0.0;
             for (int i = 0; i <= j; i++) {
                 h(i, j) = nn[i];

@@ -220,6 +220,12 @@ struct VecSet {
 // launches return at once and out is left as it was.
 cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int nblk, double *part, double *out,
                         cudaStream_t s, const int *gate = nullptr, double *host_out = nullptr);
+// w = X + kc divF(X) on the block pairs of a single-level brick grid (launch_pair_op's operator)
+// with out[0..k-1] = <w, v_i> and out[k] = <w, w>, every cell weighted by wt; part: scratch of
+// (nblk / 2) * (k + 1) doubles; host_out as for launch_mdot
+cudaError_t launch_pair_apply_dots(const GridDev &g, const float *X, const float *eta, double kc, float *w,
+                                   const VecSet &V, double wt, double *part, double *out, double *host_out,
+                                   cudaStream_t s);
 
 // dst = (src - sum c_i v_i) * scale
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s);

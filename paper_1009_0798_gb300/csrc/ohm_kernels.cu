@@ -1252,10 +1252,15 @@ struct G18 {
     __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
 };
 
-template <bool APPLY, bool RESTRICT>
-__global__ void __launch_bounds__(512, 4) k_pair_op(GridDev g, const float *__restrict__ X, const float *__restrict__ Y,
-                                                 const float *__restrict__ eta, float kc, float *__restrict__ out,
-                                                 float *__restrict__ coarse) {
+// NV >= 0 (APPLY only): also the FGMRES products of the output w with the NV vectors of V and
+// with itself, <w, v_i> and <w, w>, each weighted by wt (h^3 for the cells of a single-level
+// grid) and folded per block pair in a fixed order into part[i][pair] (column-major, so that
+// the column sums read contiguous rows).
+template <bool APPLY, bool RESTRICT, int NV = -1>
+__global__ void __launch_bounds__(512, NV >= 0 ? 3 : 4)
+    k_pair_op(GridDev g, const float *__restrict__ X, const float *__restrict__ Y, const float *__restrict__ eta, float kc,
+              float *__restrict__ out, float *__restrict__ coarse, VecSet V = VecSet(), double wt = 0.0,
+              double *__restrict__ part = nullptr) {
     using G = G18;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tB = reinterpret_cast<float *>(smem_raw);  // [3][10 planes][10 rows][RRS]
@@ -1297,6 +1302,10 @@ __global__ void __launch_bounds__(512, 4) k_pair_op(GridDev g, const float *__re
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x = lane & 7, y = 2 * (w & 3) + ((lane >> 3) & 1), z = 2 * ((w >> 2) & 3) + (lane >> 4);
     const int cell = (z * 8 + y) * 8 + x;
+    constexpr int ND = NV >= 0 ? NV + 1 : 1;
+    float dots[ND];
+#pragma unroll
+    for (int i = 0; i < ND; i++) dots[i] = 0.f;
 #pragma unroll
     for (int h = 0; h < 2; h++) {  // the same cell of block A, then of block B
         const int b = A + h;
@@ -1311,6 +1320,11 @@ __global__ void __launch_bounds__(512, 4) k_pair_op(GridDev g, const float *__re
             const size_t id = ((size_t)b * 3 + c) * B3 + cell;
             o[c] = v_mad(kc, dv[c], APPLY ? ev[c] : v_sub(Y[id], ev[c]));
             if (out) out[id] = o[c];
+            if constexpr (NV >= 0) {
+#pragma unroll
+                for (int i = 0; i < NV; i++) dots[i] = fmaf(o[c], __ldg(V.v[i] + id), dots[i]);
+                dots[NV] = fmaf(o[c], o[c], dots[NV]);
+            }
         }
         if constexpr (RESTRICT) {
             const int oct = b & 7, pb = b >> 3;
@@ -1322,6 +1336,22 @@ __global__ void __launch_bounds__(512, 4) k_pair_op(GridDev g, const float *__re
                 sum = v_add(sum, __shfl_xor_sync(0xffffffffu, sum, 16));
                 if ((lane & 0x19) == 0) coarse[((size_t)pb * 3 + c) * B3 + (cz * 8 + cy) * 8 + cx] = v_mul(sum, 0.125f);
             }
+        }
+    }
+    if constexpr (NV >= 0) {  // warp sums, then the 16 warps in order (the tile is free by now)
+        __syncthreads();
+        double *sred = reinterpret_cast<double *>(smem_raw);  // [16][NV + 1]
+#pragma unroll
+        for (int i = 0; i <= NV; i++) {
+            float v = dots[i];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sred[w * (NV + 1) + i] = (double)v;
+        }
+        __syncthreads();
+        if (threadIdx.x <= NV) {
+            double a = 0.0;
+            for (int q = 0; q < 16; q++) a += sred[q * (NV + 1) + threadIdx.x];
+            part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = a * wt;
         }
     }
 }
@@ -2145,6 +2175,42 @@ cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int n
     OHM_NV_SWITCH(V.k, OHM_MDOT)
 #undef OHM_MDOT
     k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out, gate, host_out);
+    return cudaGetLastError();
+}
+
+// column sums of part[ncol][nrow] (column-major) in a fixed order, one thread block per column
+__global__ void __launch_bounds__(1024) k_colsum_cm(const double *__restrict__ part, int nrow, double *__restrict__ out,
+                                                    double *__restrict__ host_out) {
+    __shared__ double red[32];
+    const double *col = part + (size_t)blockIdx.x * nrow;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nrow; b += blockDim.x) a += col[b];
+    const double s = block_sum(a, red);
+    if (threadIdx.x == 0) {
+        out[blockIdx.x] = s;
+        if (host_out) host_out[blockIdx.x] = s;  // mapped pinned host memory
+    }
+}
+
+// w = L z on block pairs (the float32 operator of the inner solve) together with <w, v_i> and
+// <w, w> of the FGMRES Arnoldi step: one pass instead of the operator and the multi-dot
+cudaError_t launch_pair_apply_dots(const GridDev &g, const float *X, const float *eta, double kc, float *w,
+                                   const VecSet &V, double wt, double *part, double *out, double *host_out,
+                                   cudaStream_t s) {
+    if (g.nblk == 0) return cudaSuccess;
+    const size_t sm = 4 * G18::CS * sizeof(float);
+    const int npair = g.nblk / 2;
+#define OHM_PAIRDOT(N)                                                                                          \
+    {                                                                                                          \
+        static const bool attr_ =                                                                              \
+            (cudaFuncSetAttribute(k_pair_op<true, false, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), \
+             true);                                                                                            \
+        (void)attr_;                                                                                           \
+        k_pair_op<true, false, N><<<npair, 512, sm, s>>>(g, X, nullptr, eta, (float)kc, w, nullptr, V, wt, part);  \
+    }
+    OHM_NV_SWITCH(V.k, OHM_PAIRDOT)
+#undef OHM_PAIRDOT
+    k_colsum_cm<<<V.k + 1, 1024, 0, s>>>(part, npair, out, host_out);
     return cudaGetLastError();
 }
 
