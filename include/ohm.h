@@ -125,8 +125,9 @@ typedef struct {
 /* Builds the block tables, the multigrid grids below level 0 (coarsened by 2 while every
  * dimension is even and >= 4) and allocates all device scratch.  *out receives the handle
  * (NULL on failure).  Any base grid of multiples of 8 is accepted: the coarse grids below the
- * last one made of 8^3 blocks are stepped by grid-wide launches while they have more than 16384
- * cells and by a one-thread-block solver below that. */
+ * last one made of 8^3 blocks (under OHM_MIXED* also power-of-two grids of at most 16^3
+ * cells) are stepped by grid-wide launches while they have more than 16384 cells and by a
+ * one-thread-block solver below that (in shared memory where the grids fit). */
 int ohm_create_hierarchy(const ohm_hier_desc *d, ohm_hier **out);
 
 /* Copies eta (> 0 and finite, [nblocks][8][8][8], every block including covered ones) into
@@ -222,8 +223,8 @@ int ohm_op_sync_down(ohm_hier *h, double *B_dev);
 int ohm_op_vcycle(ohm_hier *h, const double *R_dev, double dt, double *e_dev);
 
 /* Shape of base multigrid grid m (0 = level 0): dims[3] cells, *nblocks its 8^3 blocks
- * (0 when the grid is not a multiple of 8 and lives in lexicographic [comp][z][y][x]
- * layout inside the coarsest-grid solver); when ijk is not NULL it receives 3 int32 per
+ * (0 when the grid lives in lexicographic [comp][z][y][x] layout inside the coarsest-grid
+ * solver: not a multiple of 8, or under OHM_MIXED* a power-of-two grid of at most 16^3 cells); when ijk is not NULL it receives 3 int32 per
  * block (bi, bj, bk) in the grid's storage order (the caller's order for m = 0). */
 int ohm_mg_grid_info(ohm_hier *h, int m, int32_t dims[3], int64_t *nblocks, int32_t *ijk);
 
