@@ -263,6 +263,17 @@ int ohm_op_grid_resid_restrict_f32(ohm_hier *h, int m, const float *e_dev, const
                                    double dt, float *t_dev, float *coarse_dev);
 int ohm_op_grid_prolong_add_f32(ohm_hier *h, int m, const float *coarse_dev, float *fine_dev);
 
+/* The coarsest-grid solve of the float32 inner solve (Secs. 2.2-2.3): the V-cycle over the
+ * lexicographic grids below the last blocked one, from e = 0, for the right-hand side r_dev on
+ * the first of them, with the hierarchy's sweep counts for the grids coarser than level 0
+ * (nu_coarse_pre / nu_coarse_post when set, else nu_pre / nu_post), n_coarse sweeps on the
+ * coarsest grid and omega.  r_dev and e_dev are float32 [3][nz][ny][nx] and eta_dev float32
+ * [nz][ny][nx] on that grid (the coarser grids take the mean of the 8 children, Sec. 2.2); the
+ * launches are those of a V-cycle there (the shared-memory solver where the grids fit).  The
+ * hierarchy's own eta-derived data are rebuilt by the next ohm_set_eta.  OHM_MIXED* hierarchies
+ * of one instance. */
+int ohm_op_coarsest_f32(ohm_hier *h, const float *r_dev, const float *eta_dev, double dt, float *e_dev);
+
 /* out = L X = X + lambda dt div F(X) (Eq. 13) on leaf blocks, in float32: the operator the
  * float32 inner solve applies (covered cells of a private copy of X set to the mean of their
  * children, coarse-fine ghosts interpolated from the parent level, refluxing through float64

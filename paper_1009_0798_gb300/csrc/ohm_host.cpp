@@ -2327,6 +2327,30 @@ int ohm_op_grid_prolong_add_f32(ohm_hier *h, int m, const float *coarse_dev, flo
     return OHM_OK;
 }
 
+int ohm_op_coarsest_f32(ohm_hier *h, const float *r_dev, const float *eta_dev, double dt, float *e_dev) {
+    if (!h || h->batched || !h->mixed || !r_dev || !eta_dev || !e_dev || !(dt > 0) || h->small.empty())
+        return OHM_ERR_INVALID;
+    const auto &d0 = h->small[0];
+    const size_t n0 = (size_t)d0[0] * d0[1] * d0[2];
+    const double lamdt = h->d.lambda * dt;
+    CK(cudaMemcpyAsync(h->smallbuf[0].r, r_dev, 3 * n0 * sizeof(float), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(h->smallbuf[0].eta, eta_dev, n0 * sizeof(float), cudaMemcpyDeviceToDevice, h->s));
+    SmallDev<float> sm = small_dev<float>(h);
+    CK(launch_small_setup<float>(sm, 0.0, true, h->s));     // eta of the coarser grids
+    CK(launch_small_setup<float>(sm, lamdt, false, h->s));  // inverse diagonals (paths that read them)
+    h->eta_set = false;
+    h->inv_dt = NAN;
+    const ohm_hier_desc &d = h->d;
+    const bool csb = d.nu_coarse_pre || d.nu_coarse_post;
+    int st;
+    if ((st = small_vcycle<float>(h, lamdt, csb ? d.nu_coarse_pre : d.nu_pre, csb ? d.nu_coarse_post : d.nu_post,
+                                  d.n_coarse)))
+        return st;
+    CK(cudaMemcpyAsync(e_dev, h->smallbuf[0].e, 3 * n0 * sizeof(float), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return OHM_OK;
+}
+
 int ohm_op_apply_L_f32(ohm_hier *h, const float *X_dev, double dt, float *out_dev) {
     if (!h || h->batched || !h->mixed || !X_dev || !out_dev || !(dt > 0) || !h->eta_set) return OHM_ERR_INVALID;
     const size_t bytes = (size_t)h->nblocks * 3 * B3 * sizeof(float);

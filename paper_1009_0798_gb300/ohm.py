@@ -86,6 +86,7 @@ def lib():
         L.ohm_op_grid_resid_restrict_f32.argtypes = [vp, C.c_int, vp, vp, vp, dp, vp, vp]
         L.ohm_op_grid_prolong_add_f32.argtypes = [vp, C.c_int, vp, vp]
         L.ohm_op_apply_L_f32.argtypes = [vp, vp, dp, vp]
+        L.ohm_op_coarsest_f32.argtypes = [vp, vp, vp, dp, vp]
         L.ohm_prof_enable.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ohm_prof_read.argtypes = [vp, C.POINTER(dp), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.ohm_launch_count.argtypes = [vp]
@@ -327,6 +328,11 @@ def ohm_op_grid_resid_restrict_f32(h: Hierarchy, m: int, e, r, eta, dt: float, t
 def ohm_op_grid_prolong_add_f32(h: Hierarchy, m: int, coarse, fine) -> None:
     _check(lib().ohm_op_grid_prolong_add_f32(h.handle, m, _ptr32(coarse, "coarse"), _ptr32(fine, "fine")),
            "ohm_op_grid_prolong_add_f32")
+
+
+def ohm_op_coarsest_f32(h: Hierarchy, r, eta, dt: float, e) -> None:
+    _check(lib().ohm_op_coarsest_f32(h.handle, _ptr32(r, "r"), _ptr32(eta, "eta"), float(dt), _ptr32(e, "e")),
+           "ohm_op_coarsest_f32")
 
 
 def ohm_op_apply_L_f32(h: Hierarchy, X, dt: float, out) -> None:

@@ -9,10 +9,13 @@ that grid) and to the oracle's FP64 restatement of the step, and compares elemen
   e + omega (e_GS - e);
 * the same sweep on single blocks (`k_smooth_rb`, a grid whose blocks do not pair along x) and
   as two colour passes (`k_smooth<float>`);
-* residual + restriction (`k_resid_restrict<float>`) into a blocked and a lexicographic
-  coarse grid, and prolongation (`k_prolong_add8<float>`, `k_prolong_add<float>`), Sec. 2.2;
-* the float32 composite operator L X (`k_composite<float,float>`, with coarse-fine ghosts and
-  refluxing) on uniform and 3-level AMR hierarchies.
+* residual + restriction into a blocked coarse grid (`k_pair_op` on block pairs) and into a
+  lexicographic one (`k_resid_restrict<float>`), and prolongation (`k_prolong_add8<float>`,
+  `k_prolong_add<float>`), Sec. 2.2;
+* the float32 operator L X on a uniform hierarchy (`k_pair_op`) and on a 3-level AMR hierarchy
+  (`k_composite<float,float>`, with coarse-fine ghosts and refluxing);
+* the coarsest-grid solve (`k_bottom_sm`, with the grid-wide steps before it where a grid is
+  large) against the same V-cycle composed from the oracle's grid passes.
 
 Tolerance.  Inputs are O(1) normal fields and eta = 10^U(-0.5, 0.5) per cell, dt = 5 h^2 (so
 1 + alpha is about 10-30).  Both sides start from the same float32 values; the oracle works in
@@ -191,3 +194,56 @@ def test_float32_operator_matches_oracle(ohm, orc, name):
     leaf = h.is_leaf()
     assert np.all(got[~leaf] == 0.0)
     check32(got[leaf], want[leaf], f"operator {name}")
+
+
+def oracle_coarse_vcycle(o, m0, r, eta0, dt, nu1, nu2, nc, omega):
+    """The V-cycle of the coarsest-grid solver over oracle grids m0 .. n_mg - 1 (Sec. 2.2):
+    from e = 0, nu1 relaxed red-black sweeps, residual restricted to the next grid, nc sweeps on
+    the coarsest, trilinear prolongation and nu2 sweeps on the way up; eta of each coarser grid
+    the mean of its 8 children."""
+    last = o.n_mg - 1
+    etas = {m0: eta0}
+    for m in range(m0, last):
+        etas[m + 1] = o.grid_restrict(m, etas[m], 1)
+    es, rs = {}, {m0: r}
+    for m in range(m0, last):
+        e = np.zeros_like(rs[m])
+        for _ in range(nu1):
+            e = oracle_sweep(o, m, e, rs[m], etas[m], dt, omega)
+        es[m] = e
+        rs[m + 1] = o.grid_restrict(m, o.grid_residual(m, e, rs[m], etas[m], dt), 3)
+    e = np.zeros_like(rs[last])
+    for _ in range(nc):
+        e = oracle_sweep(o, last, e, rs[last], etas[last], dt, omega)
+    for m in range(last - 1, m0 - 1, -1):
+        e = o.grid_prolong_add(m, e, es[m])
+        for _ in range(nu2):
+            e = oracle_sweep(o, m, e, rs[m], etas[m], dt, omega)
+    return e
+
+
+# 32^3: power-of-two grids 16^3 .. 2^3 in the shared-memory solver; 48 x 24 x 24: 24 x 12 x 12,
+# 12 x 6 x 6 and 6 x 3 x 3 (other extents); 56^3: 28^3 stepped grid-wide (more than 16384 cells),
+# then 14^3 and 7^3 in shared memory
+COARSE_BASES = [(32, 32, 32), (48, 24, 24), (56, 56, 56)]
+
+
+@pytest.mark.parametrize("base", COARSE_BASES)
+@pytest.mark.parametrize("omega", [1.0, 1.2])
+def test_float32_coarsest_grid_solve_matches_oracle_vcycle(ohm, orc, base, omega):
+    """`ohm_op_coarsest_f32` (the coarsest-grid solver of the float32 inner solve, V(2,2) with 4
+    coarsest sweeps here) against the same V-cycle composed from the oracle's grid passes, at the
+    single-pass tolerance (measured: about 5e-8 relative L2, 4e-7 x rms in the worst element)."""
+    h = W.uniform(*base, 1.0 / base[0])
+    o = orc.Oracle(h, 0.5)
+    g = mixed(ohm, h, omega)
+    m0 = last_blocked(ohm, g) + 1
+    dims, nb, _ = ohm.ohm_mg_grid_info(g, m0)
+    assert nb == 0
+    _, r, eta = grid_inputs(dims, 90 + base[1])
+    dt = 5.0 * h.dx0 ** 2
+    e = torch.full((3 * dims[0] * dims[1] * dims[2],), float("nan"), dtype=torch.float32, device="cuda")
+    ohm.ohm_op_coarsest_f32(g, f32(r)[0], f32(eta)[0], dt, e)
+    got = host(e).reshape(r.shape)
+    want = oracle_coarse_vcycle(o, m0, r, eta[0], dt, 2, 2, 4, omega if omega else 1.0)
+    check32(got, want, f"coarsest solve {base} omega={omega}: grid {dims}")
