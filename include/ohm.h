@@ -78,11 +78,14 @@ typedef struct {
                                    nu_coarse_pre / nu_coarse_post are set                      */
     int32_t n_coarse;           /* red-black sweeps on the coarsest grid (>= 1)               */
     int32_t max_outer;          /* V-cycles allowed per step (>= 1)                           */
-    int32_t krylov;             /* OHM_MIXED(_FF) only: 0 = the float32 inner solve is defect
-                                   correction with the V-cycle (Eqs. 16-18); m in 1..11 = it is
-                                   FGMRES(m) right-preconditioned by the same V-cycle (not in
-                                   the paper; same converged solution, fewer cycles).  Must be
-                                   0 for OHM_FP64.                                              */
+    int32_t krylov;             /* 0 = the paper's defect correction with the V-cycle (Eqs.
+                                   16-18: the float32 inner solve of mixed precision, or one
+                                   float64 V-cycle per outer iteration); m in 1..11 = FGMRES(m)
+                                   right-preconditioned by the same V-cycle (not in the paper;
+                                   same converged solution, fewer cycles): the float32 inner
+                                   solve of mixed precision, or under OHM_FP64 one float64
+                                   FGMRES solve to the step's tolerance per outer iteration
+                                   (batched hierarchies: mixed precision only).                 */
     double inner_tol;           /* OHM_MIXED(_FF): each float32 inner solve reduces its residual by
                                    max(inner_tol, 0.3 tol / current ||R||/||S||); 0 selects
                                    1e-5.  Values below ~1e-6 ask more than float32 can give: the

@@ -480,13 +480,15 @@ int allocate(ohm_hier *H, std::string &err, int64_t *dry_bytes = nullptr) {
     want(&H->ghostE, (size_t)H->nslot * 3 * T3 * tsz);
     if (H->mixed) want(&H->ghostEtaT, (size_t)H->nslot * T3 * tsz);
     want(&H->amrbuf.r, n * 3 * B3 * tsz);
-    if (H->mixed) {
-        want(&H->rout, n * 3 * B3 * tsz);
-        want(&H->eacc, n * 3 * B3 * tsz);
+    if (H->mixed) want(&H->rout, n * 3 * B3 * tsz);
+    // the inner correction: float32 under mixed precision, float64 for the FP64 FGMRES
+    if (H->mixed || H->d.krylov > 0) want(&H->eacc, n * 3 * B3 * tsz);
+    {
         const int m = H->d.krylov;
         if (m > 0) {
-            for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * sizeof(float));
-            for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * sizeof(float));
+            // Arnoldi basis and preconditioned vectors in the multigrid's precision
+            for (int i = 0; i <= m; i++) want((void **)&H->kv[i], n * 3 * B3 * tsz);
+            for (int i = 0; i < m; i++) want((void **)&H->kz[i], n * 3 * B3 * tsz);
             want((void **)&H->wblk, n * sizeof(double));
             const size_t K = (size_t)H->K;
             if (H->batched) {
@@ -1104,6 +1106,9 @@ int update_all(ohm_hier *H, double *B, const T *e, const uint8_t *imask = nullpt
 }
 
 template <typename T>
+int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles);
+
+template <typename T>
 int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *stats) {
     const double lam = H->d.lambda, lamdt = lam * dt;
     int st;
@@ -1134,11 +1139,19 @@ int cn_step_impl(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats *
             result = tol >= 0 ? OHM_ERR_NOT_CONVERGED : OHM_OK;
             break;
         }
-        if ((st = vcycle<T>(H, lamdt))) return st;
-        if ((st = update_all<T>(H, B, (const T *)H->amrbuf.e))) return st;
+        if (H->d.krylov > 0) {
+            // FGMRES in float64, right-preconditioned by the V-cycle, to the tolerance in one
+            // solve (no float32 limit to stop at); `it` counts its V-cycles
+            const double target = tol >= 0 ? 0.3 * tol / std::max(nr[0], 1e-300) : 0.0;
+            if ((st = inner_fgmres<T>(H, lamdt, target, &it))) return st;
+            if ((st = update_all<T>(H, B, (const T *)H->eacc))) return st;
+        } else {
+            if ((st = vcycle<T>(H, lamdt))) return st;
+            if ((st = update_all<T>(H, B, (const T *)H->amrbuf.e))) return st;
+            it++;
+        }
         if ((st = sync_down(H, B))) return st;
         if ((st = fill_ghosts_B(H, B))) return st;
-        it++;
     }
     if (stats) {
         stats->cycles = it;
@@ -1181,6 +1194,50 @@ int apply_L32(ohm_hier *H, float *x, const float *y, double a, double c, double 
                                      (const float *)H->ghostEtaT, a, c, d, out, (float *)nullptr, false);
 }
 
+// float64 counterparts of the Krylov helpers (the FP64 FGMRES)
+template <typename T>
+struct VecSetSel {
+    using type = VecSet;
+};
+template <>
+struct VecSetSel<double> {
+    using type = VecSetD;
+};
+template <typename T>
+using VecSetOf = typename VecSetSel<T>::type;
+
+int mdot(ohm_hier *H, const double *w, const VecSetD &S, double *out) {
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_mdot(w, S, H->wblk, (int)H->nblocks, H->kpart, H->kdots, H->s,
+                                                         H->hnorm_dev ? H->hnorm_dev + 8 : nullptr));
+    if (!H->hnorm_dev)
+        CK(cudaMemcpyAsync(H->hdots, H->kdots, (S.k + 1) * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    CK(cudaStreamSynchronize(H->s));
+    memcpy(out, H->hdots, (S.k + 1) * sizeof(double));
+    return OHM_OK;
+}
+
+// out = a x + c divF(x) + d y for a float64 correction field (ghosts of x, the state's eta)
+int apply_L64(ohm_hier *H, double *x, const double *y, double a, double c, double d, double *out) {
+    int st;
+    if ((st = sync_down_t<double>(H, x))) return st;
+    if ((st = fill_ghosts_t<double>(H, x, (double *)H->ghostE))) return st;
+    return composite_t<double, double>(H, x, y, H->eta64, (const double *)H->ghostE, H->ghostEta64, a, c, d, out,
+                                       (double *)nullptr, false);
+}
+
+int apply_Lt(ohm_hier *H, float *x, const float *y, double a, double c, double d, float *out, double lamdt) {
+    return apply_L32(H, x, y, a, c, d, out, lamdt);
+}
+int apply_Lt(ohm_hier *H, double *x, const double *y, double a, double c, double d, double *out, double) {
+    return apply_L64(H, x, y, a, c, d, out);
+}
+
+int apply_mdot(ohm_hier *H, const double *z, double *w, const VecSetD &S, double lamdt, double *out) {
+    int st;
+    if ((st = apply_L64(H, const_cast<double *>(z), nullptr, 1.0, lamdt, 0.0, w))) return st;
+    return mdot(H, w, S, out);
+}
+
 // w = L z with its products <w, v_i> (i < S.k) and <w, w>: in one pass on block pairs where the
 // hierarchy is one brick grid, else the operator followed by the multi-dot.
 int apply_mdot(ohm_hier *H, const float *z, float *w, const VecSet &S, double lamdt, double *out) {
@@ -1201,25 +1258,29 @@ int apply_mdot(ohm_hier *H, const float *z, float *w, const VecSet &S, double la
     return mdot(H, w, S, out);
 }
 
-// Float32 inner solve of L x = rout by FGMRES(m) (Saad 1993), right-preconditioned by one
-// V-cycle per Arnoldi step, classical Gram-Schmidt in the leaf-volume inner product, Givens
-// rotations on the host, restarts from the true residual.  Stops when the residual has
-// dropped by `target`, when a whole restart cycle gained less than a factor 2 (float32 has
-// nothing more to give), or when the step's V-cycle budget is used.  x is left in eacc.
+// Inner solve of L x = R by FGMRES(m) (Saad 1993), right-preconditioned by one V-cycle per
+// Arnoldi step, classical Gram-Schmidt in the leaf-volume inner product, Givens rotations on
+// the host, restarts from the true residual: in float32 for mixed precision (R = rout, the
+// float32 copy of the outer residual), in float64 for OHM_FP64 (R = the float64 residual).
+// Stops when the residual has dropped by `target`, when a whole restart cycle gained less than
+// a factor 2 (float32 has nothing more to give), or when the step's V-cycle budget is used.  x
+// is left in eacc.
+template <typename T>
 int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
     const int m = H->d.krylov;
     const size_t nel = (size_t)H->nblocks * 3 * B3;
-    float *x = (float *)H->eacc, *rhs = (float *)H->rout;
+    // right-hand side: the float32 copy of the outer residual, or the float64 residual itself
+    T *x = (T *)H->eacc, *rhs = (T *)(std::is_same<T, float>::value ? H->rout : H->amrbuf.r);
     int st;
-    CK(cudaMemsetAsync(x, 0, nel * sizeof(float), H->s));
+    CK(cudaMemsetAsync(x, 0, nel * sizeof(T), H->s));
     double nn[KMAX + 1];
-    VecSet none;
+    VecSetOf<T> none;
     none.k = 0;
     if ((st = mdot(H, rhs, none, nn))) return st;
     const double beta0 = std::sqrt(nn[0]);
     if (!(beta0 > 0) || !std::isfinite(beta0)) return OHM_OK;
     double beta = beta0, beta_restart = beta0;
-    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[0], rhs, none, (float)(1.0 / beta), nel, H->s));
+    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[0], rhs, none, (T)(1.0 / beta), nel, H->s));
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     auto h = [&](int i, int j) -> double & { return Hm[(size_t)i * m + j]; };
     for (;;) {
@@ -1233,20 +1294,20 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             void *r_save = H->amrbuf.r, *e_save = H->amrbuf.e;
             H->amrbuf.r = H->kv[j];
             H->amrbuf.e = H->kz[j];
-            st = vcycle<float>(H, lamdt);
+            st = vcycle<T>(H, lamdt);
             H->amrbuf.r = r_save;
             H->amrbuf.e = e_save;
             if (st) return st;
             (*cycles)++;
             // w = L z_j, orthogonalised against v_0..v_j
-            VecSet S;
+            VecSetOf<T> S;
             S.k = j + 1;
-            for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
-            if ((st = apply_mdot(H, H->kz[j], H->kv[j + 1], S, lamdt, nn))) return st;
+            for (int i = 0; i <= j; i++) S.v[i] = (const T *)H->kv[i];
+            if ((st = apply_mdot(H, (const T *)H->kz[j], (T *)H->kv[j + 1], S, lamdt, nn))) return st;
             double proj = 0.0;
             for (int i = 0; i <= j; i++) {
                 h(i, j) = nn[i];
-                S.c[i] = (float)nn[i];
+                S.c[i] = (T)nn[i];
                 proj += nn[i] * nn[i];
             }
             // ||w - sum h_i v_i||^2 = <w,w> - sum h_i^2 for orthonormal v_i: when that keeps more
@@ -1256,12 +1317,12 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             double hn;
             if (ww - proj > 0.01 * ww) {
                 hn = std::sqrt(ww - proj);
-                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, (float)(1.0 / hn), nel, H->s));
+                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], S, (T)(1.0 / hn), nel, H->s));
             } else {
-                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[j + 1], H->kv[j + 1], S, 1.0f, nel, H->s));
-                if ((st = mdot(H, H->kv[j + 1], none, nn))) return st;
+                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], S, T(1), nel, H->s));
+                if ((st = mdot(H, (const T *)H->kv[j + 1], none, nn))) return st;
                 hn = std::sqrt(std::max(nn[0], 0.0));
-                if (hn > 0) LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[j + 1], H->kv[j + 1], none, (float)(1.0 / hn), nel, H->s));
+                if (hn > 0) LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], none, (T)(1.0 / hn), nel, H->s));
             }
             h(j + 1, j) = hn;
             // Givens rotations
@@ -1290,22 +1351,22 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             y[i] = h(i, i) != 0 ? s / h(i, i) : 0.0;
         }
         if (jend > 0) {
-            VecSet Z;
+            VecSetOf<T> Z;
             Z.k = jend;
             for (int i = 0; i < jend; i++) {
-                Z.v[i] = H->kz[i];
-                Z.c[i] = (float)(-y[i]);
+                Z.v[i] = (const T *)H->kz[i];
+                Z.c[i] = (T)(-y[i]);
             }
-            LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(x, x, Z, 1.0f, nel, H->s));
+            LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(x, x, Z, T(1), nel, H->s));
         }
         if (done || *cycles >= H->d.max_outer || jend == 0) break;
         // restart from the true residual rhs - L x
-        if ((st = apply_L32(H, x, rhs, -1.0, -lamdt, 1.0, H->kv[0], lamdt))) return st;
-        if ((st = mdot(H, H->kv[0], none, nn))) return st;
+        if ((st = apply_Lt(H, x, rhs, -1.0, -lamdt, 1.0, (T *)H->kv[0], lamdt))) return st;
+        if ((st = mdot(H, (const T *)H->kv[0], none, nn))) return st;
         beta = std::sqrt(std::max(nn[0], 0.0));
         if (beta <= target * beta0 || !(beta > 0) || beta > 0.5 * beta_restart) break;
         beta_restart = beta;
-        LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(H->kv[0], H->kv[0], none, (float)(1.0 / beta), nel, H->s));
+        LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[0], (T *)H->kv[0], none, (T)(1.0 / beta), nel, H->s));
     }
     return OHM_OK;
 }
@@ -1355,7 +1416,7 @@ int cn_step_mixed(ohm_hier *H, double *B, double dt, double tol, ohm_step_stats 
         const double target = tol >= 0 ? std::max(fl, 0.3 * tol / std::max(nr[0], 1e-300)) : fl;
         ff = H->ff_mid && !(tol >= 0 && nr[0] * target <= tol);
         if (H->d.krylov > 0) {
-            if ((st = inner_fgmres(H, lamdt, target, &cycles))) return st;
+            if ((st = inner_fgmres<float>(H, lamdt, target, &cycles))) return st;
         } else {
         CK(cudaMemsetAsync(eacc, 0, nbytes, H->s));
         double prev = 1.0;
@@ -1774,8 +1835,8 @@ bool valid_desc(const ohm_hier_desc *d, std::string &err) {
     if (d->nu_pre < 0 || d->nu_post < 0 || d->n_coarse < 1 || d->max_outer < 1) { err = "bad cycle counts"; return false; }
     if (!(d->omega == 0 || (d->omega > 0 && d->omega < 2))) { err = "omega must be 0 (= 1) or in (0, 2)"; return false; }
     if (d->nu_coarse_pre < 0 || d->nu_coarse_post < 0) { err = "bad coarse-grid sweep counts"; return false; }
-    if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision == OHM_FP64)) {
-        err = "krylov must be 0, or 1..11 with OHM_MIXED or OHM_MIXED_FF";
+    if (d->krylov < 0 || d->krylov >= KMAX || (d->krylov > 0 && d->precision == OHM_FP64 && d->n_instances >= 1)) {
+        err = "krylov must be 0, or 1..11 (batched hierarchies: with mixed precision only)";
         return false;
     }
     if (!(d->inner_tol >= 0 && d->inner_tol < 1)) { err = "inner_tol must be in [0, 1)"; return false; }

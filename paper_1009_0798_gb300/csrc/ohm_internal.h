@@ -230,6 +230,16 @@ cudaError_t launch_pair_apply_dots(const GridDev &g, const float *X, const float
 // dst = (src - sum c_i v_i) * scale
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s);
 
+// The same Krylov vector operations on float64 vectors (the float64 FGMRES of OHM_FP64)
+struct VecSetD {
+    const double *v[KMAX];
+    double c[KMAX];
+    int k = 0;
+};
+cudaError_t launch_mdot(const double *w, const VecSetD &V, const double *wb, int nblk, double *part, double *out,
+                        cudaStream_t s, double *host_out = nullptr);
+cudaError_t launch_maxpy(double *dst, const double *src, const VecSetD &V, double scale, size_t n, cudaStream_t s);
+
 cudaError_t launch_zero_covered(const GridDev &g, double *x, cudaStream_t s);
 
 // Per-instance FGMRES(m) scalars of a batched hierarchy, kept on the device so that a whole

@@ -2178,6 +2178,82 @@ cudaError_t launch_mdot(const float *w, const VecSet &V, const double *wb, int n
     return cudaGetLastError();
 }
 
+// float64 Krylov vectors: one warp per block for the products (double2 loads, float64 sums), a
+// grid-stride loop for the updates
+template <int NV>
+__global__ void __launch_bounds__(256) k_mdot_d(const double *__restrict__ w, VecSetD V, const double *__restrict__ wb,
+                                                int nblk, double *__restrict__ part) {
+    __shared__ double sred[8][NV + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
+    double f[NV + 1];
+#pragma unroll
+    for (int i = 0; i <= NV; i++) f[i] = 0.0;
+    const double wt = b < nblk ? wb[b] : 0.0;
+    if (wt != 0.0) {
+        const double2 *w2 = reinterpret_cast<const double2 *>(w + (size_t)b * 1536);
+#pragma unroll 1
+        for (int q = lane; q < 768; q += 32) {
+            const double2 x = w2[q];
+            f[NV] = fma(x.x, x.x, fma(x.y, x.y, f[NV]));
+#pragma unroll
+            for (int i = 0; i < NV; i++) {
+                const double2 v = reinterpret_cast<const double2 *>(V.v[i] + (size_t)b * 1536)[q];
+                f[i] = fma(x.x, v.x, fma(x.y, v.y, f[i]));
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i <= NV; i++) {
+        double v = f[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sred[warp][i] = v * wt;
+    }
+    __syncthreads();
+    if (threadIdx.x <= NV) {
+        double a = 0.0;
+        for (int q = 0; q < 8; q++) a += sred[q][threadIdx.x];
+        part[(size_t)blockIdx.x * (NV + 1) + threadIdx.x] = a;
+    }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(256) k_maxpy_d(double2 *dst, const double2 *src, VecSetD V, double scale, size_t n2) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n2; q += (size_t)gridDim.x * blockDim.x) {
+        double2 x = src[q];
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            const double2 v = reinterpret_cast<const double2 *>(V.v[i])[q];
+            x.x = fma(-V.c[i], v.x, x.x);
+            x.y = fma(-V.c[i], v.y, x.y);
+        }
+        x.x *= scale;
+        x.y *= scale;
+        dst[q] = x;
+    }
+}
+
+cudaError_t launch_mdot(const double *w, const VecSetD &V, const double *wb, int nblk, double *part, double *out,
+                        cudaStream_t s, double *host_out) {
+    const int grid = (nblk + 7) / 8;
+#define OHM_MDOTD(N) k_mdot_d<N><<<grid, 256, 0, s>>>(w, V, wb, nblk, part)
+    OHM_NV_SWITCH(V.k, OHM_MDOTD)
+#undef OHM_MDOTD
+    k_colsum<<<V.k + 1, 256, 0, s>>>(part, grid, V.k + 1, out, nullptr, host_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpy(double *dst, const double *src, const VecSetD &V, double scale, size_t n, cudaStream_t s) {
+    const size_t n2 = n / 2;
+    const int grid = (int)std::min<size_t>((n2 + 255) / 256, 152 * 16);
+    double2 *d2 = reinterpret_cast<double2 *>(dst);
+    const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#define OHM_MAXPYD(N) k_maxpy_d<N><<<grid, 256, 0, s>>>(d2, s2, V, scale, n2)
+    OHM_NV_SWITCH(V.k, OHM_MAXPYD)
+#undef OHM_MAXPYD
+    return cudaGetLastError();
+}
+
 // column sums of part[ncol][nrow] (column-major) in a fixed order, one thread block per column
 __global__ void __launch_bounds__(1024) k_colsum_cm(const double *__restrict__ part, int nrow, double *__restrict__ out,
                                                     double *__restrict__ host_out) {

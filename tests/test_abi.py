@@ -72,8 +72,8 @@ def test_invalid_descriptors_are_rejected_without_gpu(libohm, case):
         kw["lam"] = 0.0
     elif case == "bad_counts":
         kw["n_coarse"] = 0
-    elif case == "krylov_fp64":
-        kw["krylov"] = 4
+    elif case == "krylov_fp64":  # float64 FGMRES is for single problems only
+        kw.update(krylov=4, n_instances=2)
     elif case == "bad_inner_tol":
         kw.update(precision=libohm.OHM_MIXED, inner_tol=1.5)
     elif case == "bad_precision":

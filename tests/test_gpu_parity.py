@@ -293,6 +293,30 @@ def test_mixed_precision_matches_fp64_oracle(ohm, orc, name, krylov, precision):
         assert st["rel_l2"] == pytest.approx(rel, rel=1e-9)
 
 
+@pytest.mark.parametrize("name", ["uniform_32", "amr_3level", "sinusoid_e1"])
+def test_fp64_fgmres_matches_oracle(ohm, orc, name):
+    """OHM_FP64 with FGMRES(4) right-preconditioned by the float64 V-cycle (one solve to the
+    tolerance per outer iteration) reaches the oracle's converged solution, in fewer V-cycles
+    than the float64 defect correction."""
+    h = HIERS[name]()
+    b, eta = rand_fields(h, 8, 1.0)
+    b = orc.Oracle(h, 0.5, eta).sync_down(b)
+    dt = 4.0 * h.dx(h.nlevels - 1) ** 2
+    want, _ = orc.Oracle(h, 0.5, eta).cn_step(b, dt, 1e-14, 2, 2, 8, 80)
+    cyc = {}
+    for kr in (0, 4):
+        g = make(ohm, h, precision=0, max_outer=80, krylov=kr)
+        B = dev(b)
+        st = ohm.ohm_cn_step(g, B, dev(eta), dt, 1e-12)
+        assert st["converged"]
+        assert rel_err(host(B), want.ravel()) < 1e-10
+        rel, _ = ohm.ohm_residual_norm(g, B)
+        assert rel <= 1e-12
+        cyc[kr] = st["cycles"]
+    print(name, cyc)
+    assert cyc[4] < cyc[0]
+
+
 # relative residual each mixed mode reports at the oracle's converged solution (float64: rounding;
 # float-float: about 2^-48 times the operator's scale), and the accuracy of its norms
 OUTER = {1: (1e-13, 1e-12), 2: (1e-12, 1e-5)}
