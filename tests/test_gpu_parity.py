@@ -462,7 +462,7 @@ def test_zero_field_stays_zero_and_not_converged_status(ohm, orc):
 def test_invalid_calls(ohm):
     h = W.uniform(16, 16, 16, 1.0 / 16)
     with pytest.raises(ohm.OhmError):
-        make(ohm, h, krylov=4)  # Krylov inner solve needs OHM_MIXED
+        make(ohm, h, krylov=4, n_instances=2)  # float64 FGMRES: single problems only
     g = make(ohm, h)
     B = torch.zeros(h.nblocks * 1536, dtype=torch.float64, device="cuda")
     with pytest.raises(ohm.OhmError) as ei:
