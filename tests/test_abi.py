@@ -108,7 +108,7 @@ def test_batch_bytes_grow_with_instances(libohm):
     kry = libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, precision=libohm.OHM_MIXED, n_instances=4, krylov=4)
     assert kry > four  # Krylov basis and per-instance product scratch
     with pytest.raises(libohm.OhmError):
-        libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, n_instances=4, krylov=4)  # FP64 has no Krylov
+        libohm.ohm_hierarchy_bytes(h.base_cells, h.dx0, h.blocks, n_instances=4, krylov=4)  # no batched FP64 Krylov
 
 
 def test_server_rejects_bad_descriptor_without_gpu(libohm):
