@@ -327,17 +327,29 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+# The source of the sweep and of the point update it uses: from the update's constants to the
+# block-pair residual section of ohm_kernels.cu.  A traffic figure stays valid while this text
+# is unchanged (edits elsewhere in the file do not touch the sweep).
+SWEEP_SRC_START = "// Constants of the point update (Eqs. 19-23)"
+SWEEP_SRC_END = "// ------------------------------------------------------------------ residual on brick pairs"
+
+
+def sweep_source_sha() -> str:
+    src = open(os.path.join(ROOT, "paper_1009_0798_gb300", "csrc", "ohm_kernels.cu")).read()
+    i = src.index(SWEEP_SRC_START)
+    j = src.index(SWEEP_SRC_END, i)
+    return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
+
+
 def kernel_traffic(kind: str):
     """DRAM bytes per cell of a kernel from a committed ncu capture, if it was taken on the
-    current kernel source (hash match), else None."""
+    current source of the sweep (hash match), else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    src = open(os.path.join(ROOT, "paper_1009_0798_gb300", "csrc", "ohm_kernels.cu"), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:16]
     d = json.load(open(path))
     e = d.get(kind)
-    if not e or e.get("source_sha") != h:
+    if not e or e.get("sweep_source_sha") != sweep_source_sha():
         return None
     return float(e["dram_bytes_per_cell"])
 
