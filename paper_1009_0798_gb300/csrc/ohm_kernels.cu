@@ -1252,11 +1252,31 @@ struct G18 {
     __device__ static __forceinline__ int at(int i, int j, int k) { return k * PS + j * RRS + i + OFF; }
 };
 
+// Contribution of a cell's face along AX to the flux divergence of component C, for the face on
+// side so (+-1 cell along AX, as a tile offset) with qs = +-1/4: es Q on the high side, -es Q on
+// the low one -- the terms of face_pair for that face alone, in the same operations.
+template <int AX, int C>
+__device__ __forceinline__ float octet_face(const float *__restrict__ tB, int p, int so, float qs, float es) {
+    constexpr int SC = C == 0 ? 1 : (C == 1 ? G18::RRS : G18::PS);
+    const float *BA = tB + AX * G18::CS + p, *BC = tB + C * G18::CS + p;
+    const float d0 = v_sub(BA[SC], BA[-SC]);
+    const float dn = v_sub(BA[so + SC], BA[so - SC]);
+    return v_mul(es, v_mad(v_add(dn, d0), qs, v_sub(BC[0], BC[so])));
+}
+
 // NV >= 0 (APPLY only): also the FGMRES products of the output w with the NV vectors of V and
 // with itself, <w, v_i> and <w, w>, each weighted by wt (h^3 for the cells of a single-level
 // grid) and folded per block pair in a fixed order into part[i][pair] (column-major, so that
 // the column sums read contiguous rows).
-template <bool APPLY, bool RESTRICT, int NV = -1>
+// OCT (residual + restriction with no fine output): the restriction needs only the octet sums
+// of the flux divergence, and in the conservative form (Eq. 8) every flux through a face inside
+// an octet enters its two cells with opposite signs, so the sum over the octet is the net flux
+// through the octet's 24 outer faces.  Each cell of an octet sits at one of its corners and
+// owns exactly one outer face per axis (the high face where its coordinate is odd, the low one
+// where it is even); it computes those three faces instead of its six, and the octet sum of
+// (Y - X) + kc divF(X) is formed as before.  Equal to the full form in exact arithmetic (the
+// internal fluxes cancel); about 40% fewer operations and 30% fewer tile reads per cell.
+template <bool APPLY, bool RESTRICT, int NV = -1, bool OCT = false>
 __global__ void __launch_bounds__(512, NV >= 0 ? 3 : 4)
     k_pair_op(GridDev g, const float *__restrict__ X, const float *__restrict__ Y, const float *__restrict__ eta, float kc,
               float *__restrict__ out, float *__restrict__ coarse, VecSet V = VecSet(), double wt = 0.0,
@@ -1310,16 +1330,27 @@ __global__ void __launch_bounds__(512, NV >= 0 ? 3 : 4)
     for (int h = 0; h < 2; h++) {  // the same cell of block A, then of block B
         const int b = A + h;
         const TileAcc<float, G> acc{tB, tE, G::at(1 + 8 * h + x, 1 + y, 1 + z)};
-        float es[6], dv[3];
-        face_sums<float>(acc, es);
-        cell_divergence<float>(acc, es, dv);
+        float dv[3];
+        if constexpr (OCT) {
+            const int p = acc.p, ox = (x & 1) ? 1 : -1, oy = (y & 1) ? G::RRS : -G::RRS, oz = (z & 1) ? G::PS : -G::PS;
+            const float qx = (x & 1) ? 0.25f : -0.25f, qy = (y & 1) ? 0.25f : -0.25f, qz = (z & 1) ? 0.25f : -0.25f;
+            const float e0 = tE[p];
+            const float esx = v_add(e0, tE[p + ox]), esy = v_add(e0, tE[p + oy]), esz = v_add(e0, tE[p + oz]);
+            dv[0] = v_add(octet_face<1, 0>(tB, p, oy, qy, esy), octet_face<2, 0>(tB, p, oz, qz, esz));
+            dv[1] = v_add(octet_face<0, 1>(tB, p, ox, qx, esx), octet_face<2, 1>(tB, p, oz, qz, esz));
+            dv[2] = v_add(octet_face<0, 2>(tB, p, ox, qx, esx), octet_face<1, 2>(tB, p, oy, qy, esy));
+        } else {
+            float es[6];
+            face_sums<float>(acc, es);
+            cell_divergence<float>(acc, es, dv);
+        }
         const float ev[3] = {acc.template B<0, 0, 0, 0>(), acc.template B<1, 0, 0, 0>(), acc.template B<2, 0, 0, 0>()};
         float o[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const size_t id = ((size_t)b * 3 + c) * B3 + cell;
             o[c] = v_mad(kc, dv[c], APPLY ? ev[c] : v_sub(Y[id], ev[c]));
-            if (out) out[id] = o[c];
+            if (!OCT && out) out[id] = o[c];
             if constexpr (NV >= 0) {
 #pragma unroll
                 for (int i = 0; i < NV; i++) dots[i] = fmaf(o[c], __ldg(V.v[i] + id), dots[i]);
@@ -1363,10 +1394,13 @@ cudaError_t launch_pair_op(const GridDev &g, const float *X, const float *Y, con
     static const bool attr = (cudaFuncSetAttribute(k_pair_op<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                               cudaFuncSetAttribute(k_pair_op<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                               cudaFuncSetAttribute(k_pair_op<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              cudaFuncSetAttribute(k_pair_op<false, true, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                               true);
     (void)attr;
     if (apply)
         k_pair_op<true, false><<<g.nblk / 2, 512, sm, s>>>(g, X, nullptr, eta, (float)kc, out, nullptr);
+    else if (coarse && !out)  // only the octet means: outer faces of each octet
+        k_pair_op<false, true, -1, true><<<g.nblk / 2, 512, sm, s>>>(g, X, Y, eta, (float)kc, nullptr, coarse);
     else if (coarse)
         k_pair_op<false, true><<<g.nblk / 2, 512, sm, s>>>(g, X, Y, eta, (float)kc, out, coarse);
     else

@@ -9,8 +9,9 @@ that grid) and to the oracle's FP64 restatement of the step, and compares elemen
   e + omega (e_GS - e);
 * the same sweep on single blocks (`k_smooth_rb`, a grid whose blocks do not pair along x) and
   as two colour passes (`k_smooth<float>`);
-* residual + restriction into a blocked coarse grid (`k_pair_op` on block pairs) and into a
-  lexicographic one (`k_resid_restrict<float>`), and prolongation (`k_prolong_add8<float>`,
+* residual + restriction into a blocked coarse grid (`k_pair_op` on block pairs, with the fine
+  residual and, as the V-cycle runs it, without: octet means from the octets' outer faces) and
+  into a lexicographic one (`k_resid_restrict<float>`), and prolongation (`k_prolong_add8<float>`,
   `k_prolong_add<float>`), Sec. 2.2;
 * the float32 operator L X on a uniform hierarchy (`k_pair_op`) and on a 3-level AMR hierarchy
   (`k_composite<float,float>`, with coarse-fine ghosts and refluxing);
@@ -175,6 +176,29 @@ def test_float32_residual_restriction_and_prolongation(ohm, orc, to_lex):
     scale = np.abs(cf).max() + np.abs(ff).max()
     print(f"prolongation m={m}: worst {np.abs(got - want).max() / scale:.2e} of scale")
     assert np.abs(got - want).max() <= 8 * U32 * scale
+
+
+@pytest.mark.parametrize("base", [(64, 32, 32), (128, 64, 48)])
+def test_float32_restricted_residual_without_fine_output(ohm, orc, base):
+    """Residual + restriction as the V-cycle launches it, with no fine residual requested: on
+    block pairs each octet's mean is formed from the fluxes through the octet's outer faces (the
+    fluxes through its inner faces cancel in the conservative form).  The coarse values must
+    equal the oracle's restriction of its residual (Sec. 2.2, Eq. 20)."""
+    h = W.uniform(*base, 1.0 / base[0])
+    o = orc.Oracle(h, 0.5)
+    g = mixed(ohm, h)
+    dims, nb, ijk = ohm.ohm_mg_grid_info(g, 0)
+    cdims, cnb, cijk = ohm.ohm_mg_grid_info(g, 1)
+    assert cnb > 0
+    e, r, eta = grid_inputs(dims, 55)
+    dt = 5.0 * h.dx0 ** 2
+    e_d, _ = f32(grid_of_dense(e, ijk))
+    r_d, _ = f32(grid_of_dense(r, ijk))
+    eta_d, _ = f32(grid_of_dense(eta, ijk))
+    c = torch.full((cnb * 1536,), float("nan"), dtype=torch.float32, device="cuda")
+    ohm.ohm_op_grid_resid_restrict_f32(g, 0, e_d, r_d, eta_d, dt, None, c)
+    want = o.grid_restrict(0, o.grid_residual(0, e, r, eta, dt), 3)
+    check32(dense_of_grid(host(c).reshape(cnb, 3, 8, 8, 8), cijk, cdims, 3), want, f"octet restriction {base}")
 
 
 @pytest.mark.parametrize("name", ["uniform_32", "amr_3level"])
