@@ -343,8 +343,8 @@ int ohm_fp64_fma_rate(double *dfma_per_s, void *stream);
  * coordinate out of range or a block twice (checked on the host), or a bad argument return
  * OHM_ERR_INVALID before any work is enqueued.
  * The first call on a device looks up the scratch array's address and keeps it for the life of
- * the process; make that first call before any stream capture, and do not call after a
- * cudaDeviceReset of that device (the kept address is then stale).  All calls share the scratch
+ * the process; do not call after a cudaDeviceReset of that device (the kept address is then
+ * stale).  All calls share the scratch
  * array (it keeps the last call's contents; what must start at zero is cleared by each call),
  * so calls whose work overlaps on the GPU race with each other and must be serialised by the
  * caller. */

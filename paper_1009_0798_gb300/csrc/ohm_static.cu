@@ -13,9 +13,9 @@
 // exits; every call shares it and it keeps the last call's contents (the parts that must
 // start at zero are cleared by each call).  Calls whose work overlaps on the GPU (other
 // streams, other host threads) race on it.  The first call on a device looks up the array's
-// device address and keeps it for the life of the process; make that first call before any
-// stream capture.  A device reset (cudaDeviceReset) invalidates the kept address, so the call
-// must not be used on a device after it has been reset.  Every call copies the block list to the
+// device address and keeps it for the life of the process.  A device reset (cudaDeviceReset)
+// invalidates the kept address, so the call must not be used on a device after it has been
+// reset.  Every call copies the block list to the
 // device, reads the norms back and synchronises its stream before it returns.
 #include <cuda_runtime.h>
 
