@@ -1312,17 +1312,18 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             }
             // ||w - sum h_i v_i||^2 = <w,w> - sum h_i^2 for orthonormal v_i: when that keeps more
             // than 1% of <w,w> the orthogonalisation and the normalisation are one pass,
-            // otherwise the norm is measured after orthogonalising
+            // otherwise the norm is measured after orthogonalising.  The pass that forms
+            // v_{j+1} (or scales it) is issued only when another Arnoldi step follows: after
+            // the last step of a restart cycle, or one that met the target, v_{j+1} is never read.
             const double ww = nn[j + 1];
             double hn;
-            if (ww - proj > 0.01 * ww) {
+            const bool one_pass = ww - proj > 0.01 * ww;
+            if (one_pass) {
                 hn = std::sqrt(ww - proj);
-                LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], S, (T)(1.0 / hn), nel, H->s));
             } else {
                 LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], S, T(1), nel, H->s));
                 if ((st = mdot(H, (const T *)H->kv[j + 1], none, nn))) return st;
                 hn = std::sqrt(std::max(nn[0], 0.0));
-                if (hn > 0) LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], none, (T)(1.0 / hn), nel, H->s));
             }
             h(j + 1, j) = hn;
             // Givens rotations
@@ -1342,6 +1343,12 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
             if (std::fabs(g[j + 1]) <= target * beta0 || !(hn > 0)) {
                 done = true;
                 break;
+            }
+            if (j + 1 < m && *cycles < H->d.max_outer) {  // v_{j+1} for the next Arnoldi step
+                if (one_pass)
+                    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], S, (T)(1.0 / hn), nel, H->s));
+                else
+                    LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[j + 1], (T *)H->kv[j + 1], none, (T)(1.0 / hn), nel, H->s));
             }
         }
         // x += sum y_i z_i with R y = g
@@ -1588,10 +1595,13 @@ int fg_cycle(ohm_hier *H, double lamdt) {
         for (int i = 0; i <= j; i++) S.v[i] = H->kv[i];
         if ((st = mdot_inst_dev(H, H->kv[j + 1], S))) return st;
         FG(FG_ORTHO, j);
-        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], S))) return st;
+        // v_m, formed by the last step, is never read: that step orthogonalises only where a
+        // norm must be measured, and scales nothing
+        const bool last = j + 1 == m;
+        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], S, last ? H->fg.any_need2 : nullptr))) return st;
         if ((st = mdot_inst_dev(H, H->kv[j + 1], none, H->fg.any_need2))) return st;
         FG(FG_RENORM, j);
-        if ((st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], none, H->fg.any_need2))) return st;
+        if (!last && (st = maxpy_inst_dev(H, H->kv[j + 1], H->kv[j + 1], none, H->fg.any_need2))) return st;
         FG(FG_GIVENS, j);
     }
     FG(FG_SOLVE, 0);
