@@ -1272,13 +1272,18 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
     // right-hand side: the float32 copy of the outer residual, or the float64 residual itself
     T *x = (T *)H->eacc, *rhs = (T *)(std::is_same<T, float>::value ? H->rout : H->amrbuf.r);
     int st;
-    CK(cudaMemsetAsync(x, 0, nel * sizeof(T), H->s));
+    // x starts at 0: the first solution update writes Z y without reading x, and x is cleared
+    // only if the solve ends before any update
+    bool x_set = false;
     double nn[KMAX + 1];
     VecSetOf<T> none;
     none.k = 0;
     if ((st = mdot(H, rhs, none, nn))) return st;
     const double beta0 = std::sqrt(nn[0]);
-    if (!(beta0 > 0) || !std::isfinite(beta0)) return OHM_OK;
+    if (!(beta0 > 0) || !std::isfinite(beta0)) {
+        CK(cudaMemsetAsync(x, 0, nel * sizeof(T), H->s));
+        return OHM_OK;
+    }
     double beta = beta0, beta_restart = beta0;
     LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[0], rhs, none, (T)(1.0 / beta), nel, H->s));
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
@@ -1364,7 +1369,8 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
                 Z.v[i] = (const T *)H->kz[i];
                 Z.c[i] = (T)(-y[i]);
             }
-            LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(x, x, Z, T(1), nel, H->s));
+            LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy(x, x_set ? x : nullptr, Z, T(1), nel, H->s));
+            x_set = true;
         }
         if (done || *cycles >= H->d.max_outer || jend == 0) break;
         // restart from the true residual rhs - L x
@@ -1375,6 +1381,7 @@ int inner_fgmres(ohm_hier *H, double lamdt, double target, int *cycles) {
         beta_restart = beta;
         LAUNCH(H, OHM_K_KRYLOV, (int)H->nblocks, launch_maxpy((T *)H->kv[0], (T *)H->kv[0], none, (T)(1.0 / beta), nel, H->s));
     }
+    if (!x_set) CK(cudaMemsetAsync(x, 0, nel * sizeof(T), H->s));
     return OHM_OK;
 }
 

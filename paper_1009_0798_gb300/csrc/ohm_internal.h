@@ -227,7 +227,7 @@ cudaError_t launch_pair_apply_dots(const GridDev &g, const float *X, const float
                                    const VecSet &V, double wt, double *part, double *out, double *host_out,
                                    cudaStream_t s);
 
-// dst = (src - sum c_i v_i) * scale
+// dst = (src - sum c_i v_i) * scale; src null stands for 0
 cudaError_t launch_maxpy(float *dst, const float *src, const VecSet &V, float scale, size_t n, cudaStream_t s);
 
 // The same Krylov vector operations on float64 vectors (the float64 FGMRES of OHM_FP64)

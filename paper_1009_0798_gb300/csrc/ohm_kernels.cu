@@ -2162,11 +2162,11 @@ __global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ part,
     }
 }
 
-// dst = (src - sum_i c_i v_i) * scale (dst may equal src); float4 over n/4 groups
+// dst = (src - sum_i c_i v_i) * scale (dst may equal src; src null reads as 0); float4 over n/4 groups
 template <int NV>
 __global__ void __launch_bounds__(256) k_maxpy(float4 *dst, const float4 *src, VecSet V, float scale, size_t n4) {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
-        float4 x = src[q];
+        float4 x = src ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < NV; i++) {
             const float4 v = reinterpret_cast<const float4 *>(V.v[i])[q];
@@ -2254,7 +2254,7 @@ __global__ void __launch_bounds__(256) k_mdot_d(const double *__restrict__ w, Ve
 template <int NV>
 __global__ void __launch_bounds__(256) k_maxpy_d(double2 *dst, const double2 *src, VecSetD V, double scale, size_t n2) {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n2; q += (size_t)gridDim.x * blockDim.x) {
-        double2 x = src[q];
+        double2 x = src ? src[q] : make_double2(0.0, 0.0);
 #pragma unroll
         for (int i = 0; i < NV; i++) {
             const double2 v = reinterpret_cast<const double2 *>(V.v[i])[q];
